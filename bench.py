@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the batched EFM collision step on GB300.
+
+Workload (one "step"): 4096 spatial cells in 3D, N drawn uniformly from {24, 32, 40, 48}, box
+[-8, 8]^3, hard-sphere kernel, angular rank R = 32, FP32 transforms and products; each step is one
+forward-Euler update F <- F + dt Q^sigma[F] (dt = 0.01) of every cell with the fused FP64 moment,
+entropy and entropy-production reductions, launched through the C ABI (one graph-captured launch
+per distinct N).  Inputs are Maxwellians (density U[0.5,2], |u| <= 1, temperature U[0.5,2]) times
+(1 + 0.3 sum of 3 Gaussian bumps), renormalised, seed 1234 (+ rank).
+
+Metric: collision evaluations per second counted as cell grid points, sum_cells N^3 per second.
+Timing: W warm-up steps, then K steps between CUDA events on the launching stream, bracketed by a
+barrier and device synchronisation; max over ranks.  The inputs (about 0.9 GB) exceed the L2.
+
+--impl reference times the FP64 CPU oracle (direct O(R N^6) sum of the paper's operator) on the
+host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "collision evals/sec (cells×N^d) and HBM GB/s vs roofline; surrogate vs plain"
+UNIT = "cell-points/s"
+L_BOX = 8.0
+R_RANK = 32
+DT = 0.01
+N_CHOICES = (24, 32, 40, 48)
+
+
+def workload_config(ncells):
+    return {"workload": "batched 3D hard-sphere EFM Euler step: %d cells, N~U{24,32,40,48}, L=8, R=32, "
+                        "FP32 transforms, FP64 moments/entropy" % ncells,
+            "cells": ncells, "N_choices": list(N_CHOICES), "L": L_BOX, "kernel": "hard_sphere",
+            "R": R_RANK, "dt": DT, "launch": "one graph-captured persistent cluster launch per N",
+            "l2": "inputs larger than L2 (about 0.9 GB of FP32 cells)"}
+
+
+# ------------------------------------------------------------------ per-cell work model ------
+
+def n_ops(R=R_RANK):
+    """Inverse 3D transforms per cell: n_mu n_phi (1 + n_c) directions + the loss (R = 32 ->
+    (2, 4, 2) -> 24 + 1)."""
+    table = {32: (2, 4, 2), 64: (2, 4, 4)}
+    nmu, nphi, nc = table[R]
+    return nmu * nphi * (1 + nc) + 1
+
+
+def flops_per_cell(N, R=R_RANK):
+    """Algorithmic FP32 flops of one collision evaluation of one cell: (1 + n_ops) real 3D FFTs at
+    2.5 M log2 M flops each (M = N^3), the spectral multiply (2 flops per half-spectrum complex
+    value) and the accumulate (2 flops per real point) of every op."""
+    M = float(N) ** 3
+    ops = n_ops(R)
+    return (1 + ops) * 2.5 * M * np.log2(M) + ops * (M + 2.0 * M)
+
+
+def bytes_per_cell(N):
+    """Algorithmic HBM bytes: read F once, write F once (FP32)."""
+    return 8.0 * float(N) ** 3
+
+
+# ------------------------------------------------------------------ clocks -------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed helpers ------
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle legs ----------
+
+def oracle_cell_seconds(N, seed):
+    import oracle
+    from paper_1704_07369_gb300 import inputs
+    F = inputs.mixture_cell(3, N, L_BOX, seed)
+    p = oracle.Params(d=3, N=N, T=L_BOX, kernel=oracle.KERNEL_HARD_SPHERE, R=R_RANK)
+    t0 = time.perf_counter()
+    oracle.collide(p, F)
+    return time.perf_counter() - t0
+
+
+def mix_rate_from_samples(samples):
+    """Cell-points/s of the oracle on the N mix from timed cells, extrapolating the direct sum's
+    N^6 cost (fit through the timed sizes) to the untimed sizes."""
+    Ns = np.array(sorted(samples))
+    ts = np.array([samples[n] for n in Ns])
+    if len(Ns) >= 2:
+        expo = np.polyfit(np.log(Ns), np.log(ts), 1)[0]
+    else:
+        expo = 6.0
+    t_of = {n: samples.get(n, ts[-1] * (n / Ns[-1]) ** expo) for n in N_CHOICES}
+    mean_pts = np.mean([n ** 3 for n in N_CHOICES])
+    mean_t = np.mean([t_of[n] for n in N_CHOICES])
+    return mean_pts / mean_t, expo, t_of
+
+
+def cpu_baseline():
+    import oracle
+    oracle.build()
+    samples = {24: oracle_cell_seconds(24, 1234), 32: oracle_cell_seconds(32, 1235)}
+    rate, expo, t_of = mix_rate_from_samples(samples)
+    return {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "one full N=24 cell (%.2f s) and one N=32 cell (%.2f s), FP64 direct sum of eq. Qsk "
+                      "(O(R N^6)); N=40/48 extrapolated with the fitted cost exponent %.2f" %
+                      (samples[24], samples[32], expo)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = oracle_cell_seconds(24, 1234 + i)
+        if i >= args.warmup:
+            times.append(dt)
+    t24 = float(np.mean(times))
+    rate, expo, _ = mix_rate_from_samples({24: t24})
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t24 * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.cells),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "each step: one full N=24 cell of the workload by the FP64 direct sum "
+                                       "(eq. Qsk); rate on the N mix extrapolated with cost ~ N^6"},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm -----------------
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1704_07369_gb300 as ef
+    from paper_1704_07369_gb300 import inputs
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    ef.build()
+    seed = 1234 + 100003 * rank
+    Ns = inputs.ragged_sizes(args.cells, seed=seed)
+    offs = np.concatenate([[0], np.cumsum(Ns.astype(np.int64) ** 3)])
+    total_pts = int(offs[-1])
+    host = torch.empty(total_pts, dtype=torch.float32, pin_memory=True)
+    hv = host.numpy()
+    for i, n in enumerate(Ns):
+        hv[offs[i]:offs[i + 1]] = inputs.mixture_cell(3, int(n), L_BOX, seed + i).ravel()
+    plan = ef.Plan(3, None, L_BOX, ef.EF_KERNEL_HARD_SPHERE, R_RANK, ef.EF_PREC_F32, batched_N=Ns)
+    plan.set_graph(True)
+    F = host.to(device)
+    diag = torch.zeros(args.cells, ef.EF_DIAG_STRIDE, dtype=torch.float64, device=device)
+    stream = torch.cuda.Stream(device)
+    nlaunch = len(set(int(n) for n in Ns))
+
+    def step():
+        plan.euler(F, DT, 1, diag, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    st = plan.status(sync=1, reset=1)
+    if st not in (ef.EF_OK,):
+        raise RuntimeError("device status %d after warm-up" % st)
+
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    st = plan.status(sync=1, reset=1)
+    ms_max = max_over_ranks(world, ms, device)
+    step_s = ms_max / 1e3 / args.steps
+    pts_per_step = float(total_pts)
+    value = pts_per_step * world / step_s
+
+    # roofline of the collide kernel (the only kernel in the step): algorithmic FP32 flops per
+    # launch over the average launch duration (launches are back to back on the stream)
+    flops_step = float(sum(flops_per_cell(int(n)) for n in Ns))
+    bytes_step = float(sum(bytes_per_cell(int(n)) for n in Ns))
+    per_launch_s = step_s / nlaunch
+    sm_clock = 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12       # TFLOP/s at the maximum SM clock
+    achieved_tf = flops_step / nlaunch / per_launch_s / 1e12
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = 6800.0
+    hbm_src = "fallback"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            hbm_peak = float(json.load(f).get("hbm_gbs", hbm_peak))
+            hbm_src = "measured"
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("kernel_hash") == ef_kernel_hash():
+            traffic = tj.get("bytes_per_launch_full_step")
+    roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved_tf / fp32_peak, "traffic": traffic,
+            "peak_source": "FP32 CUDA-core peak from unit counts: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
+            "hbm_view": {"achieved_GBps": bytes_step / step_s / 1e9, "peak_GBps": hbm_peak,
+                         "frac": bytes_step / step_s / 1e9 / hbm_peak, "peak_source": hbm_src}}
+
+    # end to end through the C ABI with host buffers: H2D of F, the step, D2H of F and diagnostics
+    e2e = None
+    if not args.no_e2e:
+        out_host = torch.empty_like(host, pin_memory=True)
+        diag_host = torch.empty(diag.shape, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize()
+        barrier(world)
+        k = max(1, min(args.steps, 10))
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(k):
+                F.copy_(host, non_blocking=True)
+                step()
+                out_host.copy_(F, non_blocking=True)
+                diag_host.copy_(diag, non_blocking=True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(world, t0.elapsed_time(t1), device) / k
+        e2e = {"value": pts_per_step * world / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": host.numel() * 4,
+               "d2h_bytes_per_step": out_host.numel() * 4 + diag_host.numel() * 8,
+               "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.cells),
+            "cells_per_s": args.cells * world / step_s, "status": int(st), "roofline": roof,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch * args.steps}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    elif not args.no_cpu_baseline:
+        line["cpu_baseline"] = None
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def ef_kernel_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1704_07369_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".inc", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cells", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,144 @@
+/*
+ * ef.h -- C ABI of the GB300 (sm_103a) library for the entropic Fourier method (EFM) collision
+ * operator of Cai, Fan & Ying, "An entropic Fourier method for the Boltzmann equation"
+ * (arXiv:1704.07369).
+ *
+ * The library evaluates, for every cell of a batch, the discrete collision operator
+ *
+ *     Q^sigma_r = sum_{p,q,s} (A^sigma)^{rs}_{pq} (F_p F_q - F_r F_s)          (eq. Qsr)
+ *
+ * on an N^d periodic velocity grid over [-L, L]^d, in its Fourier form (eq. Qsk) with the
+ * modified-Jackson-filtered kernel modes B^sigma_N(l,m) = sigma_N(l) sigma_N(m) B_N(l,m)
+ * (eq. Bsigma, eq. JacksonFilter2) and the low-rank fast algorithm of Sec. 4.1 (eq. fastAlg):
+ * forward FFT of F, per-direction spectral multiplies, inverse FFTs, gain minus loss.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid: per axis j in {-N/2, ..., N/2-1}, v_j = h j, h = 2L/N; array index i = j + N/2; a cell is
+ *   N^d values in C order (axis 0 slowest).  Cells are stored back to back ("cell-major").
+ * Even N (Sec. 4.1): kernel modes with any component -N/2 are zero; the filter uses n = N/2.  The
+ *   loss term multiplies the grid value F_r (DVM form, eq. QCvr / eq. Qsr).
+ * Memory: every F / Q / diag pointer is a DEVICE pointer owned by the caller, contiguous, of the
+ *   plan's precision (float for EF_PREC_F32, double for EF_PREC_F64; diagnostics are always
+ *   double).  The plan owns its tables, workspace and status word.  No entry point allocates
+ *   device memory, synchronises the device or blocks the host except ef_plan_create* /
+ *   ef_plan_destroy and ef_plan_status(plan, 1).
+ * Streams: operations are enqueued on the given CUDA stream (0 = legacy default stream) and return
+ *   immediately.  The plan's device must be current on the calling thread.
+ * Errors: every function returns an ef_status; on failure nothing is launched and
+ *   ef_last_error() (thread-local) describes why.  Argument checks run before any launch.
+ *   Device-side conditions (non-finite values, a positivity violation under an Euler step) are
+ *   recorded in the plan's status word and read with ef_plan_status().
+ * Thread safety: a plan may be used from one host thread at a time.
+ */
+#ifndef EF_H
+#define EF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ef_plan_s *ef_plan_t;
+typedef struct CUstream_st *ef_stream_t;      /* same object as cudaStream_t */
+
+typedef enum {
+    EF_OK = 0,
+    EF_ERR_INVALID_ARG = 1,   /* a null pointer, bad size, mismatched cell count ... */
+    EF_ERR_UNSUPPORTED = 2,   /* valid request outside what this build implements */
+    EF_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in ef_last_error) */
+    EF_ERR_OOM = 4,           /* device memory for the plan could not be allocated */
+    EF_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+    EF_ERR_POSITIVITY = 6,    /* an Euler step produced F < 0 (dt max nu > 1) */
+    EF_ERR_NOT_FINITE = 7     /* a NaN or Inf reached the output */
+} ef_status;
+
+typedef enum { EF_PREC_F32 = 0, EF_PREC_F64 = 1 } ef_precision;
+
+/* Collision kernels.  EF_KERNEL_MAXWELL: Maxwell molecules, B = 1/(2 pi) in 2D (Sec. 4.2) and
+ * B = 1/(4 pi) in 3D.  EF_KERNEL_HARD_SPHERE: B = |g| / (4 pi) (3D only). */
+typedef enum { EF_KERNEL_MAXWELL = 0, EF_KERNEL_HARD_SPHERE = 1 } ef_kernel;
+
+/* Per-cell diagnostics, EF_DIAG_STRIDE doubles per cell (h = 2L/N, v = h j):
+ *   [0] mass h^d sum F          [1..3] momentum h^d sum F v (unused axes 0)
+ *   [4] energy h^d sum |v|^2 F / 2                [5] entropy eta = h^d sum F ln F (Sec. 4.2)
+ *   [6] entropy production sum Q ln F over F > 0 (<= 0 by the discrete H-theorem, Theorem 1)
+ *   [7] min F      [8] max nu (collision frequency; 0 when not computed)
+ *   [9] min of the updated F (Euler), or min Q (collide / moments with Q). */
+#define EF_DIAG_STRIDE 10
+
+/* Full description of one discretisation.  Zero / negative fields take the defaults below. */
+typedef struct {
+    int d;                 /* 2 or 3 */
+    int N;                 /* grid points per axis; even, >= 8, one of the built sizes */
+    double L;              /* box half width, > 0 */
+    ef_kernel kernel;
+    int R;                 /* angular rank: number of (l, m) terms of the low-rank kernel (eq. fastAlg);
+                              2D: even, >= 2; 3D: 2 n_mu n_phi n_c */
+    ef_precision prec;
+    double R_tr;           /* truncation radius R of eq. approximated_collision; default
+                              4 L / (3 sqrt 2 + 1), the largest allowed by Sec. 1.2 */
+    int n_mu, n_phi, n_c;  /* 3D angular quadrature; default from R (32 -> 2,4,2; 64 -> 2,4,4) */
+    int J;                 /* 3D Maxwell: Gaussian terms for 1/|y+z|; default 6 */
+    int sigma_enabled;     /* 1 (default, EFM) or 0: no filter (Fourier collocation method);
+                              pass -1 for the default */
+} ef_plan_desc;
+
+/* Create a plan for cells of one size N.  Cells are passed at call time (ncells), cell c at
+ * element offset c * N^d.  Argument meaning as in ef_plan_desc. */
+ef_status ef_plan_create(int d, int N, double L, ef_kernel kernel, int R, ef_precision prec,
+                         ef_plan_t *out);
+
+/* As ef_plan_create with every field of ef_plan_desc. */
+ef_status ef_plan_create_ex(const ef_plan_desc *desc, ef_plan_t *out);
+
+/* Plan for a fixed batch of ncells cells of uneven size: N_host[c] (host array) is the size of
+ * cell c; cell c starts at element offset sum_{c' < c} N_host[c']^d.  One launch per distinct
+ * N, all enqueued on the caller's stream (captured once into a CUDA graph when
+ * ef_plan_set_graph(plan, 1)). */
+ef_status ef_plan_create_batched(int d, int64_t ncells, const int *N_host, double L, ef_kernel kernel,
+                                 int R, ef_precision prec, ef_plan_t *out);
+
+ef_status ef_plan_destroy(ef_plan_t plan);
+
+/* Q = Q^sigma[F] for ncells cells (eq. Qsk / eq. Qsr).  F_dev and Q_dev must not overlap.
+ * For a batched plan ncells must equal the plan's cell count. */
+ef_status ef_collide(ef_plan_t plan, const void *F_dev, void *Q_dev, int64_t ncells, ef_stream_t stream);
+
+/* nsteps forward Euler steps F <- F + dt Q^sigma[F], in place.  If diag_dev is not null it
+ * receives nsteps * ncells * EF_DIAG_STRIDE doubles ([step][cell][k], moments of F before each
+ * step, entropy production of that step, max nu and the min of the updated F); a step whose
+ * updated F has a negative value sets EF_ERR_POSITIVITY in the status word (positivity holds when
+ * dt max nu <= 1, proof of Theorem 1). */
+ef_status ef_euler_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, double *diag_dev,
+                        int64_t ncells, ef_stream_t stream);
+
+/* Moments and entropy of each cell (layout EF_DIAG_STRIDE, entries [0..7] and [9]; [8] = 0).
+ * Q_dev may be null; then [6] = 0 and [9] = 0. */
+ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_dev, double *out_dev,
+                             int64_t ncells, ef_stream_t stream);
+
+/* Read the plan's device status word (the first error seen by a kernel, EF_OK if none).  With
+ * sync = 1 the call first synchronises the plan's device; with sync = 0 it returns the value
+ * copied back by the last synchronising call.  reset = 1 clears the word after reading. */
+ef_status ef_plan_status(ef_plan_t plan, int sync, int reset);
+
+/* Route ef_collide / ef_euler_step through a CUDA graph captured on first use per
+ * (F, Q, ncells, stream) (1), or launch directly (0, default). */
+ef_status ef_plan_set_graph(ef_plan_t plan, int enable);
+
+/* Introspection (host values):  info[0] = d, [1] = number of distinct N, [2] = number of
+ * spectral directions (inverse transforms per cell, loss included) of the first class, [3] =
+ * cluster size of the first class, [4] = threads per CTA of the first class, [5] = cells (batched
+ * plans; 0 otherwise), [6] = precision, [7] = kernel launches per ef_collide. */
+ef_status ef_plan_info(ef_plan_t plan, int64_t info[8]);
+
+const char *ef_status_string(ef_status s);
+const char *ef_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EF_H */

@@ -69,6 +69,7 @@ def _load():
         lib.oracle_idft_real.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
         lib.oracle_collide.argtypes = [pp, dp, dp]
         lib.oracle_collide_points.argtypes = [pp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp]
+        lib.oracle_collide_points_hat.argtypes = [pp, dp, dp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), dp]
         lib.oracle_G.argtypes = [pp, ctypes.c_int64, dp]
         lib.oracle_dvm.argtypes = [pp, dp, dp, dp, dp]
         lib.oracle_nu.argtypes = [pp, dp, dp]
@@ -178,6 +179,36 @@ def collide_points(p: Params, F: np.ndarray, idx) -> np.ndarray:
     Q = np.zeros(idx.size)
     if _load().oracle_collide_points(ctypes.byref(p.c()), _dp(F), int(idx.size),
                                      idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(Q)):
+        raise ValueError("bad parameters")
+    return Q
+
+
+def dft_fft(F: np.ndarray) -> np.ndarray:
+    """The DFT of eq. DFT computed with NumPy's FFT (a library primitive) for large grids:
+    Fh_k = N^{-d} sum_j F_j exp(-2 pi i k.j / N) with j = i - N/2, i.e. the FFT over array
+    indices times the phase (-1)^{sum k}."""
+    F = np.asarray(F, dtype=np.float64)
+    d, N = F.ndim, F.shape[0]
+    Fh = np.fft.fftn(F) / F.size
+    k = np.fft.fftfreq(N, 1.0 / N).astype(np.int64)
+    ph = np.ones(())
+    for a in range(d):
+        shape = [1] * d
+        shape[a] = N
+        ph = ph * np.exp(1j * np.pi * k * (N // 2) * 2.0 / N).reshape(shape)
+    return Fh * ph
+
+
+def collide_points_fft(p: Params, F: np.ndarray, idx) -> np.ndarray:
+    """Q^sigma[F] at flat grid indices ``idx``, rank-separated form, with Fh from NumPy's FFT."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    Fh = dft_fft(F)
+    re = np.ascontiguousarray(Fh.real.ravel())
+    im = np.ascontiguousarray(Fh.imag.ravel())
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    Q = np.zeros(idx.size)
+    if _load().oracle_collide_points_hat(ctypes.byref(p.c()), _dp(re), _dp(im), _dp(F), int(idx.size),
+                                         idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(Q)):
         raise ValueError("bad parameters")
     return Q
 

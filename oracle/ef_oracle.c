@@ -425,17 +425,16 @@ int oracle_collide(const oracle_params *p, const double *F, double *Q)
 /* Q^sigma at selected grid points (flat indices idx[0..npts)), from the rank-separated form
  * (eq. fastFGM evaluated by collocation):
  *   Q_r = sum_t w_t [sum_l sigma beta_t Fh_l E_l(r)] [sum_m sigma gamma_t Fh_m E_m(r)]
- *         - [sum_l Fh_l E_l(r)] [sum_m B^sigma(m,m) Fh_m E_m(r)].
- * Fh is computed by the direct DFT; cost O(N^{2d} + npts R N^d). */
-int oracle_collide_points(const oracle_params *p, const double *F, int npts, const int64_t *idx, double *Q)
+ *         - F_r [sum_m B^sigma(m,m) Fh_m E_m(r)].
+ * Fh (the DFT of F, eq. DFT) is given; F_r is the grid value.  Cost O(npts R N^d). */
+int oracle_collide_points_hat(const oracle_params *p, const double *Fr, const double *Fi, const double *F,
+                              int npts, const int64_t *idx, double *Q)
 {
     kern_tables kt;
     if (make_tables(p, &kt)) { free_tables(&kt); return -1; }
     const int64_t M = kt.M;
     const int N = p->N, d = p->d;
-    double *Fr = malloc(sizeof(double) * M), *Fi = malloc(sizeof(double) * M);
     double *bmm = malloc(sizeof(double) * M);
-    oracle_dft(d, N, F, Fr, Fi);
     for (int64_t m = 0; m < M; ++m) bmm[m] = bsig(&kt, m, m);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int n = 0; n < npts; ++n) {
@@ -460,16 +459,24 @@ int oracle_collide_points(const oracle_params *p, const double *F, int npts, con
             }
             gain += kt.w[t] * (ar * br - ai * bi);
         }
-        double fr = 0, nr = 0;
-        for (int64_t l = 0; l < M; ++l) {
-            double xr = Fr[l] * er[l] - Fi[l] * ei[l];
-            fr += xr; nr += bmm[l] * xr;
-        }
-        Q[n] = gain - fr * nr;
+        double nr = 0;
+        for (int64_t l = 0; l < M; ++l) nr += bmm[l] * (Fr[l] * er[l] - Fi[l] * ei[l]);
+        Q[n] = gain - F[idx[n]] * nr;
         free(er); free(ei);
     }
-    free(Fr); free(Fi); free(bmm); free_tables(&kt);
+    free(bmm); free_tables(&kt);
     return 0;
+}
+
+/* As oracle_collide_points_hat with Fh from the direct DFT, O(N^{2d} + npts R N^d). */
+int oracle_collide_points(const oracle_params *p, const double *F, int npts, const int64_t *idx, double *Q)
+{
+    const int64_t M = ipow(p->N, p->d);
+    double *Fr = malloc(sizeof(double) * M), *Fi = malloc(sizeof(double) * M);
+    oracle_dft(p->d, p->N, F, Fr, Fi);
+    int rc = oracle_collide_points_hat(p, Fr, Fi, F, npts, idx, Q);
+    free(Fr); free(Fi);
+    return rc;
 }
 
 /* G(y, z) = sum_{i,j} B^sigma(i,j) E_{-i}(y) E_{-j}(z) (eq. G / tildeG without the N^{-2d}

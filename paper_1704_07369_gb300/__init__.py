@@ -1,0 +1,217 @@
+"""Python binding of the GB300 EFM collision library (``include/ef.h``, ``libef.so``).
+
+Argument marshalling only: every step of the collision operator runs in the library's CUDA
+kernels.  Torch tensors provide device memory and streams; pointers are passed through the C ABI.
+The library must have been built (``build()``); there is no CPU or PyTorch fallback, and a
+missing or unloadable ``libef.so`` raises immediately.
+
+Names follow the C API: ``ef_plan_create``, ``ef_plan_create_ex``, ``ef_plan_create_batched``,
+``ef_collide``, ``ef_euler_step``, ``ef_moments_entropy``, ``ef_plan_status``, ...
+The :class:`Plan` class wraps a handle with the same operations as methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libef.so")
+
+EF_OK = 0
+EF_ERR_INVALID_ARG = 1
+EF_ERR_UNSUPPORTED = 2
+EF_ERR_CUDA = 3
+EF_ERR_OOM = 4
+EF_ERR_TIMEOUT = 5
+EF_ERR_POSITIVITY = 6
+EF_ERR_NOT_FINITE = 7
+
+EF_PREC_F32 = 0
+EF_PREC_F64 = 1
+EF_KERNEL_MAXWELL = 0
+EF_KERNEL_HARD_SPHERE = 1
+EF_DIAG_STRIDE = 10
+
+# every symbol include/ef.h declares
+SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
+           "ef_collide", "ef_euler_step", "ef_moments_entropy", "ef_plan_status",
+           "ef_plan_set_graph", "ef_plan_info", "ef_status_string", "ef_last_error")
+
+
+class EfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (status, msg))
+        self.status = status
+
+
+class ef_plan_desc(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("N", ctypes.c_int), ("L", ctypes.c_double),
+                ("kernel", ctypes.c_int), ("R", ctypes.c_int), ("prec", ctypes.c_int),
+                ("R_tr", ctypes.c_double), ("n_mu", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("n_c", ctypes.c_int), ("J", ctypes.c_int), ("sigma_enabled", ctypes.c_int)]
+
+
+_lib = None
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    from . import buildlib
+    return buildlib.build(force=force, verbose=verbose)
+
+
+def lib():
+    """The loaded ``libef.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIBPATH):
+            raise RuntimeError("libef.so is not built at %s (call paper_1704_07369_gb300.build())" % LIBPATH)
+        L = ctypes.CDLL(LIBPATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        pp = ctypes.POINTER(vp)
+        L.ef_plan_create.argtypes = [i32, i32, dbl, i32, i32, i32, pp]
+        L.ef_plan_create_ex.argtypes = [ctypes.POINTER(ef_plan_desc), pp]
+        L.ef_plan_create_batched.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_int), dbl, i32, i32, i32, pp]
+        L.ef_plan_destroy.argtypes = [vp]
+        L.ef_collide.argtypes = [vp, vp, vp, i64, vp]
+        L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
+        L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.ef_plan_status.argtypes = [vp, i32, i32]
+        L.ef_plan_set_graph.argtypes = [vp, i32]
+        L.ef_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
+        L.ef_status_string.restype = ctypes.c_char_p
+        L.ef_status_string.argtypes = [i32]
+        L.ef_last_error.restype = ctypes.c_char_p
+        for name in SYMBOLS:
+            if name not in ("ef_status_string", "ef_last_error"):
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != EF_OK:
+        L = lib()
+        raise EfError(L.ef_status_string(st).decode(), L.ef_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ C-API mirrors ----------
+
+def ef_plan_create(d, N, L, kernel, R, prec):
+    h = ctypes.c_void_p()
+    _check(lib().ef_plan_create(d, N, float(L), kernel, R, prec, ctypes.byref(h)))
+    return h
+
+
+def ef_plan_create_ex(d, N, L, kernel, R, prec, R_tr=0.0, n_mu=0, n_phi=0, n_c=0, J=0, sigma_enabled=-1):
+    desc = ef_plan_desc(d, N, float(L), kernel, R, prec, float(R_tr), n_mu, n_phi, n_c, J, sigma_enabled)
+    h = ctypes.c_void_p()
+    _check(lib().ef_plan_create_ex(ctypes.byref(desc), ctypes.byref(h)))
+    return h
+
+
+def ef_plan_create_batched(d, N_list, L, kernel, R, prec):
+    arr = (ctypes.c_int * len(N_list))(*[int(n) for n in N_list])
+    h = ctypes.c_void_p()
+    _check(lib().ef_plan_create_batched(d, len(N_list), arr, float(L), kernel, R, prec, ctypes.byref(h)))
+    return h
+
+
+def ef_plan_destroy(plan):
+    _check(lib().ef_plan_destroy(plan))
+
+
+def ef_collide(plan, F, Q, ncells, stream=None):
+    _check(lib().ef_collide(plan, _ptr(F), _ptr(Q), int(ncells), _stream(stream)))
+
+
+def ef_euler_step(plan, F, dt, nsteps, diag, ncells, stream=None):
+    _check(lib().ef_euler_step(plan, _ptr(F), float(dt), int(nsteps), _ptr(diag), int(ncells), _stream(stream)))
+
+
+def ef_moments_entropy(plan, F, Q, out, ncells, stream=None):
+    _check(lib().ef_moments_entropy(plan, _ptr(F), _ptr(Q), _ptr(out), int(ncells), _stream(stream)))
+
+
+def ef_plan_status(plan, sync=1, reset=0):
+    return lib().ef_plan_status(plan, int(sync), int(reset))
+
+
+def ef_plan_set_graph(plan, enable):
+    _check(lib().ef_plan_set_graph(plan, int(enable)))
+
+
+def ef_plan_info(plan):
+    info = (ctypes.c_int64 * 8)()
+    _check(lib().ef_plan_info(plan, info))
+    keys = ("d", "classes", "directions", "cluster", "threads", "cells", "prec", "launches")
+    return dict(zip(keys, list(info)))
+
+
+class Plan:
+    """Owning wrapper of an ``ef_plan_t``."""
+
+    def __init__(self, d, N, L, kernel, R, prec, batched_N=None, **ex):
+        self.d, self.L, self.prec, self.kernel, self.R = d, L, prec, kernel, R
+        if batched_N is not None:
+            self.N_list = [int(n) for n in batched_N]
+            self.handle = ef_plan_create_batched(d, self.N_list, L, kernel, R, prec)
+            self.ncells = len(self.N_list)
+        else:
+            self.N_list = None
+            self.N = N
+            self.handle = ef_plan_create_ex(d, N, L, kernel, R, prec, **ex) if ex else \
+                ef_plan_create(d, N, L, kernel, R, prec)
+            self.ncells = None
+
+    def collide(self, F, Q, ncells=None, stream=None):
+        ef_collide(self.handle, F, Q, self._n(F, ncells), stream)
+
+    def euler(self, F, dt, nsteps=1, diag=None, ncells=None, stream=None):
+        ef_euler_step(self.handle, F, dt, nsteps, diag, self._n(F, ncells), stream)
+
+    def moments(self, F, Q, out, ncells=None, stream=None):
+        ef_moments_entropy(self.handle, F, Q, out, self._n(F, ncells), stream)
+
+    def status(self, sync=1, reset=0):
+        return ef_plan_status(self.handle, sync, reset)
+
+    def set_graph(self, enable=True):
+        ef_plan_set_graph(self.handle, enable)
+
+    def info(self):
+        return ef_plan_info(self.handle)
+
+    def _n(self, F, ncells):
+        if ncells is not None:
+            return ncells
+        if self.ncells is not None:
+            return self.ncells
+        return F.numel() // (self.N ** self.d)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            ef_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,418 @@
+// ef_collide_impl.cuh -- the fused EFM collision kernel (one thread-block cluster per cell).
+//
+// Per cell (Sec. 4.1, eq. fastAlg; the DVM form eq. Qsr evaluated by collocation, Sec. 3.1):
+//   F1  each CTA of the cluster owns N/C planes of axis 0; it transforms its planes along the
+//       last axis (real -> half complex) and, in 3D, along axis 1, into its shared-memory slab.
+//   F2  every thread gathers one axis-0 pencil (a fixed spectral column p) from the slabs of all
+//       CTAs through distributed shared memory, finishes the forward transform along axis 0 and
+//       keeps the pencil Fhat[:, p] in registers for the rest of the cell.
+//   for each op (one spectral direction u, or the loss):
+//     A  Fhat[:, p] * M_u[:, p] (filter and radial kernel factor, L2-resident table), inverse
+//        transform along axis 0, scatter the result to the owning CTAs' slabs (DSMEM stores).
+//     B  each CTA finishes the inverse transform of its planes (axis 1, then half complex ->
+//        real along the last axis, two rows per thread) and folds the real-space values into the
+//        S / G accumulators, or, for the loss op, forms Q = G - F nu and writes the output
+//        (Q, or F + dt Q for an Euler step) with FP64 diagnostics.
+// Two cluster barriers per op separate the scatter (A) from the local passes (B).
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "ef_fft.cuh"
+#include "ef_internal.h"
+
+namespace ef {
+
+namespace cg = cooperative_groups;
+
+constexpr int kMaxThreads = 320;
+
+template <typename T>
+__device__ __forceinline__ void sincospi_t(T x, T *s, T *c);
+template <>
+__device__ __forceinline__ void sincospi_t<float>(float x, float *s, float *c) { sincospif(x, s, c); }
+template <>
+__device__ __forceinline__ void sincospi_t<double>(double x, double *s, double *c) { sincospi(x, s, c); }
+
+template <typename T>
+__device__ __forceinline__ T log_t(T x);
+template <>
+__device__ __forceinline__ float log_t<float>(float x) { return logf(x); }
+template <>
+__device__ __forceinline__ double log_t<double>(double x) { return log(x); }
+
+__device__ __forceinline__ void record_status(int *status, int code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+// shared-memory bytes of one CTA (must match the carve-up in the kernel)
+template <typename T, int D, int N>
+__host__ __device__ constexpr size_t smem_bytes_for(int planes, int sg_global)
+{
+    constexpr int H = N / 2 + 1;
+    constexpr int N1 = (D == 3) ? N : 1;
+    size_t is = (size_t)planes * N1 * H * sizeof(C2<T>);
+    size_t sg = sg_global ? 0 : 2 * (size_t)planes * N1 * (N + 1) * sizeof(T);
+    sg = (sg + 15) / 16 * 16;
+    size_t tw = (size_t)N * sizeof(C2<T>);
+    size_t part = (32 + 1) * kDiag * sizeof(double);
+    return is + sg + tw + part;
+}
+
+template <typename T, int D, int N>
+__global__ void __launch_bounds__(kMaxThreads, 1) collide_kernel(const CollideArgs a)
+{
+    constexpr int H = N / 2 + 1;
+    constexpr int N1 = (D == 3) ? N : 1;
+    constexpr int NP = N1 * H;         // spectral columns of one axis-0 plane = pencils
+    constexpr int RS = N + 1;          // padded real row stride of S and G
+    constexpr int64_t CELL = (int64_t)N * N1 * N;
+
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int P = a.planes;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int rows = P * N1;           // real rows owned by this CTA
+    const int npairs = rows / 2;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2<T> *Is = reinterpret_cast<C2<T> *>(smem_raw);
+    size_t off = (size_t)P * NP * sizeof(C2<T>);
+    T *Sb, *Gb;
+    if (a.sg_global) {
+        const int64_t slot = blockIdx.x;
+        T *base = reinterpret_cast<T *>(a.sg_ws) + slot * (int64_t)2 * rows * RS;
+        Sb = base;
+        Gb = base + (int64_t)rows * RS;
+    } else {
+        Sb = reinterpret_cast<T *>(smem_raw + off);
+        Gb = Sb + (size_t)rows * RS;
+        off += 2 * (size_t)rows * RS * sizeof(T);
+        off = (off + 15) / 16 * 16;
+    }
+    C2<T> *tw = reinterpret_cast<C2<T> *>(smem_raw + off);
+    off += (size_t)N * sizeof(C2<T>);
+    double *part = reinterpret_cast<double *>(smem_raw + off);      // [32 warps + 1][kDiag]
+
+    for (int j = tid; j < N; j += nt) {
+        T s, c;
+        sincospi_t<T>(T(2 * j) / T(N), &s, &c);
+        tw[j] = C2<T>{c, -s};
+    }
+    __syncthreads();
+
+    const int64_t nclusters = gridDim.x / C;
+    const int64_t cid = blockIdx.x / C;
+    const int pencil = rank * nt + tid;            // this thread's spectral column (stage A)
+    const bool has_pencil = pencil < NP;
+    const T scale = T(1) / T(CELL);
+    const T *Mbase = reinterpret_cast<const T *>(a.mult);
+
+    for (int64_t c = cid; c < a.ncells; c += nclusters) {
+        const int64_t coff = a.cell_off ? a.cell_off[c] : c * CELL;
+        const int64_t cglob = a.cell_id ? a.cell_id[c] : c;
+        const T *F = reinterpret_cast<const T *>(a.F) + coff;
+        T *Out = reinterpret_cast<T *>(a.Q) + coff;
+
+        // ---------------- F1: own planes, last axis real -> half complex (two rows per thread)
+        for (int q = tid; q < npairs; q += nt) {
+            const int r0 = 2 * q;
+            const T *src = F + ((int64_t)rank * rows + r0) * N;
+            T x0[N], x1[N];
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                x0[n] = src[n];
+                x1[n] = src[N + n];
+            }
+            C2<T> X0[H], X1[H];
+            r2c_pair<N, T>(x0, x1, X0, X1, tw);
+#pragma unroll
+            for (int k = 0; k < H; ++k) {
+                Is[r0 * H + k] = X0[k];
+                Is[(r0 + 1) * H + k] = X1[k];
+            }
+        }
+        if constexpr (D == 3) {
+            __syncthreads();
+            for (int q = tid; q < P * H; q += nt) {            // axis 1, forward
+                const int zl = q / H, lx = q % H;
+                C2<T> *col = Is + (size_t)zl * NP + lx;
+                C2<T> v[N];
+#pragma unroll
+                for (int y = 0; y < N; ++y) v[y] = col[y * H];
+                fft<N, -1, N>(v, tw);
+#pragma unroll
+                for (int y = 0; y < N; ++y) col[y * H] = v[y];
+            }
+        }
+        cl.sync();
+
+        // ---------------- F2: gather the axis-0 pencil and finish the forward transform
+        C2<T> fh[N];
+        if (has_pencil) {
+#pragma unroll
+            for (int z = 0; z < N; ++z) {
+                const int owner = z / P, zl = z - owner * P;
+                const C2<T> *src = cl.map_shared_rank(Is, owner);
+                fh[z] = src[(size_t)zl * NP + pencil];
+            }
+            fft<N, -1, N>(fh, tw);
+#pragma unroll
+            for (int z = 0; z < N; ++z) fh[z] = cscale(fh[z], scale);
+        }
+        cl.sync();
+
+        // diagnostics accumulators (loss op only)
+        double dsum[kDiag];
+#pragma unroll
+        for (int k = 0; k < kDiag; ++k) dsum[k] = 0.0;
+        double dmin_f = 1e300, dmax_nu = -1e300, dmin_out = 1e300;
+
+        for (int o = 0; o < a.nops; ++o) {
+            const Op op = a.ops[o];
+            // ---------------- A: multiply, inverse along axis 0, scatter to owners
+            if (has_pencil) {
+                const T *M = Mbase + (size_t)op.dir * N * NP + pencil;
+                C2<T> v[N];
+#pragma unroll
+                for (int z = 0; z < N; ++z) v[z] = cscale(fh[z], __ldg(M + (size_t)z * NP));
+                fft<N, 1, N>(v, tw);
+#pragma unroll
+                for (int z = 0; z < N; ++z) {
+                    const int owner = z / P, zl = z - owner * P;
+                    C2<T> *dst = cl.map_shared_rank(Is, owner);
+                    dst[(size_t)zl * NP + pencil] = v[z];
+                }
+            }
+            cl.sync();
+
+            // ---------------- B: local inverse passes and accumulation
+            if constexpr (D == 3) {
+                for (int q = tid; q < P * H; q += nt) {        // axis 1, inverse
+                    const int zl = q / H, lx = q % H;
+                    C2<T> *col = Is + (size_t)zl * NP + lx;
+                    C2<T> v[N];
+#pragma unroll
+                    for (int y = 0; y < N; ++y) v[y] = col[y * H];
+                    fft<N, 1, N>(v, tw);
+#pragma unroll
+                    for (int y = 0; y < N; ++y) col[y * H] = v[y];
+                }
+                __syncthreads();
+            }
+            for (int q = tid; q < npairs; q += nt) {
+                const int r0 = 2 * q;
+                C2<T> X0[H], X1[H];
+#pragma unroll
+                for (int k = 0; k < H; ++k) {
+                    X0[k] = Is[r0 * H + k];
+                    X1[k] = Is[(r0 + 1) * H + k];
+                }
+                T y0[N], y1[N];
+                c2r_pair<N, T>(X0, X1, y0, y1, tw);
+                T *S0 = Sb + (size_t)r0 * RS, *S1 = S0 + RS;
+                T *G0 = Gb + (size_t)r0 * RS, *G1 = G0 + RS;
+                const T w = T(op.w);
+                switch (op.kind) {
+                case OP_S_SET:
+#pragma unroll
+                    for (int n = 0; n < N; ++n) { S0[n] = w * y0[n]; S1[n] = w * y1[n]; }
+                    break;
+                case OP_S_ADD:
+#pragma unroll
+                    for (int n = 0; n < N; ++n) { S0[n] += w * y0[n]; S1[n] += w * y1[n]; }
+                    break;
+                case OP_G_SET:
+#pragma unroll
+                    for (int n = 0; n < N; ++n) { G0[n] = y0[n] * S0[n]; G1[n] = y1[n] * S1[n]; }
+                    break;
+                case OP_G_ADD:
+#pragma unroll
+                    for (int n = 0; n < N; ++n) { G0[n] += y0[n] * S0[n]; G1[n] += y1[n] * S1[n]; }
+                    break;
+                default: {  // OP_LOSS: Q = G - F nu; output; diagnostics
+                    const int64_t grow0 = (int64_t)rank * rows + r0;
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int64_t grow = grow0 + half;
+                        const T *nu = half ? y1 : y0;
+                        const T *G = half ? G1 : G0;
+                        const T *Frow = F + grow * N;
+                        T *Orow = Out + grow * N;
+                        // velocity indices of this row: grow = z * N1 + y (3D) or grow = z (2D)
+                        const int jz = (int)(grow / N1) - N / 2;
+                        const int jy = (D == 3) ? (int)(grow % N1) - N / 2 : 0;
+                        T s_m = 0, s_mx = 0, s_e2 = 0, s_eta = 0, s_prod = 0;
+                        T mn_f = Frow[0], mx_nu = nu[0], mn_out = T(3.0e38);
+                        bool bad = false, neg = false;
+#pragma unroll
+                        for (int n = 0; n < N; ++n) {
+                            const T f = Frow[n];
+                            const T qv = G[n] - f * nu[n];
+                            T outv;
+                            if (a.out_mode == OUT_EULER) {
+                                outv = f + T(a.dt) * qv;
+                                if (outv < T(0) && T(a.dt) * nu[n] > T(1)) neg = true;
+                            } else {
+                                outv = qv;
+                            }
+                            Orow[n] = outv;
+                            if (!isfinite(outv)) bad = true;
+                            if (a.diag) {
+                                const T jx = T(n - N / 2);
+                                s_m += f;
+                                s_mx += f * jx;
+                                s_e2 += f * jx * jx;
+                                if (f > T(0)) {
+                                    const T lf = log_t<T>(f);
+                                    s_eta += f * lf;
+                                    s_prod += qv * lf;
+                                }
+                                mn_f = f < mn_f ? f : mn_f;
+                                mx_nu = nu[n] > mx_nu ? nu[n] : mx_nu;
+                                mn_out = outv < mn_out ? outv : mn_out;
+                            }
+                        }
+                        if (bad) record_status(a.status, 7);     // EF_ERR_NOT_FINITE
+                        if (neg) record_status(a.status, 6);     // EF_ERR_POSITIVITY
+                        if (a.diag) {
+                            // moments in array-axis order: [1] axis 0, [2] axis 1, [3] axis 2
+                            const double m = (double)s_m;
+                            dsum[0] += m;
+                            if (D == 3) {
+                                dsum[1] += m * jz;
+                                dsum[2] += m * jy;
+                                dsum[3] += (double)s_mx;
+                            } else {
+                                dsum[1] += m * jz;
+                                dsum[2] += (double)s_mx;
+                            }
+                            dsum[4] += (double)s_e2 + m * ((double)jy * jy + (double)jz * jz);
+                            dsum[5] += (double)s_eta;
+                            dsum[6] += (double)s_prod;
+                            dmin_f = fmin(dmin_f, (double)mn_f);
+                            dmax_nu = fmax(dmax_nu, (double)mx_nu);
+                            dmin_out = fmin(dmin_out, (double)mn_out);
+                        }
+                    }
+                } break;
+                }
+            }
+            cl.sync();
+        }
+
+        // ---------------- per-cell FP64 reduction of the diagnostics
+        if (a.diag) {
+            dsum[7] = dmin_f;
+            dsum[8] = dmax_nu;
+            dsum[9] = dmin_out;
+            const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
+#pragma unroll
+            for (int k = 0; k < kDiag; ++k) {
+                double v = dsum[k];
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) {
+                    const double u = __shfl_xor_sync(0xffffffffu, v, s);
+                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                }
+                if (lane == 0) part[warp * kDiag + k] = v;
+            }
+            __syncthreads();
+            if (tid < kDiag) {
+                const int k = tid;
+                double v = part[k];
+                for (int w2 = 1; w2 < nw; ++w2) {
+                    const double u = part[w2 * kDiag + k];
+                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                }
+                part[32 * kDiag + k] = v;
+            }
+            cl.sync();
+            if (rank == 0 && tid < kDiag) {
+                const int k = tid;
+                double v = part[32 * kDiag + k];
+                for (int r = 1; r < C; ++r) {
+                    const double *rp = cl.map_shared_rank(part, r);
+                    const double u = rp[32 * kDiag + k];
+                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                }
+                const double hd = (D == 3) ? a.h * a.h * a.h : a.h * a.h;
+                if (k == 0 || k == 5) v *= hd;
+                else if (k >= 1 && k <= 3) v *= hd * a.h;
+                else if (k == 4) v *= 0.5 * hd * a.h * a.h;
+                if (D == 2 && k == 3) v = 0.0;
+                a.diag[cglob * kDiag + k] = v;
+            }
+            cl.sync();
+        }
+    }
+    cl.sync();   // no CTA leaves while a peer may still read its shared memory
+}
+
+// ------------------------------------------------------------------ moments kernel ---------
+
+// One CTA per cell: FP64 moments / entropy of F (and entropy production with Q).
+template <typename T, int D>
+__global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, const int64_t *cell_off,
+                                                      const int64_t *cell_N, int64_t ncells, int N_uniform,
+                                                      double h_uniform_times_N, double *out)
+{
+    __shared__ double red[8][kDiag];
+    for (int64_t c = blockIdx.x; c < ncells; c += gridDim.x) {
+        const int N = cell_N ? (int)cell_N[c] : N_uniform;
+        const int64_t cell = (D == 3) ? (int64_t)N * N * N : (int64_t)N * N;
+        const int64_t coff = cell_off ? cell_off[c] : c * cell;
+        const double h = h_uniform_times_N / N;
+        double s[kDiag];
+        for (int k = 0; k < kDiag; ++k) s[k] = 0.0;
+        double mn = 1e300, mq = 1e300;
+        for (int64_t i = threadIdx.x; i < cell; i += blockDim.x) {
+            const double f = (double)F[coff + i];
+            const int jx = (int)(i % N) - N / 2;
+            const int jy = (int)((i / N) % N) - N / 2;
+            const int jz = (D == 3) ? (int)(i / ((int64_t)N * N)) - N / 2 : 0;
+            s[0] += f;
+            if (D == 3) { s[1] += f * jz; s[2] += f * jy; s[3] += f * jx; }
+            else { s[1] += f * jy; s[2] += f * jx; }
+            s[4] += f * ((double)jx * jx + (double)jy * jy + (double)jz * jz);
+            if (f > 0) {
+                const double lf = log(f);
+                s[5] += f * lf;
+                if (Q) s[6] += (double)Q[coff + i] * lf;
+            }
+            mn = fmin(mn, f);
+            if (Q) mq = fmin(mq, (double)Q[coff + i]);
+        }
+        s[7] = mn;
+        s[9] = Q ? mq : 0.0;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int k = 0; k < kDiag; ++k) {
+            double v = s[k];
+            for (int sh = 16; sh > 0; sh >>= 1) {
+                const double u = __shfl_xor_sync(0xffffffffu, v, sh);
+                v = (k == 7 || k == 9) ? fmin(v, u) : v + u;
+            }
+            if (lane == 0) red[warp][k] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kDiag) {
+            const int k = threadIdx.x;
+            double v = red[0][k];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                v = (k == 7 || k == 9) ? fmin(v, red[w][k]) : v + red[w][k];
+            const double hd = (D == 3) ? h * h * h : h * h;
+            if (k == 0 || k == 5) v *= hd;
+            else if (k >= 1 && k <= 3) v *= hd * h;
+            else if (k == 4) v *= 0.5 * hd * h * h;
+            if (k == 8) v = 0.0;
+            if (D == 2 && k == 3) v = 0.0;
+            out[c * kDiag + k] = v;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace ef

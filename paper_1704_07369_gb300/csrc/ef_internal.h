@@ -1,0 +1,51 @@
+// ef_internal.h -- structures shared by the host plan code (ef_plan.cpp) and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+
+namespace ef {
+
+// One step of the per-cell direction loop.  Each op runs one inverse transform of the spectral
+// multiply M_dir(l) * Fhat(l) (Sec. 4.1, eq. fastAlg with the filter folded into M) and folds the
+// real-space result a(r) into the accumulators:
+//   OP_S_SET   S  = w a            OP_S_ADD  S += w a
+//   OP_G_SET   G  = a S            OP_G_ADD  G += a S
+//   OP_LOSS    nu = a;  Q = G - F nu   (the gain/loss split of Sec. 3.1.2, eq. def_A)
+enum OpKind : int { OP_S_SET = 0, OP_S_ADD = 1, OP_G_SET = 2, OP_G_ADD = 3, OP_LOSS = 4 };
+
+struct Op {
+    int dir;        // row of the multiplier table
+    int kind;       // OpKind
+    double w;       // weight (S ops)
+};
+
+enum OutMode : int { OUT_COLLIDE = 0, OUT_EULER = 1 };
+
+constexpr int kMaxOps = 512;
+constexpr int kDiag = 10;
+
+// Kernel arguments for one size class (all cells of one N).
+struct CollideArgs {
+    const void *F;            // input cells (element type Tr)
+    void *Q;                  // output cells (OUT_COLLIDE) or F itself (OUT_EULER, in place)
+    const int64_t *cell_off;  // device: element offset of each cell of the class (null: c * N^d)
+    const int64_t *cell_id;   // device: global cell index of each cell of the class (null: c)
+    int64_t ncells;           // cells in this class
+    const void *mult;         // device: multiplier tables [ndir][N1 * H][N]... see layout below
+    const Op *ops;            // device: op list
+    int nops;
+    int cluster;              // CTAs per cell
+    int planes;               // axis-0 planes per CTA = N / cluster
+    int sg_global;            // 1: S and G accumulators in global workspace, 0: shared memory
+    void *sg_ws;              // global S/G workspace (sg_global), [slot][2][planes*N1*(N+1)]
+    int out_mode;             // OutMode
+    double dt;                // Euler step
+    double h;                 // grid spacing 2L/N
+    double *diag;             // nullable: [cell_id][kDiag]
+    int *status;              // device status word
+};
+
+// Multiplier table layout for one class: mult[dir][lz][p], p = ly * H + lx (3D) or p = lx (2D),
+// H = N/2 + 1, lz in [0, N) in FFT order; the loss table is the last dir.
+
+}  // namespace ef

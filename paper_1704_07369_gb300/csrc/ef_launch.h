@@ -1,0 +1,34 @@
+// ef_launch.h -- per-(precision, dimension) kernel entry points defined in the ef_collide_*.cu
+// translation units, called by the host plan code.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "ef_internal.h"
+
+namespace ef {
+
+#define EF_DECLARE_VARIANT(SUF)                                                                      \
+    bool collide_supported_##SUF(int N);                                                             \
+    size_t collide_smem_##SUF(int N, int planes, int sg_global);                                     \
+    cudaError_t collide_setup_##SUF(int N, size_t smem, int cluster, int tpb, int *max_clusters);    \
+    cudaError_t collide_launch_##SUF(int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, \
+                                     cudaStream_t s);
+
+EF_DECLARE_VARIANT(f32_2d)
+EF_DECLARE_VARIANT(f32_3d)
+EF_DECLARE_VARIANT(f64_2d)
+EF_DECLARE_VARIANT(f64_3d)
+
+#undef EF_DECLARE_VARIANT
+
+// moments / entropy (ef_moments.cu)
+cudaError_t moments_launch(int prec, int d, const void *F, const void *Q, const int64_t *cell_off,
+                           const int64_t *cell_N, int64_t ncells, int N_uniform, double twoL, double *out,
+                           cudaStream_t s);
+
+constexpr int kMaxThreadsHost = 320;
+
+}  // namespace ef

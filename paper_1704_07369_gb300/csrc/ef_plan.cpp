@@ -1,0 +1,834 @@
+// ef_plan.cpp -- host side of the C ABI in include/ef.h: plan construction (filter, angular
+// quadrature, radial kernel factors, multiplier tables, op lists), cluster / block shape choice,
+// argument checks and kernel launches.
+//
+// The multiplier table of spectral direction u holds M_u(l) = sigma_N(l) Phi_u(l . e_u) for every
+// mode l of the half spectrum (FP64 on the host, stored in the plan's precision), where Phi_u is
+// the radial factor of the low-rank kernel decomposition (Sec. 4.1, eq. fastAlg):
+//   2D Maxwell      psi_R(x) = 2 R sinc(pi R x / T)                        (eq. discrete_hatB)
+//   3D hard sphere  phi(x)   = R^2 [2 sinc(pi R x/T) - sinc^2(pi R x/(2T))]
+//   3D Maxwell      phi_j(x) = 2 int_0^R rho exp(-u_j^2 rho^2) cos(pi rho x / T) d rho
+// The gain is sum over pairs (u, u*) of w a_u a_u*, a_u = IFFT(M_u Fhat); the loss table is
+// L(m) = sum_pairs w M_u(m) M_u*(m) = sigma(m)^2 B_fast(m, m) (eq. def_A).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ef.h"
+#include "ef_internal.h"
+#include "ef_launch.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ef_status fail(ef_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+ef_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;
+}
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------------- plan math ---------------
+
+// Modified Jackson filter (eq. JacksonFilter2) with n = N/2 for even N; sigma(-N/2) = 0 (Sec. 4.1).
+double jackson(int N, int k, bool enabled)
+{
+    if (k == -N / 2) return 0.0;
+    if (!enabled) return 1.0;
+    const int n = N / 2;
+    const int b = std::abs(k);
+    if (b >= n) return 0.0;
+    const double np1 = n + 1.0;
+    const double t = kPi * b / np1, c = kPi / np1;
+    return ((np1 - b) * std::cos(t) + std::sin(t) * std::cos(c) / std::sin(c)) / np1;
+}
+
+double sinc(double y) { return std::fabs(y) < 1e-8 ? 1.0 - y * y / 6.0 : std::sin(y) / y; }
+
+// Gauss-Legendre nodes / weights on [-1, 1] (Newton on the three-term recurrence).
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int k = 2; k <= n; ++k) {
+            const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+template <class Fn>
+void parallel_for(int64_t n, Fn fn)
+{
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 4096) nt = 1;
+    std::atomic<int64_t> next(0);
+    auto worker = [&]() {
+        for (;;) {
+            const int64_t b = next.fetch_add(1024);
+            if (b >= n) break;
+            const int64_t e = std::min(n, b + 1024);
+            for (int64_t i = b; i < e; ++i) fn(i);
+        }
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; ++t) th.emplace_back(worker);
+    worker();
+    for (auto &t : th) t.join();
+}
+
+// Radial profile of one direction.
+struct Profile {
+    int type;        // 0: 2D psi, 1: 3D hard sphere phi, 2: 3D Maxwell Gaussian-damped phi
+    double u;        // Gaussian rate (type 2)
+};
+
+struct Dir {
+    double e[3];
+    Profile prof;
+};
+
+struct Pair {
+    int de, ds;      // gain term w * a_de * a_ds
+    double w;
+};
+
+struct Desc {
+    int d, N, R, nmu, nphi, nc, J, sigma;
+    double L, T, Rtr;
+    ef_kernel kernel;
+    ef_precision prec;
+};
+
+// Directions and gain pairs of the low-rank kernel (independent of N).
+void build_directions(const Desc &ds, std::vector<Dir> &dirs, std::vector<Pair> &pairs)
+{
+    dirs.clear();
+    pairs.clear();
+    if (ds.d == 2) {
+        // theta_t = t pi / R over [0, pi); e_t^perp = e_{t + R/2}; weight (1/pi)(pi/R) per term,
+        // each unordered pair appearing twice in sum_t.
+        for (int t = 0; t < ds.R; ++t) {
+            const double th = kPi * t / ds.R;
+            dirs.push_back(Dir{{std::cos(th), std::sin(th), 0.0}, Profile{0, 0.0}});
+        }
+        for (int t = 0; t < ds.R / 2; ++t) pairs.push_back(Pair{t, t + ds.R / 2, 2.0 / ds.R});
+        return;
+    }
+    // 3D: e on the half sphere (Gauss-Legendre in mu = cos(polar) on [0,1], uniform azimuth),
+    // e* on the half circle orthogonal to e; weight (1/pi) w_mu (2 pi / n_phi) (pi / n_c).
+    std::vector<double> gx, gw;
+    gauss_legendre(ds.nmu, gx, gw);
+    std::vector<double> uj, cj;
+    if (ds.kernel == EF_KERNEL_MAXWELL) {
+        // 1/sqrt(s) = (2/sqrt(pi)) int_0^inf exp(-u^2 s) du; u = exp(tau), tau in
+        // [ln(0.4/R), ln(35/R)] by (J-1)-point Gauss-Legendre, plus one u = 0 term for the rest.
+        const int n = ds.J - 1;
+        std::vector<double> tx, tw;
+        if (n > 0) gauss_legendre(n, tx, tw);
+        const double ta = std::log(0.4 / ds.Rtr), tb = std::log(35.0 / ds.Rtr);
+        uj.push_back(0.0);
+        cj.push_back(2.0 / std::sqrt(kPi) * std::exp(ta));
+        for (int j = 0; j < n; ++j) {
+            const double tau = ta + 0.5 * (tx[j] + 1.0) * (tb - ta);
+            uj.push_back(std::exp(tau));
+            cj.push_back(2.0 / std::sqrt(kPi) * 0.5 * (tb - ta) * tw[j] * std::exp(tau));
+        }
+    } else {
+        uj.push_back(0.0);
+        cj.push_back(1.0);
+    }
+    for (size_t j = 0; j < uj.size(); ++j) {
+        const Profile pr{ds.kernel == EF_KERNEL_MAXWELL ? 2 : 1, uj[j]};
+        for (int a = 0; a < ds.nmu; ++a) {
+            const double mu = 0.5 * (gx[a] + 1.0), wmu = 0.5 * gw[a];
+            const double st = std::sqrt(1.0 - mu * mu);
+            for (int b = 0; b < ds.nphi; ++b) {
+                const double al = 2.0 * kPi * b / ds.nphi;
+                const double ev[3] = {st * std::cos(al), st * std::sin(al), mu};
+                const double uv[3] = {mu * std::cos(al), mu * std::sin(al), -st};
+                const double vv[3] = {-std::sin(al), std::cos(al), 0.0};
+                const int de = (int)dirs.size();
+                dirs.push_back(Dir{{ev[0], ev[1], ev[2]}, pr});
+                for (int c = 0; c < ds.nc; ++c) {
+                    const double ph = kPi * c / ds.nc;
+                    Dir es{{std::cos(ph) * uv[0] + std::sin(ph) * vv[0], std::cos(ph) * uv[1] + std::sin(ph) * vv[1],
+                            std::cos(ph) * uv[2] + std::sin(ph) * vv[2]},
+                           pr};
+                    const int dsi = (int)dirs.size();
+                    dirs.push_back(es);
+                    const double w = (1.0 / kPi) * wmu * (2.0 * kPi / ds.nphi) * (kPi / ds.nc) * cj[j];
+                    pairs.push_back(Pair{de, dsi, w});
+                }
+            }
+        }
+    }
+}
+
+// radial factor Phi(x), x = l . e
+struct RadialEval {
+    double T, Rtr;
+    std::vector<double> rho, wr;   // composite Gauss-Legendre on [0, R]: 16 panels x 8 nodes
+    RadialEval(double T_, double R_) : T(T_), Rtr(R_)
+    {
+        std::vector<double> gx, gw;
+        gauss_legendre(8, gx, gw);
+        const double hp = Rtr / 16.0;
+        for (int p = 0; p < 16; ++p)
+            for (int i = 0; i < 8; ++i) {
+                rho.push_back(hp * (p + 0.5 * (gx[i] + 1.0)));
+                wr.push_back(0.5 * hp * gw[i]);
+            }
+    }
+    double operator()(const Profile &pr, double x) const
+    {
+        if (pr.type == 0) return 2.0 * Rtr * sinc(kPi * Rtr * x / T);
+        if (pr.type == 1) {
+            const double a = kPi * x / T, s2 = sinc(0.5 * a * Rtr);
+            return Rtr * Rtr * (2.0 * sinc(a * Rtr) - s2 * s2);
+        }
+        const double a = kPi * x / T;
+        double acc = 0.0;
+        for (size_t i = 0; i < rho.size(); ++i)
+            acc += wr[i] * rho[i] * std::exp(-pr.u * pr.u * rho[i] * rho[i]) * std::cos(a * rho[i]);
+        return 2.0 * acc;
+    }
+};
+
+int mode_of(int N, int i) { return i < N / 2 ? i : i - N; }
+
+// ---------------------------------------------------------------- plan objects -------------
+
+struct ClassPlan {
+    int N = 0;
+    int64_t ncells = 0;                 // batched: cells of this size; uniform plan: 0
+    int cluster = 1, tpb = 32, planes = 0, sg_global = 0;
+    size_t smem = 0;
+    int max_clusters = 0;
+    int ndir = 0, nops = 0;
+    void *d_mult = nullptr;
+    ef::Op *d_ops = nullptr;
+    int64_t *d_cell_off = nullptr, *d_cell_id = nullptr;
+    void *d_sg = nullptr;
+    int64_t sg_slots = 0;
+};
+
+}  // namespace
+
+struct ef_plan_s {
+    Desc desc;
+    int device = 0;
+    bool batched = false;
+    int64_t ncells = 0;
+    std::vector<ClassPlan> classes;
+    int64_t *d_all_off = nullptr, *d_all_N = nullptr;
+    int *d_status = nullptr;
+    int h_status = 0;
+    bool use_graph = false;
+    // graph cache: one captured step per (mode, F, Q, ncells, dt, diag, stream)
+    cudaGraphExec_t gexec = nullptr;
+    const void *g_F = nullptr;
+    void *g_Q = nullptr;
+    int64_t g_n = -1;
+    int g_mode = -1;
+    double g_dt = 0.0;
+    double *g_diag = nullptr;
+    cudaStream_t g_stream = nullptr;
+};
+
+namespace {
+
+bool size_built(int prec, int d, int N)
+{
+    if (prec == EF_PREC_F32) return d == 3 ? ef::collide_supported_f32_3d(N) : ef::collide_supported_f32_2d(N);
+    return d == 3 ? ef::collide_supported_f64_3d(N) : ef::collide_supported_f64_2d(N);
+}
+
+size_t smem_for(int prec, int d, int N, int planes, int sg)
+{
+    if (prec == EF_PREC_F32) return d == 3 ? ef::collide_smem_f32_3d(N, planes, sg) : ef::collide_smem_f32_2d(N, planes, sg);
+    return d == 3 ? ef::collide_smem_f64_3d(N, planes, sg) : ef::collide_smem_f64_2d(N, planes, sg);
+}
+
+cudaError_t setup_for(int prec, int d, int N, size_t smem, int cl, int tpb, int *mc)
+{
+    if (prec == EF_PREC_F32)
+        return d == 3 ? ef::collide_setup_f32_3d(N, smem, cl, tpb, mc) : ef::collide_setup_f32_2d(N, smem, cl, tpb, mc);
+    return d == 3 ? ef::collide_setup_f64_3d(N, smem, cl, tpb, mc) : ef::collide_setup_f64_2d(N, smem, cl, tpb, mc);
+}
+
+cudaError_t launch_for(int prec, int d, int N, const ef::CollideArgs &a, int grid, int tpb, size_t smem, cudaStream_t s)
+{
+    if (prec == EF_PREC_F32)
+        return d == 3 ? ef::collide_launch_f32_3d(N, a, grid, tpb, smem, s) : ef::collide_launch_f32_2d(N, a, grid, tpb, smem, s);
+    return d == 3 ? ef::collide_launch_f64_3d(N, a, grid, tpb, smem, s) : ef::collide_launch_f64_2d(N, a, grid, tpb, smem, s);
+}
+
+// Choose the cluster size / block shape for one N: the smallest cluster whose CTAs hold their
+// slab and (if possible) the S/G accumulators in shared memory, with one pencil per thread.
+ef_status choose_shape(const Desc &ds, ClassPlan &cp)
+{
+    const int N = cp.N, d = ds.d;
+    const int H = N / 2 + 1, N1 = d == 3 ? N : 1, NP = N1 * H;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int smem_max = 0;
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int cands[] = {1, 2, 4, 8, 16};
+    std::string why;
+    for (int sg = 0; sg <= 1; ++sg) {
+        for (int C : cands) {
+            if (N % C) continue;
+            const int planes = N / C;
+            const int rows = planes * N1;
+            if (rows % 2) continue;
+            int need = std::max({(NP + C - 1) / C, rows / 2, d == 3 ? planes * H : 1});
+            int tpb = std::max(64, (need + 31) / 32 * 32);
+            if (tpb > ef::kMaxThreadsHost) continue;
+            if ((int64_t)C * tpb < NP) continue;
+            const size_t smem = smem_for(ds.prec, d, N, planes, sg);
+            if ((long)smem > smem_max) continue;
+            int mc = 0;
+            cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, &mc);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                why = cudaGetErrorString(e);
+                continue;
+            }
+            if (mc <= 0) continue;
+            cp.cluster = C;
+            cp.tpb = tpb;
+            cp.planes = planes;
+            cp.sg_global = sg;
+            cp.smem = smem;
+            cp.max_clusters = mc;
+            return EF_OK;
+        }
+    }
+    return fail(EF_ERR_UNSUPPORTED, "no launch shape fits N=" + std::to_string(N) + " on this device " + why);
+}
+
+template <typename T>
+void *upload_table(const std::vector<double> &h, cudaError_t &err)
+{
+    std::vector<T> t(h.size());
+    for (size_t i = 0; i < h.size(); ++i) t[i] = (T)h[i];
+    void *p = nullptr;
+    err = cudaMalloc(&p, t.size() * sizeof(T));
+    if (err != cudaSuccess) return nullptr;
+    err = cudaMemcpy(p, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return p;
+}
+
+ef_status build_class(const Desc &ds, ClassPlan &cp)
+{
+    const int N = cp.N, d = ds.d;
+    const int H = N / 2 + 1, N1 = d == 3 ? N : 1, NP = N1 * H;
+    std::vector<Dir> dirs;
+    std::vector<Pair> pairs;
+    build_directions(ds, dirs, pairs);
+    const int ndir = (int)dirs.size();
+    const int64_t per = (int64_t)N * NP;
+    std::vector<double> tab((size_t)(ndir + 1) * per, 0.0);
+    std::vector<double> sig1(N);
+    for (int i = 0; i < N; ++i) sig1[i] = jackson(N, mode_of(N, i), ds.sigma != 0);
+    RadialEval rad(ds.T, ds.Rtr);
+    parallel_for((int64_t)ndir * per, [&](int64_t idx) {
+        const int u = (int)(idx / per);
+        const int64_t i = idx % per;
+        const int lz = (int)(i / NP), p = (int)(i % NP);
+        int k[3] = {mode_of(N, lz), 0, 0};
+        double s = sig1[lz];
+        if (d == 3) {
+            const int ly = p / H, lx = p % H;
+            k[1] = mode_of(N, ly);
+            k[2] = lx < N / 2 ? lx : lx - N;
+            s *= sig1[ly] * sig1[lx < N / 2 ? lx : N / 2];
+        } else {
+            const int lx = p;
+            k[1] = lx < N / 2 ? lx : lx - N;
+            s *= sig1[lx < N / 2 ? lx : N / 2];
+        }
+        double val = 0.0;
+        if (s != 0.0) {
+            const Dir &D0 = dirs[u];
+            const double x = k[0] * D0.e[0] + k[1] * D0.e[1] + k[2] * D0.e[2];
+            val = s * rad(D0.prof, x);
+        }
+        tab[(size_t)u * per + i] = val;
+    });
+    double *loss = &tab[(size_t)ndir * per];
+    for (const Pair &pr : pairs)
+        for (int64_t i = 0; i < per; ++i) loss[i] += pr.w * tab[(size_t)pr.de * per + i] * tab[(size_t)pr.ds * per + i];
+
+    // op list: for each gain direction e, accumulate S = sum w a_e* then G (+)= a_e S
+    std::vector<ef::Op> ops;
+    std::map<int, std::vector<const Pair *>> groups;
+    std::vector<int> order;
+    for (const Pair &pr : pairs) {
+        if (!groups.count(pr.de)) order.push_back(pr.de);
+        groups[pr.de].push_back(&pr);
+    }
+    bool first_g = true;
+    for (int de : order) {
+        bool first_s = true;
+        for (const Pair *pr : groups[de]) {
+            ops.push_back(ef::Op{pr->ds, first_s ? ef::OP_S_SET : ef::OP_S_ADD, pr->w});
+            first_s = false;
+        }
+        ops.push_back(ef::Op{de, first_g ? ef::OP_G_SET : ef::OP_G_ADD, 1.0});
+        first_g = false;
+    }
+    ops.push_back(ef::Op{ndir, ef::OP_LOSS, 1.0});
+    if ((int)ops.size() > ef::kMaxOps) return fail(EF_ERR_UNSUPPORTED, "too many spectral directions");
+    cp.ndir = ndir + 1;
+    cp.nops = (int)ops.size();
+
+    cudaError_t e = cudaSuccess;
+    cp.d_mult = ds.prec == EF_PREC_F32 ? upload_table<float>(tab, e) : upload_table<double>(tab, e);
+    if (e != cudaSuccess) return cuda_fail(e, "multiplier table");
+    e = cudaMalloc((void **)&cp.d_ops, ops.size() * sizeof(ef::Op));
+    if (e != cudaSuccess) return cuda_fail(e, "op list");
+    e = cudaMemcpy(cp.d_ops, ops.data(), ops.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "op list copy");
+    return choose_shape(ds, cp);
+}
+
+ef_status ensure_sg(ef_plan_s *p, ClassPlan &cp, int grid_clusters)
+{
+    if (!cp.sg_global) return EF_OK;
+    const int N = cp.N, N1 = p->desc.d == 3 ? N : 1;
+    const int64_t rows = (int64_t)cp.planes * N1;
+    const int64_t slots = (int64_t)grid_clusters * cp.cluster;
+    if (slots <= cp.sg_slots) return EF_OK;
+    if (cp.d_sg) cudaFree(cp.d_sg);
+    const size_t el = p->desc.prec == EF_PREC_F32 ? 4 : 8;
+    cudaError_t e = cudaMalloc(&cp.d_sg, (size_t)slots * 2 * rows * (N + 1) * el);
+    if (e != cudaSuccess) { cp.d_sg = nullptr; cp.sg_slots = 0; return cuda_fail(e, "S/G workspace"); }
+    cp.sg_slots = slots;
+    return EF_OK;
+}
+
+void destroy_plan(ef_plan_s *p)
+{
+    if (!p) return;
+    for (ClassPlan &cp : p->classes) {
+        cudaFree(cp.d_mult);
+        cudaFree(cp.d_ops);
+        cudaFree(cp.d_cell_off);
+        cudaFree(cp.d_cell_id);
+        cudaFree(cp.d_sg);
+    }
+    cudaFree(p->d_all_off);
+    cudaFree(p->d_all_N);
+    cudaFree(p->d_status);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    delete p;
+}
+
+ef_status fill_desc(const ef_plan_desc *in, Desc &ds)
+{
+    if (!in) return fail(EF_ERR_INVALID_ARG, "null plan description");
+    ds.d = in->d;
+    ds.N = in->N;
+    ds.L = in->L;
+    ds.kernel = in->kernel;
+    ds.R = in->R;
+    ds.prec = in->prec;
+    if (ds.d != 2 && ds.d != 3) return fail(EF_ERR_INVALID_ARG, "d must be 2 or 3");
+    if (!(ds.L > 0.0) || !std::isfinite(ds.L)) return fail(EF_ERR_INVALID_ARG, "L must be positive");
+    if (ds.prec != EF_PREC_F32 && ds.prec != EF_PREC_F64) return fail(EF_ERR_INVALID_ARG, "bad precision");
+    if (ds.kernel != EF_KERNEL_MAXWELL && ds.kernel != EF_KERNEL_HARD_SPHERE) return fail(EF_ERR_INVALID_ARG, "bad kernel");
+    if (ds.d == 2 && ds.kernel != EF_KERNEL_MAXWELL) return fail(EF_ERR_UNSUPPORTED, "2D supports Maxwell molecules only");
+    ds.T = ds.L;
+    ds.Rtr = in->R_tr > 0 ? in->R_tr : 4.0 * ds.L / (3.0 * std::sqrt(2.0) + 1.0);
+    ds.sigma = in->sigma_enabled < 0 ? 1 : (in->sigma_enabled ? 1 : 0);
+    ds.J = in->J > 0 ? in->J : 6;
+    if (ds.d == 2) {
+        if (ds.R < 2 || ds.R % 2) return fail(EF_ERR_INVALID_ARG, "2D needs an even R >= 2");
+        ds.nmu = ds.nphi = ds.nc = 0;
+    } else {
+        if (in->n_mu > 0 && in->n_phi > 0 && in->n_c > 0) {
+            ds.nmu = in->n_mu;
+            ds.nphi = in->n_phi;
+            ds.nc = in->n_c;
+        } else {
+            switch (ds.R) {
+            case 8: ds.nmu = 1; ds.nphi = 2; ds.nc = 2; break;
+            case 16: ds.nmu = 1; ds.nphi = 4; ds.nc = 2; break;
+            case 32: ds.nmu = 2; ds.nphi = 4; ds.nc = 2; break;
+            case 64: ds.nmu = 2; ds.nphi = 4; ds.nc = 4; break;
+            case 128: ds.nmu = 4; ds.nphi = 4; ds.nc = 4; break;
+            default: return fail(EF_ERR_UNSUPPORTED, "no default angular quadrature for this R; set n_mu, n_phi, n_c");
+            }
+        }
+        if (2 * ds.nmu * ds.nphi * ds.nc != ds.R) return fail(EF_ERR_INVALID_ARG, "R must equal 2 n_mu n_phi n_c");
+    }
+    return EF_OK;
+}
+
+ef_status check_N(const Desc &ds, int N)
+{
+    if (N < 8 || N % 2) return fail(EF_ERR_INVALID_ARG, "N must be even and >= 8");
+    if (!size_built(ds.prec, ds.d, N)) return fail(EF_ERR_UNSUPPORTED, "N=" + std::to_string(N) + " is not a built size");
+    return EF_OK;
+}
+
+ef_status check_device(const ef_plan_s *p)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != p->device) return fail(EF_ERR_INVALID_ARG, "the plan's device is not current");
+    return EF_OK;
+}
+
+ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, double dt, double *diag,
+              cudaStream_t s)
+{
+    const Desc &ds = p->desc;
+    for (ClassPlan &cp : p->classes) {
+        const int64_t n = p->batched ? cp.ncells : ncells;
+        if (n <= 0) continue;
+        const int grid = (int)std::min<int64_t>(n, cp.max_clusters);
+        ef_status st = ensure_sg(p, cp, grid);
+        if (st != EF_OK) return st;
+        ef::CollideArgs a{};
+        a.F = F;
+        a.Q = Out;
+        a.cell_off = cp.d_cell_off;
+        a.cell_id = cp.d_cell_id;
+        a.ncells = n;
+        a.mult = cp.d_mult;
+        a.ops = cp.d_ops;
+        a.nops = cp.nops;
+        a.cluster = cp.cluster;
+        a.planes = cp.planes;
+        a.sg_global = cp.sg_global;
+        a.sg_ws = cp.d_sg;
+        a.out_mode = mode;
+        a.dt = dt;
+        a.h = 2.0 * ds.L / cp.N;
+        a.diag = diag;
+        a.status = p->d_status;
+        cudaError_t e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, s);
+        if (e != cudaSuccess) return cuda_fail(e, "collide launch");
+    }
+    return EF_OK;
+}
+
+ef_status finish_plan(ef_plan_s *p)
+{
+    cudaError_t e = cudaMalloc((void **)&p->d_status, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "status word");
+    e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "status word");
+    for (ClassPlan &cp : p->classes) {
+        ef_status st = build_class(p->desc, cp);
+        if (st != EF_OK) return st;
+    }
+    return EF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ef_status_string(ef_status s)
+{
+    switch (s) {
+    case EF_OK: return "EF_OK";
+    case EF_ERR_INVALID_ARG: return "EF_ERR_INVALID_ARG";
+    case EF_ERR_UNSUPPORTED: return "EF_ERR_UNSUPPORTED";
+    case EF_ERR_CUDA: return "EF_ERR_CUDA";
+    case EF_ERR_OOM: return "EF_ERR_OOM";
+    case EF_ERR_TIMEOUT: return "EF_ERR_TIMEOUT";
+    case EF_ERR_POSITIVITY: return "EF_ERR_POSITIVITY";
+    case EF_ERR_NOT_FINITE: return "EF_ERR_NOT_FINITE";
+    }
+    return "EF_UNKNOWN_STATUS";
+}
+
+const char *ef_last_error(void) { return g_last_error.c_str(); }
+
+ef_status ef_plan_create_ex(const ef_plan_desc *desc, ef_plan_t *out)
+{
+    if (!out) return fail(EF_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    Desc ds;
+    ef_status st = fill_desc(desc, ds);
+    if (st != EF_OK) return st;
+    st = check_N(ds, desc->N);
+    if (st != EF_OK) return st;
+    ef_plan_s *p = new ef_plan_s();
+    p->desc = ds;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    ClassPlan cp;
+    cp.N = ds.N;
+    p->classes.push_back(cp);
+    st = finish_plan(p);
+    if (st != EF_OK) { destroy_plan(p); return st; }
+    *out = p;
+    return EF_OK;
+}
+
+ef_status ef_plan_create(int d, int N, double L, ef_kernel kernel, int R, ef_precision prec, ef_plan_t *out)
+{
+    ef_plan_desc desc;
+    std::memset(&desc, 0, sizeof(desc));
+    desc.d = d;
+    desc.N = N;
+    desc.L = L;
+    desc.kernel = kernel;
+    desc.R = R;
+    desc.prec = prec;
+    desc.sigma_enabled = -1;
+    return ef_plan_create_ex(&desc, out);
+}
+
+ef_status ef_plan_create_batched(int d, int64_t ncells, const int *N_host, double L, ef_kernel kernel, int R,
+                                 ef_precision prec, ef_plan_t *out)
+{
+    if (!out) return fail(EF_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    if (ncells <= 0 || !N_host) return fail(EF_ERR_INVALID_ARG, "batched plan needs ncells > 0 and N_host");
+    ef_plan_desc desc;
+    std::memset(&desc, 0, sizeof(desc));
+    desc.d = d;
+    desc.N = N_host[0];
+    desc.L = L;
+    desc.kernel = kernel;
+    desc.R = R;
+    desc.prec = prec;
+    desc.sigma_enabled = -1;
+    Desc ds;
+    ef_status st = fill_desc(&desc, ds);
+    if (st != EF_OK) return st;
+    std::map<int, std::vector<int64_t>> byN;
+    std::vector<int64_t> off(ncells), Ns(ncells);
+    int64_t acc = 0;
+    for (int64_t c = 0; c < ncells; ++c) {
+        st = check_N(ds, N_host[c]);
+        if (st != EF_OK) return st;
+        off[c] = acc;
+        Ns[c] = N_host[c];
+        acc += d == 3 ? (int64_t)N_host[c] * N_host[c] * N_host[c] : (int64_t)N_host[c] * N_host[c];
+        byN[N_host[c]].push_back(c);
+    }
+    ef_plan_s *p = new ef_plan_s();
+    p->desc = ds;
+    p->batched = true;
+    p->ncells = ncells;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    // largest cells first: their launches go first, smaller ones fill in behind
+    for (auto it = byN.rbegin(); it != byN.rend(); ++it) {
+        ClassPlan cp;
+        cp.N = it->first;
+        cp.ncells = (int64_t)it->second.size();
+        std::vector<int64_t> co(cp.ncells), ci(cp.ncells);
+        for (int64_t i = 0; i < cp.ncells; ++i) {
+            ci[i] = it->second[i];
+            co[i] = off[ci[i]];
+        }
+        e = cudaMalloc((void **)&cp.d_cell_off, cp.ncells * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&cp.d_cell_id, cp.ncells * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMemcpy(cp.d_cell_off, co.data(), cp.ncells * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(cp.d_cell_id, ci.data(), cp.ncells * sizeof(int64_t), cudaMemcpyHostToDevice);
+        p->classes.push_back(cp);
+        if (e != cudaSuccess) { destroy_plan(p); return cuda_fail(e, "cell tables"); }
+    }
+    e = cudaMalloc((void **)&p->d_all_off, ncells * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_all_N, ncells * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_all_off, off.data(), ncells * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_all_N, Ns.data(), ncells * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { destroy_plan(p); return cuda_fail(e, "cell tables"); }
+    st = finish_plan(p);
+    if (st != EF_OK) { destroy_plan(p); return st; }
+    *out = p;
+    return EF_OK;
+}
+
+ef_status ef_plan_destroy(ef_plan_t plan)
+{
+    if (!plan) return fail(EF_ERR_INVALID_ARG, "null plan");
+    destroy_plan(plan);
+    return EF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One step (all size classes) either launched directly or through the plan's cached CUDA graph.
+ef_status step(ef_plan_s *p, const void *F, void *Q, int64_t ncells, int mode, double dt, double *diag, cudaStream_t s)
+{
+    if (!(p->use_graph && s != nullptr)) return run(p, F, Q, ncells, mode, dt, diag, s);
+    const bool hit = p->gexec && p->g_F == F && p->g_Q == Q && p->g_n == ncells && p->g_stream == s &&
+                     p->g_mode == mode && p->g_dt == dt && p->g_diag == diag;
+    if (!hit) {
+        if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
+        ef_status st;
+        // shapes and workspaces are settled outside the capture
+        for (ClassPlan &cp : p->classes) {
+            const int64_t n = p->batched ? cp.ncells : ncells;
+            if (n > 0) {
+                st = ensure_sg(p, cp, (int)std::min<int64_t>(n, cp.max_clusters));
+                if (st != EF_OK) return st;
+            }
+        }
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        st = run(p, F, Q, ncells, mode, dt, diag, s);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(s, &g);
+        if (st != EF_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        e = cudaGraphInstantiate(&p->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { p->gexec = nullptr; return cuda_fail(e, "graph instantiate"); }
+        p->g_F = F;
+        p->g_Q = Q;
+        p->g_n = ncells;
+        p->g_stream = s;
+        p->g_mode = mode;
+        p->g_dt = dt;
+        p->g_diag = diag;
+    }
+    cudaError_t e = cudaGraphLaunch(p->gexec, s);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return EF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ef_status ef_collide(ef_plan_t p, const void *F, void *Q, int64_t ncells, ef_stream_t stream)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (ncells < 0) return fail(EF_ERR_INVALID_ARG, "ncells < 0");
+    if (p->batched && ncells != p->ncells) return fail(EF_ERR_INVALID_ARG, "ncells differs from the batched plan");
+    if (ncells == 0) return EF_OK;
+    if (!F || !Q) return fail(EF_ERR_INVALID_ARG, "null F or Q");
+    if (F == Q) return fail(EF_ERR_INVALID_ARG, "F and Q must not overlap");
+    ef_status st = check_device(p);
+    if (st != EF_OK) return st;
+    return step(p, F, Q, ncells, ef::OUT_COLLIDE, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+ef_status ef_euler_step(ef_plan_t p, void *F, double dt, int nsteps, double *diag, int64_t ncells, ef_stream_t stream)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (nsteps < 0 || ncells < 0) return fail(EF_ERR_INVALID_ARG, "negative nsteps or ncells");
+    if (!std::isfinite(dt)) return fail(EF_ERR_INVALID_ARG, "dt must be finite");
+    if (p->batched && ncells != p->ncells) return fail(EF_ERR_INVALID_ARG, "ncells differs from the batched plan");
+    if (nsteps == 0 || ncells == 0) return EF_OK;
+    if (!F) return fail(EF_ERR_INVALID_ARG, "null F");
+    ef_status st = check_device(p);
+    if (st != EF_OK) return st;
+    for (int k = 0; k < nsteps; ++k) {
+        st = step(p, F, F, ncells, ef::OUT_EULER, dt, diag ? diag + (int64_t)k * ncells * ef::kDiag : nullptr,
+                  (cudaStream_t)stream);
+        if (st != EF_OK) return st;
+    }
+    return EF_OK;
+}
+
+ef_status ef_moments_entropy(ef_plan_t p, const void *F, const void *Q, double *out, int64_t ncells, ef_stream_t stream)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (ncells < 0) return fail(EF_ERR_INVALID_ARG, "ncells < 0");
+    if (p->batched && ncells != p->ncells) return fail(EF_ERR_INVALID_ARG, "ncells differs from the batched plan");
+    if (ncells == 0) return EF_OK;
+    if (!F || !out) return fail(EF_ERR_INVALID_ARG, "null F or out");
+    ef_status st = check_device(p);
+    if (st != EF_OK) return st;
+    cudaError_t e = ef::moments_launch(p->desc.prec == EF_PREC_F32 ? 0 : 1, p->desc.d, F, Q, p->d_all_off, p->d_all_N,
+                                       ncells, p->desc.N, 2.0 * p->desc.L, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+    return EF_OK;
+}
+
+ef_status ef_plan_status(ef_plan_t p, int sync, int reset)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (sync) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "device synchronize");
+        e = cudaMemcpy(&p->h_status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "status read");
+        if (reset) {
+            e = cudaMemset(p->d_status, 0, sizeof(int));
+            if (e != cudaSuccess) return cuda_fail(e, "status reset");
+        }
+    }
+    const int s = p->h_status;
+    if (reset) p->h_status = 0;
+    return (ef_status)s;
+}
+
+ef_status ef_plan_set_graph(ef_plan_t p, int enable)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    p->use_graph = enable != 0;
+    if (!p->use_graph && p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+    }
+    return EF_OK;
+}
+
+ef_status ef_plan_info(ef_plan_t p, int64_t info[8])
+{
+    if (!p || !info) return fail(EF_ERR_INVALID_ARG, "null plan or info");
+    info[0] = p->desc.d;
+    info[1] = (int64_t)p->classes.size();
+    info[2] = p->classes.empty() ? 0 : p->classes[0].ndir;
+    info[3] = p->classes.empty() ? 0 : p->classes[0].cluster;
+    info[4] = p->classes.empty() ? 0 : p->classes[0].tpb;
+    info[5] = p->batched ? p->ncells : 0;
+    info[6] = p->desc.prec;
+    info[7] = (int64_t)p->classes.size();
+    return EF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every function that
+include/ef.h declares; argument checks that need no device return the documented codes."""
+import ctypes
+import os
+import re
+
+import paper_1704_07369_gb300 as ef
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ef.h")) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(ef_[a-z_]+)\s*\(", src))
+
+
+def test_library_exports_every_declared_symbol():
+    ef.build()
+    lib = ef.lib()
+    names = _declared()
+    assert names == set(ef.SYMBOLS)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_host_side_argument_checks():
+    lib = ef.lib()
+    h = ctypes.c_void_p()
+    assert lib.ef_plan_create(4, 16, 8.0, 0, 16, 0, ctypes.byref(h)) == ef.EF_ERR_INVALID_ARG
+    assert b"d must be" in lib.ef_last_error()
+    assert lib.ef_plan_create(3, 16, -1.0, 1, 32, 0, ctypes.byref(h)) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_plan_create(2, 16, 8.0, 1, 16, 0, ctypes.byref(h)) == ef.EF_ERR_UNSUPPORTED
+    assert lib.ef_plan_create(2, 16, 8.0, 0, 15, 0, ctypes.byref(h)) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_plan_create(3, 16, 8.0, 1, 30, 0, ctypes.byref(h)) == ef.EF_ERR_UNSUPPORTED
+    assert lib.ef_plan_create(3, 16, 8.0, 1, 32, 0, None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_collide(None, None, None, 1, None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_plan_destroy(None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_status_string(ef.EF_ERR_POSITIVITY) == b"EF_ERR_POSITIVITY"
+
+
+def test_oracle_is_not_on_the_product_path():
+    """The package never imports the oracle (only tests, smoke and the bench's CPU legs do)."""
+    pkg = os.path.join(ROOT, "paper_1704_07369_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".cpp", ".h", ".inc")):
+                with open(os.path.join(dirpath, fn)) as f:
+                    src = f.read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), fn
+                assert "ef_oracle" not in src and "liboracle" not in src, fn
