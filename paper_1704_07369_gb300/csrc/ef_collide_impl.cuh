@@ -26,7 +26,11 @@ namespace ef {
 
 namespace cg = cooperative_groups;
 
-constexpr int kMaxThreads = 320;
+// Threads per CTA the kernel is compiled for.  A CTA with more than 8 warps puts 3 warps on some
+// SM sub-partition, which caps registers at 168 per thread; the large pencils (FP32 N >= 40, all
+// FP64) need more, so those instantiations are limited to 256 threads (255 registers).
+template <typename T, int N>
+__host__ __device__ constexpr int max_threads() { return (sizeof(T) == 8 || N >= 40) ? 256 : 320; }
 
 template <typename T>
 __device__ __forceinline__ void sincospi_t(T x, T *s, T *c);
@@ -62,7 +66,7 @@ __host__ __device__ constexpr size_t smem_bytes_for(int planes, int sg_global)
 }
 
 template <typename T, int D, int N>
-__global__ void __launch_bounds__(kMaxThreads, 1) collide_kernel(const CollideArgs a)
+__global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const CollideArgs a)
 {
     constexpr int H = N / 2 + 1;
     constexpr int N1 = (D == 3) ? N : 1;
@@ -111,28 +115,41 @@ __global__ void __launch_bounds__(kMaxThreads, 1) collide_kernel(const CollideAr
     const T scale = T(1) / T(CELL);
     const T *Mbase = reinterpret_cast<const T *>(a.mult);
 
-    for (int64_t c = cid; c < a.ncells; c += nclusters) {
+    __shared__ long long s_cell;
+    int64_t c = cid - nclusters;
+    for (;;) {
+        if (a.counter) {            // dynamic: the cluster takes the next unclaimed cell
+            if (rank == 0 && tid == 0) s_cell = (long long)atomicAdd(a.counter, 1ULL);
+            cl.sync();
+            c = *cl.map_shared_rank(&s_cell, 0);
+        } else {
+            c += nclusters;
+        }
+        if (c >= a.ncells) break;
         const int64_t coff = a.cell_off ? a.cell_off[c] : c * CELL;
         const int64_t cglob = a.cell_id ? a.cell_id[c] : c;
         const T *F = reinterpret_cast<const T *>(a.F) + coff;
         T *Out = reinterpret_cast<T *>(a.Q) + coff;
 
         // ---------------- F1: own planes, last axis real -> half complex (two rows per thread)
+        // rows q and q + rows/2 per thread: consecutive threads touch consecutive rows, so the
+        // odd row strides (H complex, N + 1 reals) keep shared-memory accesses conflict free
         for (int q = tid; q < npairs; q += nt) {
-            const int r0 = 2 * q;
-            const T *src = F + ((int64_t)rank * rows + r0) * N;
+            const int r0 = q, r1 = q + npairs;
+            const T *src0 = F + ((int64_t)rank * rows + r0) * N;
+            const T *src1 = F + ((int64_t)rank * rows + r1) * N;
             T x0[N], x1[N];
 #pragma unroll
             for (int n = 0; n < N; ++n) {
-                x0[n] = src[n];
-                x1[n] = src[N + n];
+                x0[n] = src0[n];
+                x1[n] = src1[n];
             }
             C2<T> X0[H], X1[H];
             r2c_pair<N, T>(x0, x1, X0, X1, tw);
 #pragma unroll
             for (int k = 0; k < H; ++k) {
                 Is[r0 * H + k] = X0[k];
-                Is[(r0 + 1) * H + k] = X1[k];
+                Is[r1 * H + k] = X1[k];
             }
         }
         if constexpr (D == 3) {
@@ -186,6 +203,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) collide_kernel(const CollideAr
                     C2<T> *dst = cl.map_shared_rank(Is, owner);
                     dst[(size_t)zl * NP + pencil] = v[z];
                 }
+                if (o + 1 < a.nops) {       // pull the next direction's multipliers towards L1
+                    const T *Mn = Mbase + (size_t)a.ops[o + 1].dir * N * NP + pencil;
+#pragma unroll
+                    for (int z = 0; z < N; ++z) asm volatile("prefetch.global.L1 [%0];" ::"l"(Mn + (size_t)z * NP));
+                }
             }
             cl.sync();
 
@@ -204,17 +226,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) collide_kernel(const CollideAr
                 __syncthreads();
             }
             for (int q = tid; q < npairs; q += nt) {
-                const int r0 = 2 * q;
+                const int r0 = q, r1 = q + npairs;
                 C2<T> X0[H], X1[H];
 #pragma unroll
                 for (int k = 0; k < H; ++k) {
                     X0[k] = Is[r0 * H + k];
-                    X1[k] = Is[(r0 + 1) * H + k];
+                    X1[k] = Is[r1 * H + k];
                 }
                 T y0[N], y1[N];
                 c2r_pair<N, T>(X0, X1, y0, y1, tw);
-                T *S0 = Sb + (size_t)r0 * RS, *S1 = S0 + RS;
-                T *G0 = Gb + (size_t)r0 * RS, *G1 = G0 + RS;
+                T *S0 = Sb + (size_t)r0 * RS, *S1 = Sb + (size_t)r1 * RS;
+                T *G0 = Gb + (size_t)r0 * RS, *G1 = Gb + (size_t)r1 * RS;
                 const T w = T(op.w);
                 switch (op.kind) {
                 case OP_S_SET:
@@ -234,10 +256,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) collide_kernel(const CollideAr
                     for (int n = 0; n < N; ++n) { G0[n] += y0[n] * S0[n]; G1[n] += y1[n] * S1[n]; }
                     break;
                 default: {  // OP_LOSS: Q = G - F nu; output; diagnostics
-                    const int64_t grow0 = (int64_t)rank * rows + r0;
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
-                        const int64_t grow = grow0 + half;
+                        const int64_t grow = (int64_t)rank * rows + (half ? r1 : r0);
                         const T *nu = half ? y1 : y0;
                         const T *G = half ? G1 : G0;
                         const T *Frow = F + grow * N;

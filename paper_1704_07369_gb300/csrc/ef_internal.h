@@ -43,6 +43,7 @@ struct CollideArgs {
     double h;                 // grid spacing 2L/N
     double *diag;             // nullable: [cell_id][kDiag]
     int *status;              // device status word
+    unsigned long long *counter;  // nullable: dynamic cell queue (zeroed before the launch)
 };
 
 // Multiplier table layout for one class: mult[dir][lz][p], p = ly * H + lx (3D) or p = lx (2D),

@@ -12,6 +12,7 @@ namespace ef {
 
 #define EF_DECLARE_VARIANT(SUF)                                                                      \
     bool collide_supported_##SUF(int N);                                                             \
+    int collide_maxthreads_##SUF(int N);                                                             \
     size_t collide_smem_##SUF(int N, int planes, int sg_global);                                     \
     cudaError_t collide_setup_##SUF(int N, size_t smem, int cluster, int tpb, int *max_clusters);    \
     cudaError_t collide_launch_##SUF(int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, \
@@ -29,6 +30,5 @@ cudaError_t moments_launch(int prec, int d, const void *F, const void *Q, const 
                            const int64_t *cell_N, int64_t ncells, int N_uniform, double twoL, double *out,
                            cudaStream_t s);
 
-constexpr int kMaxThreadsHost = 320;
 
 }  // namespace ef

@@ -254,6 +254,11 @@ struct ClassPlan {
 
 struct ef_plan_s {
     Desc desc;
+    // concurrent size classes: one internal stream, event and cell counter per class
+    std::vector<cudaStream_t> cstreams;
+    std::vector<cudaEvent_t> cevents;
+    cudaEvent_t fork = nullptr;
+    unsigned long long *d_counters = nullptr;
     int device = 0;
     bool batched = false;
     int64_t ncells = 0;
@@ -279,6 +284,12 @@ bool size_built(int prec, int d, int N)
 {
     if (prec == EF_PREC_F32) return d == 3 ? ef::collide_supported_f32_3d(N) : ef::collide_supported_f32_2d(N);
     return d == 3 ? ef::collide_supported_f64_3d(N) : ef::collide_supported_f64_2d(N);
+}
+
+int maxthreads_for(int prec, int d, int N)
+{
+    if (prec == EF_PREC_F32) return d == 3 ? ef::collide_maxthreads_f32_3d(N) : ef::collide_maxthreads_f32_2d(N);
+    return d == 3 ? ef::collide_maxthreads_f64_3d(N) : ef::collide_maxthreads_f64_2d(N);
 }
 
 size_t smem_for(int prec, int d, int N, int planes, int sg)
@@ -321,7 +332,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp)
             if (rows % 2) continue;
             int need = std::max({(NP + C - 1) / C, rows / 2, d == 3 ? planes * H : 1});
             int tpb = std::max(64, (need + 31) / 32 * 32);
-            if (tpb > ef::kMaxThreadsHost) continue;
+            if (tpb > maxthreads_for(ds.prec, d, N)) continue;
             if ((int64_t)C * tpb < NP) continue;
             const size_t smem = smem_for(ds.prec, d, N, planes, sg);
             if ((long)smem > smem_max) continue;
@@ -394,31 +405,37 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
         }
         tab[(size_t)u * per + i] = val;
     });
-    double *loss = &tab[(size_t)ndir * per];
-    for (const Pair &pr : pairs)
-        for (int64_t i = 0; i < per; ++i) loss[i] += pr.w * tab[(size_t)pr.de * per + i] * tab[(size_t)pr.ds * per + i];
-
-    // op list: for each gain direction e, accumulate S = sum w a_e* then G (+)= a_e S
-    std::vector<ef::Op> ops;
+    // Group the gain pairs by their first direction e: sum_c w_c a_e a_{e*_c} = a_e S_e with
+    // S_e = IFFT(Gamma_e Fhat), Gamma_e = sum_c w_c M_{e*_c} (linearity of the inverse transform),
+    // so each e costs two inverse transforms however many partners it has.
     std::map<int, std::vector<const Pair *>> groups;
     std::vector<int> order;
     for (const Pair &pr : pairs) {
         if (!groups.count(pr.de)) order.push_back(pr.de);
         groups[pr.de].push_back(&pr);
     }
-    bool first_g = true;
-    for (int de : order) {
-        bool first_s = true;
-        for (const Pair *pr : groups[de]) {
-            ops.push_back(ef::Op{pr->ds, first_s ? ef::OP_S_SET : ef::OP_S_ADD, pr->w});
-            first_s = false;
-        }
-        ops.push_back(ef::Op{de, first_g ? ef::OP_G_SET : ef::OP_G_ADD, 1.0});
-        first_g = false;
+    const int ne = (int)order.size();
+    // output table rows: [0, ne) = M_e, [ne, 2 ne) = Gamma_e, 2 ne = loss
+    std::vector<double> out((size_t)(2 * ne + 1) * per, 0.0);
+    for (int g = 0; g < ne; ++g) {
+        const int de = order[g];
+        double *Me = &out[(size_t)g * per], *Ge = &out[(size_t)(ne + g) * per];
+        std::memcpy(Me, &tab[(size_t)de * per], per * sizeof(double));
+        for (const Pair *pr : groups[de])
+            for (int64_t i = 0; i < per; ++i) Ge[i] += pr->w * tab[(size_t)pr->ds * per + i];
     }
-    ops.push_back(ef::Op{ndir, ef::OP_LOSS, 1.0});
+    double *loss = &out[(size_t)(2 * ne) * per];      // L(m) = sigma(m)^2 B_fast(m, m)
+    for (int g = 0; g < ne; ++g)
+        for (int64_t i = 0; i < per; ++i) loss[i] += out[(size_t)g * per + i] * out[(size_t)(ne + g) * per + i];
+    std::vector<ef::Op> ops;
+    for (int g = 0; g < ne; ++g) {
+        ops.push_back(ef::Op{ne + g, ef::OP_S_SET, 1.0});
+        ops.push_back(ef::Op{g, g == 0 ? ef::OP_G_SET : ef::OP_G_ADD, 1.0});
+    }
+    ops.push_back(ef::Op{2 * ne, ef::OP_LOSS, 1.0});
     if ((int)ops.size() > ef::kMaxOps) return fail(EF_ERR_UNSUPPORTED, "too many spectral directions");
-    cp.ndir = ndir + 1;
+    tab.swap(out);
+    cp.ndir = 2 * ne + 1;
     cp.nops = (int)ops.size();
 
     cudaError_t e = cudaSuccess;
@@ -459,6 +476,10 @@ void destroy_plan(ef_plan_s *p)
     cudaFree(p->d_all_off);
     cudaFree(p->d_all_N);
     cudaFree(p->d_status);
+    cudaFree(p->d_counters);
+    for (cudaStream_t st : p->cstreams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : p->cevents) cudaEventDestroy(ev);
+    if (p->fork) cudaEventDestroy(p->fork);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     delete p;
 }
@@ -520,16 +541,34 @@ ef_status check_device(const ef_plan_s *p)
     return EF_OK;
 }
 
+// Enqueue one step: every size class on its own internal stream (forked from and joined back
+// to the caller's stream), each with a dynamic cell queue, so that clusters of one class fill
+// the SMs another class leaves idle.  A single class launches directly on the caller's stream.
 ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, double dt, double *diag,
               cudaStream_t s)
 {
     const Desc &ds = p->desc;
-    for (ClassPlan &cp : p->classes) {
+    const bool multi = p->classes.size() > 1;
+    cudaError_t e;
+    if (multi) {
+        e = cudaEventRecord(p->fork, s);
+        if (e != cudaSuccess) return cuda_fail(e, "fork event");
+    }
+    for (size_t ci = 0; ci < p->classes.size(); ++ci) {
+        ClassPlan &cp = p->classes[ci];
         const int64_t n = p->batched ? cp.ncells : ncells;
         if (n <= 0) continue;
         const int grid = (int)std::min<int64_t>(n, cp.max_clusters);
         ef_status st = ensure_sg(p, cp, grid);
         if (st != EF_OK) return st;
+        cudaStream_t cs = s;
+        if (multi) {
+            cs = p->cstreams[ci];
+            e = cudaStreamWaitEvent(cs, p->fork, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "fork wait");
+            e = cudaMemsetAsync(p->d_counters + ci, 0, sizeof(unsigned long long), cs);
+            if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+        }
         ef::CollideArgs a{};
         a.F = F;
         a.Q = Out;
@@ -548,8 +587,14 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
         a.h = 2.0 * ds.L / cp.N;
         a.diag = diag;
         a.status = p->d_status;
-        cudaError_t e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, s);
+        a.counter = multi ? p->d_counters + ci : nullptr;
+        e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, cs);
         if (e != cudaSuccess) return cuda_fail(e, "collide launch");
+        if (multi) {
+            e = cudaEventRecord(p->cevents[ci], cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->cevents[ci], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "join");
+        }
     }
     return EF_OK;
 }
@@ -563,6 +608,21 @@ ef_status finish_plan(ef_plan_s *p)
     for (ClassPlan &cp : p->classes) {
         ef_status st = build_class(p->desc, cp);
         if (st != EF_OK) return st;
+    }
+    if (p->classes.size() > 1) {
+        e = cudaMalloc((void **)&p->d_counters, p->classes.size() * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e, "cell queues");
+        e = cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "events");
+        for (size_t i = 0; i < p->classes.size(); ++i) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (st) p->cstreams.push_back(st);
+            if (ev) p->cevents.push_back(ev);
+            if (e != cudaSuccess) return cuda_fail(e, "class streams");
+        }
     }
     return EF_OK;
 }
