@@ -62,7 +62,7 @@ __host__ __device__ constexpr size_t smem_bytes_for(int planes, int sg_global)
     sg = (sg + 15) / 16 * 16;
     size_t tw = (size_t)N * sizeof(C2<T>);
     size_t part = (32 + 1) * kDiag * sizeof(double);
-    return is + sg + tw + part;
+    return is + sg + tw + part + 16;        // + the cluster's current cell index
 }
 
 template <typename T, int D, int N>
@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     C2<T> *tw = reinterpret_cast<C2<T> *>(smem_raw + off);
     off += (size_t)N * sizeof(C2<T>);
     double *part = reinterpret_cast<double *>(smem_raw + off);      // [32 warps + 1][kDiag]
+    off += (32 + 1) * kDiag * sizeof(double);
+    long long *s_cell = reinterpret_cast<long long *>(smem_raw + off);
 
     for (int j = tid; j < N; j += nt) {
         T s, c;
@@ -115,13 +117,12 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     const T scale = T(1) / T(CELL);
     const T *Mbase = reinterpret_cast<const T *>(a.mult);
 
-    __shared__ long long s_cell;
     int64_t c = cid - nclusters;
     for (;;) {
         if (a.counter) {            // dynamic: the cluster takes the next unclaimed cell
-            if (rank == 0 && tid == 0) s_cell = (long long)atomicAdd(a.counter, 1ULL);
+            if (rank == 0 && tid == 0) *s_cell = (long long)atomicAdd(a.counter, 1ULL);
             cl.sync();
-            c = *cl.map_shared_rank(&s_cell, 0);
+            c = *cl.map_shared_rank(s_cell, 0);
         } else {
             c += nclusters;
         }
