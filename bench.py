@@ -49,17 +49,18 @@ def workload_config(ncells):
 # ------------------------------------------------------------------ per-cell work model ------
 
 def n_ops(R=R_RANK):
-    """Inverse 3D transforms per cell: n_mu n_phi (1 + n_c) directions + the loss (R = 32 ->
-    (2, 4, 2) -> 24 + 1)."""
+    """Inverse 3D transforms per cell.  The hard-sphere kernel's R = 2 n_mu n_phi n_c terms share
+    n_e = n_mu n_phi first directions; by linearity each e needs two transforms (a_e and the
+    weighted sum of its partners), plus one for the loss: 2 n_e + 1 (R = 32 -> 17)."""
     table = {32: (2, 4, 2), 64: (2, 4, 4)}
     nmu, nphi, nc = table[R]
-    return nmu * nphi * (1 + nc) + 1
+    return 2 * nmu * nphi + 1
 
 
 def flops_per_cell(N, R=R_RANK):
     """Algorithmic FP32 flops of one collision evaluation of one cell: (1 + n_ops) real 3D FFTs at
     2.5 M log2 M flops each (M = N^3), the spectral multiply (2 flops per half-spectrum complex
-    value) and the accumulate (2 flops per real point) of every op."""
+    value, M per op) and the accumulate (2 flops per real point per op)."""
     M = float(N) ** 3
     ops = n_ops(R)
     return (1 + ops) * 2.5 * M * np.log2(M) + ops * (M + 2.0 * M)
@@ -329,9 +330,12 @@ def run_ours(args, world, rank, local):
 
     if rank != 0:
         return 0
+    cfg = workload_config(args.cells)
+    cfg["shapes"] = [{k: v for k, v in ci.items() if k in ("N", "cells", "cluster", "threads", "prefetch", "tuned_us")}
+                     for ci in plan.class_info()]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.cells),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "cells_per_s": args.cells * world / step_s, "status": int(st), "roofline": roof,
             "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch * args.steps}
     if not args.no_cpu_baseline and world == 1:

@@ -135,6 +135,13 @@ ef_status ef_plan_set_graph(ef_plan_t plan, int enable);
  * plans; 0 otherwise), [6] = precision, [7] = kernel launches per ef_collide. */
 ef_status ef_plan_info(ef_plan_t plan, int64_t info[8]);
 
+/* Launch shape of size class i (0 <= i < info[1] of ef_plan_info), host values:
+ * out[0] = N, [1] = cells (batched plans; 0 otherwise), [2] = cluster size (CTAs per cell),
+ * [3] = threads per CTA, [4] = axis-0 planes per CTA, [5] = 1 if the S/G accumulators live in
+ * global memory, [6] = 1 if the next multiplier slice is prefetched, [7] = autotuned time of one
+ * class launch in microseconds (0 when not tuned).  EF_ERR_INVALID_ARG for a bad index. */
+ef_status ef_plan_class_info(ef_plan_t plan, int i, int64_t out[8]);
+
 const char *ef_status_string(ef_status s);
 const char *ef_last_error(void);
 

@@ -35,7 +35,7 @@ EF_DIAG_STRIDE = 10
 # every symbol include/ef.h declares
 SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
            "ef_collide", "ef_euler_step", "ef_moments_entropy", "ef_plan_status",
-           "ef_plan_set_graph", "ef_plan_info", "ef_status_string", "ef_last_error")
+           "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_status_string", "ef_last_error")
 
 
 class EfError(RuntimeError):
@@ -78,6 +78,7 @@ def lib():
         L.ef_plan_status.argtypes = [vp, i32, i32]
         L.ef_plan_set_graph.argtypes = [vp, i32]
         L.ef_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
+        L.ef_plan_class_info.argtypes = [vp, i32, ctypes.POINTER(i64)]
         L.ef_status_string.restype = ctypes.c_char_p
         L.ef_status_string.argtypes = [i32]
         L.ef_last_error.restype = ctypes.c_char_p
@@ -164,6 +165,13 @@ def ef_plan_info(plan):
     return dict(zip(keys, list(info)))
 
 
+def ef_plan_class_info(plan, i):
+    out = (ctypes.c_int64 * 8)()
+    _check(lib().ef_plan_class_info(plan, int(i), out))
+    keys = ("N", "cells", "cluster", "threads", "planes", "sg_global", "prefetch", "tuned_us")
+    return dict(zip(keys, list(out)))
+
+
 class Plan:
     """Owning wrapper of an ``ef_plan_t``."""
 
@@ -197,6 +205,9 @@ class Plan:
 
     def info(self):
         return ef_plan_info(self.handle)
+
+    def class_info(self):
+        return [ef_plan_class_info(self.handle, i) for i in range(self.info()["classes"])]
 
     def _n(self, F, ncells):
         if ncells is not None:

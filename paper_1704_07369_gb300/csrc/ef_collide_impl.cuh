@@ -46,6 +46,28 @@ __device__ __forceinline__ float log_t<float>(float x) { return logf(x); }
 template <>
 __device__ __forceinline__ double log_t<double>(double x) { return log(x); }
 
+// Cluster barriers.  full(): release/acquire, publishes prior (distributed) shared-memory writes.
+// war(): relaxed arrive, for write-after-read protection only (every value loaded before it has
+// already been consumed).  A one-CTA cluster uses the CTA barrier.
+struct Sync {
+    cg::cluster_group cl;
+    int C;
+    __device__ __forceinline__ void full()
+    {
+        if (C == 1) __syncthreads();
+        else cl.sync();
+    }
+    __device__ __forceinline__ void war()
+    {
+        if (C == 1) {
+            __syncthreads();
+        } else {
+            asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+            asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+        }
+    }
+};
+
 __device__ __forceinline__ void record_status(int *status, int code)
 {
     if (status) atomicCAS(status, 0, code);
@@ -58,7 +80,7 @@ __host__ __device__ constexpr size_t smem_bytes_for(int planes, int sg_global)
     constexpr int H = N / 2 + 1;
     constexpr int N1 = (D == 3) ? N : 1;
     size_t is = (size_t)planes * N1 * H * sizeof(C2<T>);
-    size_t sg = sg_global ? 0 : 2 * (size_t)planes * N1 * (N + 1) * sizeof(T);
+    size_t sg = sg_global ? 0 : 2 * (size_t)planes * N1 * N * sizeof(T);
     sg = (sg + 15) / 16 * 16;
     size_t tw = (size_t)N * sizeof(C2<T>);
     size_t part = (32 + 1) * kDiag * sizeof(double);
@@ -71,7 +93,6 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     constexpr int H = N / 2 + 1;
     constexpr int N1 = (D == 3) ? N : 1;
     constexpr int NP = N1 * H;         // spectral columns of one axis-0 plane = pencils
-    constexpr int RS = N + 1;          // padded real row stride of S and G
     constexpr int64_t CELL = (int64_t)N * N1 * N;
 
     cg::cluster_group cl = cg::this_cluster();
@@ -79,6 +100,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     const int rank = (int)cl.block_rank();
     const int P = a.planes;
     const int tid = threadIdx.x, nt = blockDim.x;
+    Sync bar{cl, C};
     const int rows = P * N1;           // real rows owned by this CTA
     const int npairs = rows / 2;
 
@@ -88,13 +110,13 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     T *Sb, *Gb;
     if (a.sg_global) {
         const int64_t slot = blockIdx.x;
-        T *base = reinterpret_cast<T *>(a.sg_ws) + slot * (int64_t)2 * rows * RS;
+        T *base = reinterpret_cast<T *>(a.sg_ws) + slot * (int64_t)2 * rows * N;
         Sb = base;
-        Gb = base + (int64_t)rows * RS;
+        Gb = base + (int64_t)rows * N;
     } else {
         Sb = reinterpret_cast<T *>(smem_raw + off);
-        Gb = Sb + (size_t)rows * RS;
-        off += 2 * (size_t)rows * RS * sizeof(T);
+        Gb = Sb + (size_t)rows * N;
+        off += 2 * (size_t)rows * N * sizeof(T);
         off = (off + 15) / 16 * 16;
     }
     C2<T> *tw = reinterpret_cast<C2<T> *>(smem_raw + off);
@@ -121,7 +143,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     for (;;) {
         if (a.counter) {            // dynamic: the cluster takes the next unclaimed cell
             if (rank == 0 && tid == 0) *s_cell = (long long)atomicAdd(a.counter, 1ULL);
-            cl.sync();
+            bar.full();
             c = *cl.map_shared_rank(s_cell, 0);
         } else {
             c += nclusters;
@@ -166,7 +188,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                 for (int y = 0; y < N; ++y) col[y * H] = v[y];
             }
         }
-        cl.sync();
+        bar.full();
 
         // ---------------- F2: gather the axis-0 pencil and finish the forward transform
         C2<T> fh[N];
@@ -181,7 +203,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 #pragma unroll
             for (int z = 0; z < N; ++z) fh[z] = cscale(fh[z], scale);
         }
-        cl.sync();
+        bar.war();
 
         // diagnostics accumulators (loss op only)
         double dsum[kDiag];
@@ -204,13 +226,13 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                     C2<T> *dst = cl.map_shared_rank(Is, owner);
                     dst[(size_t)zl * NP + pencil] = v[z];
                 }
-                if (o + 1 < a.nops) {       // pull the next direction's multipliers towards L1
+                if (a.prefetch && o + 1 < a.nops) {   // pull the next direction's multipliers towards L1
                     const T *Mn = Mbase + (size_t)a.ops[o + 1].dir * N * NP + pencil;
 #pragma unroll
                     for (int z = 0; z < N; ++z) asm volatile("prefetch.global.L1 [%0];" ::"l"(Mn + (size_t)z * NP));
                 }
             }
-            cl.sync();
+            bar.full();
 
             // ---------------- B: local inverse passes and accumulation
             if constexpr (D == 3) {
@@ -236,25 +258,27 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                 }
                 T y0[N], y1[N];
                 c2r_pair<N, T>(X0, X1, y0, y1, tw);
-                T *S0 = Sb + (size_t)r0 * RS, *S1 = Sb + (size_t)r1 * RS;
-                T *G0 = Gb + (size_t)r0 * RS, *G1 = Gb + (size_t)r1 * RS;
+                // S and G are stored column-major ([x][row]): consecutive threads own consecutive
+                // rows, so every access below is conflict free without padding
+                T *S0 = Sb + r0, *S1 = Sb + r1;
+                T *G0 = Gb + r0, *G1 = Gb + r1;
                 const T w = T(op.w);
                 switch (op.kind) {
                 case OP_S_SET:
 #pragma unroll
-                    for (int n = 0; n < N; ++n) { S0[n] = w * y0[n]; S1[n] = w * y1[n]; }
+                    for (int n = 0; n < N; ++n) { S0[n * rows] = w * y0[n]; S1[n * rows] = w * y1[n]; }
                     break;
                 case OP_S_ADD:
 #pragma unroll
-                    for (int n = 0; n < N; ++n) { S0[n] += w * y0[n]; S1[n] += w * y1[n]; }
+                    for (int n = 0; n < N; ++n) { S0[n * rows] += w * y0[n]; S1[n * rows] += w * y1[n]; }
                     break;
                 case OP_G_SET:
 #pragma unroll
-                    for (int n = 0; n < N; ++n) { G0[n] = y0[n] * S0[n]; G1[n] = y1[n] * S1[n]; }
+                    for (int n = 0; n < N; ++n) { G0[n * rows] = y0[n] * S0[n * rows]; G1[n * rows] = y1[n] * S1[n * rows]; }
                     break;
                 case OP_G_ADD:
 #pragma unroll
-                    for (int n = 0; n < N; ++n) { G0[n] += y0[n] * S0[n]; G1[n] += y1[n] * S1[n]; }
+                    for (int n = 0; n < N; ++n) { G0[n * rows] += y0[n] * S0[n * rows]; G1[n * rows] += y1[n] * S1[n * rows]; }
                     break;
                 default: {  // OP_LOSS: Q = G - F nu; output; diagnostics
 #pragma unroll
@@ -273,7 +297,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 #pragma unroll
                         for (int n = 0; n < N; ++n) {
                             const T f = Frow[n];
-                            const T qv = G[n] - f * nu[n];
+                            const T qv = G[n * rows] - f * nu[n];
                             T outv;
                             if (a.out_mode == OUT_EULER) {
                                 outv = f + T(a.dt) * qv;
@@ -323,7 +347,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                 } break;
                 }
             }
-            cl.sync();
+            bar.war();
         }
 
         // ---------------- per-cell FP64 reduction of the diagnostics
@@ -352,7 +376,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                 }
                 part[32 * kDiag + k] = v;
             }
-            cl.sync();
+            bar.full();
             if (rank == 0 && tid < kDiag) {
                 const int k = tid;
                 double v = part[32 * kDiag + k];
@@ -368,10 +392,10 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                 if (D == 2 && k == 3) v = 0.0;
                 a.diag[cglob * kDiag + k] = v;
             }
-            cl.sync();
+            bar.war();
         }
     }
-    cl.sync();   // no CTA leaves while a peer may still read its shared memory
+    bar.war();   // no CTA leaves while a peer may still read its shared memory
 }
 
 // ------------------------------------------------------------------ moments kernel ---------

@@ -44,6 +44,7 @@ struct CollideArgs {
     double *diag;             // nullable: [cell_id][kDiag]
     int *status;              // device status word
     unsigned long long *counter;  // nullable: dynamic cell queue (zeroed before the launch)
+    int prefetch;             // 1: prefetch the next op's multipliers into L1
 };
 
 // Multiplier table layout for one class: mult[dir][lz][p], p = ly * H + lx (3D) or p = lx (2D),

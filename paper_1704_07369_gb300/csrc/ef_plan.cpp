@@ -16,6 +16,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -239,7 +240,8 @@ int mode_of(int N, int i) { return i < N / 2 ? i : i - N; }
 struct ClassPlan {
     int N = 0;
     int64_t ncells = 0;                 // batched: cells of this size; uniform plan: 0
-    int cluster = 1, tpb = 32, planes = 0, sg_global = 0;
+    int cluster = 1, tpb = 32, planes = 0, sg_global = 0, prefetch = 1;
+    double tuned_ms = 0.0;              // autotuner's best time (0 when not tuned)
     size_t smem = 0;
     int max_clusters = 0;
     int ndir = 0, nops = 0;
@@ -312,26 +314,34 @@ cudaError_t launch_for(int prec, int d, int N, const ef::CollideArgs &a, int gri
     return d == 3 ? ef::collide_launch_f64_3d(N, a, grid, tpb, smem, s) : ef::collide_launch_f64_2d(N, a, grid, tpb, smem, s);
 }
 
-// Choose the cluster size / block shape for one N: the smallest cluster whose CTAs hold their
-// slab and (if possible) the S/G accumulators in shared memory, with one pencil per thread.
-ef_status choose_shape(const Desc &ds, ClassPlan &cp)
+struct Shape {
+    int cluster, tpb, planes, sg_global;
+    size_t smem;
+    int max_clusters;
+};
+
+// Every launch shape that fits one N: cluster sizes C | N with an even number of real rows per
+// CTA, one stage-A pencil per thread (C * tpb >= pencils), at most the instantiation's thread
+// limit, shared memory within the device's opt-in limit (S/G in global memory only when nothing
+// fits otherwise) and at least one co-resident cluster.
+std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
 {
-    const int N = cp.N, d = ds.d;
+    const int d = ds.d;
     const int H = N / 2 + 1, N1 = d == 3 ? N : 1, NP = N1 * H;
     int dev = 0;
     cudaGetDevice(&dev);
     int smem_max = 0;
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int cands[] = {1, 2, 4, 8, 16};
-    std::string why;
-    for (int sg = 0; sg <= 1; ++sg) {
+    const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+    std::vector<Shape> out;
+    for (int sg = 0; sg <= 1 && out.empty(); ++sg) {
         for (int C : cands) {
             if (N % C) continue;
             const int planes = N / C;
             const int rows = planes * N1;
             if (rows % 2) continue;
-            int need = std::max({(NP + C - 1) / C, rows / 2, d == 3 ? planes * H : 1});
-            int tpb = std::max(64, (need + 31) / 32 * 32);
+            const int need = std::max({(NP + C - 1) / C, rows / 2, d == 3 ? planes * H : 1});
+            const int tpb = std::max(64, (need + 31) / 32 * 32);
             if (tpb > maxthreads_for(ds.prec, d, N)) continue;
             if ((int64_t)C * tpb < NP) continue;
             const size_t smem = smem_for(ds.prec, d, N, planes, sg);
@@ -344,16 +354,164 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp)
                 continue;
             }
             if (mc <= 0) continue;
-            cp.cluster = C;
-            cp.tpb = tpb;
-            cp.planes = planes;
-            cp.sg_global = sg;
-            cp.smem = smem;
-            cp.max_clusters = mc;
-            return EF_OK;
+            out.push_back(Shape{C, tpb, planes, sg, smem, mc});
         }
     }
-    return fail(EF_ERR_UNSUPPORTED, "no launch shape fits N=" + std::to_string(N) + " on this device " + why);
+    return out;
+}
+
+void apply_shape(ClassPlan &cp, const Shape &sh)
+{
+    cp.cluster = sh.cluster;
+    cp.tpb = sh.tpb;
+    cp.planes = sh.planes;
+    cp.sg_global = sh.sg_global;
+    cp.smem = sh.smem;
+    cp.max_clusters = sh.max_clusters;
+}
+
+std::string device_key()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    std::string k = prop.name;
+    for (char &c : k)
+        if (c == ' ') c = '_';
+    return k + "_sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "_" + std::to_string(prop.multiProcessorCount);
+}
+
+std::string tune_key(const Desc &ds, int N)
+{
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
+                  ds.d, N, (int)ds.kernel, ds.R, ds.J, ds.nmu, ds.nphi, ds.nc, ds.sigma);
+    return buf;
+}
+
+bool cache_lookup(const std::string &key, int &C, int &tpb, int &sg, int &pf)
+{
+    const char *path = std::getenv("EF_AUTOTUNE_CACHE");
+    if (!path) return false;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string ln(line);
+        const size_t bar = ln.find('|');
+        if (bar == std::string::npos || ln.substr(0, bar) != key) continue;
+        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d %d", &C, &tpb, &sg, &pf) == 4) found = true;
+    }
+    std::fclose(f);
+    return found;
+}
+
+void cache_store(const std::string &key, int C, int tpb, int sg, int pf, double ms)
+{
+    const char *path = std::getenv("EF_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s|%d %d %d %d %.4f\n", key.c_str(), C, tpb, sg, pf, ms);
+    std::fclose(f);
+}
+
+// Plan-time autotuner: time every candidate shape (and the L1 prefetch on / off) on a scratch
+// batch of ncells_tune cells and keep the fastest.  Results are cached per device and
+// discretisation in the file named by EF_AUTOTUNE_CACHE when it is set; EF_AUTOTUNE=0 skips the
+// timing and takes the smallest cluster.
+ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
+{
+    std::string why;
+    std::vector<Shape> shapes = candidate_shapes(ds, cp.N, why);
+    if (shapes.empty())
+        return fail(EF_ERR_UNSUPPORTED, "no launch shape fits N=" + std::to_string(cp.N) + " on this device " + why);
+    apply_shape(cp, shapes[0]);
+    cp.prefetch = 1;
+    const char *env = std::getenv("EF_AUTOTUNE");
+    const bool tune = ncells_tune > 0 && !(env && env[0] == '0') && shapes.size() > 1;
+    if (!tune) return EF_OK;
+    const std::string key = tune_key(ds, cp.N);
+    int C = 0, tpb = 0, sg = 0, pf = 1;
+    if (cache_lookup(key, C, tpb, sg, pf)) {
+        for (const Shape &sh : shapes)
+            if (sh.cluster == C && sh.tpb == tpb && sh.sg_global == sg) {
+                apply_shape(cp, sh);
+                cp.prefetch = pf;
+                return EF_OK;
+            }
+    }
+    const int d = ds.d;
+    const int64_t cell = d == 3 ? (int64_t)cp.N * cp.N * cp.N : (int64_t)cp.N * cp.N;
+    const size_t el = ds.prec == EF_PREC_F32 ? 4 : 8;
+    void *F = nullptr, *Q = nullptr, *sgws = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&F, ncells_tune * cell * el);
+    if (e == cudaSuccess) e = cudaMalloc(&Q, ncells_tune * cell * el);
+    if (e == cudaSuccess) e = cudaMemset(F, 0, ncells_tune * cell * el);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = 1e30;
+    Shape best_sh = shapes[0];
+    int best_pf = 1;
+    for (size_t i = 0; e == cudaSuccess && i < shapes.size(); ++i) {
+        const Shape &sh = shapes[i];
+        const int grid = (int)std::min<int64_t>(ncells_tune, sh.max_clusters);
+        if (sh.sg_global) {
+            const int64_t rows = (int64_t)sh.planes * (d == 3 ? cp.N : 1);
+            cudaFree(sgws);
+            sgws = nullptr;
+            e = cudaMalloc(&sgws, (size_t)grid * sh.cluster * 2 * rows * cp.N * el);
+            if (e != cudaSuccess) break;
+        }
+        for (int pfv = 0; pfv <= 1; ++pfv) {
+            ef::CollideArgs a{};
+            a.F = F;
+            a.Q = Q;
+            a.ncells = ncells_tune;
+            a.mult = cp.d_mult;
+            a.ops = cp.d_ops;
+            a.nops = cp.nops;
+            a.cluster = sh.cluster;
+            a.planes = sh.planes;
+            a.sg_global = sh.sg_global;
+            a.sg_ws = sgws;
+            a.out_mode = ef::OUT_COLLIDE;
+            a.h = 1.0;
+            a.prefetch = pfv;
+            double tmin = 1e30;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess) e = launch_for(ds.prec, d, cp.N, a, grid, sh.tpb, sh.smem, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tmin = std::min(tmin, (double)ms);
+            }
+            if (e == cudaSuccess && tmin < best) {
+                best = tmin;
+                best_sh = sh;
+                best_pf = pfv;
+            }
+        }
+    }
+    cudaFree(F);
+    cudaFree(Q);
+    cudaFree(sgws);
+    if (st) cudaStreamDestroy(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune");
+    apply_shape(cp, best_sh);
+    cp.prefetch = best_pf;
+    cp.tuned_ms = best;
+    cache_store(key, best_sh.cluster, best_sh.tpb, best_sh.sg_global, best_pf, best);
+    return EF_OK;
 }
 
 template <typename T>
@@ -445,7 +603,7 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
     if (e != cudaSuccess) return cuda_fail(e, "op list");
     e = cudaMemcpy(cp.d_ops, ops.data(), ops.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "op list copy");
-    return choose_shape(ds, cp);
+    return choose_shape(ds, cp, cp.ncells > 0 ? std::min<int64_t>(cp.ncells, 512) : 0);
 }
 
 ef_status ensure_sg(ef_plan_s *p, ClassPlan &cp, int grid_clusters)
@@ -457,7 +615,7 @@ ef_status ensure_sg(ef_plan_s *p, ClassPlan &cp, int grid_clusters)
     if (slots <= cp.sg_slots) return EF_OK;
     if (cp.d_sg) cudaFree(cp.d_sg);
     const size_t el = p->desc.prec == EF_PREC_F32 ? 4 : 8;
-    cudaError_t e = cudaMalloc(&cp.d_sg, (size_t)slots * 2 * rows * (N + 1) * el);
+    cudaError_t e = cudaMalloc(&cp.d_sg, (size_t)slots * 2 * rows * N * el);
     if (e != cudaSuccess) { cp.d_sg = nullptr; cp.sg_slots = 0; return cuda_fail(e, "S/G workspace"); }
     cp.sg_slots = slots;
     return EF_OK;
@@ -588,6 +746,7 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
         a.diag = diag;
         a.status = p->d_status;
         a.counter = multi ? p->d_counters + ci : nullptr;
+        a.prefetch = cp.prefetch;
         e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, cs);
         if (e != cudaSuccess) return cuda_fail(e, "collide launch");
         if (multi) {
@@ -874,6 +1033,22 @@ ef_status ef_plan_set_graph(ef_plan_t p, int enable)
         cudaGraphExecDestroy(p->gexec);
         p->gexec = nullptr;
     }
+    return EF_OK;
+}
+
+ef_status ef_plan_class_info(ef_plan_t p, int i, int64_t out[8])
+{
+    if (!p || !out) return fail(EF_ERR_INVALID_ARG, "null plan or output");
+    if (i < 0 || i >= (int)p->classes.size()) return fail(EF_ERR_INVALID_ARG, "class index out of range");
+    const ClassPlan &cp = p->classes[i];
+    out[0] = cp.N;
+    out[1] = cp.ncells;
+    out[2] = cp.cluster;
+    out[3] = cp.tpb;
+    out[4] = cp.planes;
+    out[5] = cp.sg_global;
+    out[6] = cp.prefetch;
+    out[7] = (int64_t)(cp.tuned_ms * 1000.0);
     return EF_OK;
 }
 
