@@ -73,18 +73,97 @@ __device__ __forceinline__ void record_status(int *status, int code)
     if (status) atomicCAS(status, 0, code);
 }
 
-// shared-memory bytes of one CTA (must match the carve-up in the kernel)
+// shared-memory bytes of one CTA (must match the carve-up in the kernel).  Paired mode holds two
+// spectral slabs and G; single mode one slab and S, G.
 template <typename T, int D, int N>
-__host__ __device__ constexpr size_t smem_bytes_for(int planes, int sg_global)
+__host__ __device__ constexpr size_t smem_bytes_for(int planes, int sg_global, int paired)
 {
     constexpr int H = N / 2 + 1;
     constexpr int N1 = (D == 3) ? N : 1;
-    size_t is = (size_t)planes * N1 * H * sizeof(C2<T>);
-    size_t sg = sg_global ? 0 : 2 * (size_t)planes * N1 * N * sizeof(T);
+    size_t is = (size_t)(paired ? 2 : 1) * planes * N1 * H * sizeof(C2<T>);
+    size_t sg = sg_global ? 0 : (size_t)(paired ? 1 : 2) * planes * N1 * N * sizeof(T);
     sg = (sg + 15) / 16 * 16;
     size_t tw = (size_t)N * sizeof(C2<T>);
     size_t part = (32 + 1) * kDiag * sizeof(double);
-    return is + sg + tw + part + 16;        // + the cluster's current cell index
+    return is + sg + tw + part + 16;        // + the cluster's current cell index and a flag
+}
+
+// Per-cell diagnostics of one thread (FP64 sums of per-row FP32/FP64 partial sums).
+struct Diag {
+    double sum[kDiag];
+    double min_f, max_nu, min_out;
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int k = 0; k < kDiag; ++k) sum[k] = 0.0;
+        min_f = 1e300;
+        max_nu = -1e300;
+        min_out = 1e300;
+    }
+};
+
+// Final output of one real row: Q = q, written as Q (collide) or F + dt Q (Euler), with the
+// non-finite / positivity status checks and the diagnostic sums of the row.  nu (nullable) gives
+// the point-wise collision frequency for the positivity test; otherwise nu_big says whether
+// dt nu > 1 anywhere in this CTA's rows.
+template <typename T, int D, int N>
+__device__ __forceinline__ void emit_row(const CollideArgs &a, const T *Frow, T *Orow, const T (&q)[N], const T *nu,
+                                         bool nu_big, int64_t grow, Diag &dg)
+{
+    constexpr int N1 = (D == 3) ? N : 1;
+    const int jz = (int)(grow / N1) - N / 2;
+    const int jy = (D == 3) ? (int)(grow % N1) - N / 2 : 0;
+    T s_m = 0, s_mx = 0, s_e2 = 0, s_eta = 0, s_prod = 0;
+    T mn_f = Frow[0], mn_out = T(3.0e38);
+    bool bad = false, neg = false;
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+        const T f = Frow[n];
+        const T qv = q[n];
+        T outv;
+        if (a.out_mode == OUT_EULER) {
+            outv = f + T(a.dt) * qv;
+            const bool big = nu ? (T(a.dt) * nu[n] > T(1)) : nu_big;
+            if (outv < T(0) && big) neg = true;
+        } else {
+            outv = qv;
+        }
+        Orow[n] = outv;
+        if (!isfinite(outv)) bad = true;
+        if (a.diag) {
+            const T jx = T(n - N / 2);
+            s_m += f;
+            s_mx += f * jx;
+            s_e2 += f * jx * jx;
+            if (f > T(0)) {
+                const T lf = log_t<T>(f);
+                s_eta += f * lf;
+                s_prod += qv * lf;
+            }
+            mn_f = f < mn_f ? f : mn_f;
+            mn_out = outv < mn_out ? outv : mn_out;
+        }
+    }
+    if (bad) record_status(a.status, 7);     // EF_ERR_NOT_FINITE
+    if (neg) record_status(a.status, 6);     // EF_ERR_POSITIVITY
+    if (a.diag) {
+        // moments in array-axis order: [1] axis 0, [2] axis 1, [3] axis 2
+        const double m = (double)s_m;
+        dg.sum[0] += m;
+        if (D == 3) {
+            dg.sum[1] += m * jz;
+            dg.sum[2] += m * jy;
+            dg.sum[3] += (double)s_mx;
+        } else {
+            dg.sum[1] += m * jz;
+            dg.sum[2] += (double)s_mx;
+        }
+        dg.sum[4] += (double)s_e2 + m * ((double)jy * jy + (double)jz * jz);
+        dg.sum[5] += (double)s_eta;
+        dg.sum[6] += (double)s_prod;
+        dg.min_f = fmin(dg.min_f, (double)mn_f);
+        dg.min_out = fmin(dg.min_out, (double)mn_out);
+    }
 }
 
 template <typename T, int D, int N>
@@ -103,20 +182,25 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     Sync bar{cl, C};
     const int rows = P * N1;           // real rows owned by this CTA
     const int npairs = rows / 2;
+    const int nbuf = a.paired ? 2 : 1;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C2<T> *Is = reinterpret_cast<C2<T> *>(smem_raw);
-    size_t off = (size_t)P * NP * sizeof(C2<T>);
-    T *Sb, *Gb;
+    C2<T> *Is0 = reinterpret_cast<C2<T> *>(smem_raw);
+    C2<T> *Is1 = Is0 + (size_t)P * NP;                  // paired mode only
+    size_t off = (size_t)nbuf * P * NP * sizeof(C2<T>);
+    T *Sb = nullptr, *Gb;
     if (a.sg_global) {
         const int64_t slot = blockIdx.x;
         T *base = reinterpret_cast<T *>(a.sg_ws) + slot * (int64_t)2 * rows * N;
         Sb = base;
         Gb = base + (int64_t)rows * N;
     } else {
-        Sb = reinterpret_cast<T *>(smem_raw + off);
-        Gb = Sb + (size_t)rows * N;
-        off += 2 * (size_t)rows * N * sizeof(T);
+        if (!a.paired) {
+            Sb = reinterpret_cast<T *>(smem_raw + off);
+            off += (size_t)rows * N * sizeof(T);
+        }
+        Gb = reinterpret_cast<T *>(smem_raw + off);
+        off += (size_t)rows * N * sizeof(T);
         off = (off + 15) / 16 * 16;
     }
     C2<T> *tw = reinterpret_cast<C2<T> *>(smem_raw + off);
@@ -124,6 +208,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     double *part = reinterpret_cast<double *>(smem_raw + off);      // [32 warps + 1][kDiag]
     off += (32 + 1) * kDiag * sizeof(double);
     long long *s_cell = reinterpret_cast<long long *>(smem_raw + off);
+    int *s_nubig = reinterpret_cast<int *>(smem_raw + off + 8);
 
     for (int j = tid; j < N; j += nt) {
         T s, c;
@@ -153,10 +238,11 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
         const int64_t cglob = a.cell_id ? a.cell_id[c] : c;
         const T *F = reinterpret_cast<const T *>(a.F) + coff;
         T *Out = reinterpret_cast<T *>(a.Q) + coff;
+        if (tid == 0) *s_nubig = 0;
 
         // ---------------- F1: own planes, last axis real -> half complex (two rows per thread)
         // rows q and q + rows/2 per thread: consecutive threads touch consecutive rows, so the
-        // odd row strides (H complex, N + 1 reals) keep shared-memory accesses conflict free
+        // odd row stride (H complex) keeps shared-memory accesses conflict free
         for (int q = tid; q < npairs; q += nt) {
             const int r0 = q, r1 = q + npairs;
             const T *src0 = F + ((int64_t)rank * rows + r0) * N;
@@ -171,15 +257,15 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             r2c_pair<N, T>(x0, x1, X0, X1, tw);
 #pragma unroll
             for (int k = 0; k < H; ++k) {
-                Is[r0 * H + k] = X0[k];
-                Is[r1 * H + k] = X1[k];
+                Is0[r0 * H + k] = X0[k];
+                Is0[r1 * H + k] = X1[k];
             }
         }
         if constexpr (D == 3) {
             __syncthreads();
             for (int q = tid; q < P * H; q += nt) {            // axis 1, forward
                 const int zl = q / H, lx = q % H;
-                C2<T> *col = Is + (size_t)zl * NP + lx;
+                C2<T> *col = Is0 + (size_t)zl * NP + lx;
                 C2<T> v[N];
 #pragma unroll
                 for (int y = 0; y < N; ++y) v[y] = col[y * H];
@@ -196,7 +282,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 #pragma unroll
             for (int z = 0; z < N; ++z) {
                 const int owner = z / P, zl = z - owner * P;
-                const C2<T> *src = cl.map_shared_rank(Is, owner);
+                const C2<T> *src = cl.map_shared_rank(Is0, owner);
                 fh[z] = src[(size_t)zl * NP + pencil];
             }
             fft<N, -1, N>(fh, tw);
@@ -205,26 +291,28 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
         }
         bar.war();
 
-        // diagnostics accumulators (loss op only)
-        double dsum[kDiag];
-#pragma unroll
-        for (int k = 0; k < kDiag; ++k) dsum[k] = 0.0;
-        double dmin_f = 1e300, dmax_nu = -1e300, dmin_out = 1e300;
+        Diag dg;
+        dg.reset();
 
         for (int o = 0; o < a.nops; ++o) {
             const Op op = a.ops[o];
-            // ---------------- A: multiply, inverse along axis 0, scatter to owners
+            const bool pair = op.kind >= OP_PAIR;
+            // ---------------- A: multiply, inverse along axis 0, scatter to the owners' slabs
             if (has_pencil) {
-                const T *M = Mbase + (size_t)op.dir * N * NP + pencil;
-                C2<T> v[N];
+#pragma unroll 1
+                for (int b = 0; b < (pair ? 2 : 1); ++b) {
+                    const T *M = Mbase + (size_t)(b ? op.dir2 : op.dir) * N * NP + pencil;
+                    C2<T> *slab = b ? Is1 : Is0;
+                    C2<T> v[N];
 #pragma unroll
-                for (int z = 0; z < N; ++z) v[z] = cscale(fh[z], __ldg(M + (size_t)z * NP));
-                fft<N, 1, N>(v, tw);
+                    for (int z = 0; z < N; ++z) v[z] = cscale(fh[z], __ldg(M + (size_t)z * NP));
+                    fft<N, 1, N>(v, tw);
 #pragma unroll
-                for (int z = 0; z < N; ++z) {
-                    const int owner = z / P, zl = z - owner * P;
-                    C2<T> *dst = cl.map_shared_rank(Is, owner);
-                    dst[(size_t)zl * NP + pencil] = v[z];
+                    for (int z = 0; z < N; ++z) {
+                        const int owner = z / P, zl = z - owner * P;
+                        C2<T> *dst = cl.map_shared_rank(slab, owner);
+                        dst[(size_t)zl * NP + pencil] = v[z];
+                    }
                 }
                 if (a.prefetch && o + 1 < a.nops) {   // pull the next direction's multipliers towards L1
                     const T *Mn = Mbase + (size_t)a.ops[o + 1].dir * N * NP + pencil;
@@ -236,9 +324,12 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 
             // ---------------- B: local inverse passes and accumulation
             if constexpr (D == 3) {
-                for (int q = tid; q < P * H; q += nt) {        // axis 1, inverse
-                    const int zl = q / H, lx = q % H;
-                    C2<T> *col = Is + (size_t)zl * NP + lx;
+                const int ncol = (pair ? 2 : 1) * P * H;
+                for (int q = tid; q < ncol; q += nt) {          // axis 1, inverse
+                    const int b = q >= P * H;
+                    const int rem = q - b * P * H;
+                    const int zl = rem / H, lx = rem % H;
+                    C2<T> *col = (b ? Is1 : Is0) + (size_t)zl * NP + lx;
                     C2<T> v[N];
 #pragma unroll
                     for (int y = 0; y < N; ++y) v[y] = col[y * H];
@@ -248,103 +339,104 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                 }
                 __syncthreads();
             }
-            for (int q = tid; q < npairs; q += nt) {
-                const int r0 = q, r1 = q + npairs;
-                C2<T> X0[H], X1[H];
+            if (pair) {
+                // one row per thread, both directions at once: a_e (slab 0) and S_e (slab 1)
+                // come out of a single complex transform; G (column-major) += a_e S_e
+                const bool last = op.kind == OP_PAIR_LAST;
+                const bool big = *s_nubig != 0;
+                for (int r = tid; r < rows; r += nt) {
+                    C2<T> X0[H], X1[H];
 #pragma unroll
-                for (int k = 0; k < H; ++k) {
-                    X0[k] = Is[r0 * H + k];
-                    X1[k] = Is[r1 * H + k];
-                }
-                T y0[N], y1[N];
-                c2r_pair<N, T>(X0, X1, y0, y1, tw);
-                // S and G are stored column-major ([x][row]): consecutive threads own consecutive
-                // rows, so every access below is conflict free without padding
-                T *S0 = Sb + r0, *S1 = Sb + r1;
-                T *G0 = Gb + r0, *G1 = Gb + r1;
-                const T w = T(op.w);
-                switch (op.kind) {
-                case OP_S_SET:
-#pragma unroll
-                    for (int n = 0; n < N; ++n) { S0[n * rows] = w * y0[n]; S1[n * rows] = w * y1[n]; }
-                    break;
-                case OP_S_ADD:
-#pragma unroll
-                    for (int n = 0; n < N; ++n) { S0[n * rows] += w * y0[n]; S1[n * rows] += w * y1[n]; }
-                    break;
-                case OP_G_SET:
-#pragma unroll
-                    for (int n = 0; n < N; ++n) { G0[n * rows] = y0[n] * S0[n * rows]; G1[n * rows] = y1[n] * S1[n * rows]; }
-                    break;
-                case OP_G_ADD:
-#pragma unroll
-                    for (int n = 0; n < N; ++n) { G0[n * rows] += y0[n] * S0[n * rows]; G1[n * rows] += y1[n] * S1[n * rows]; }
-                    break;
-                default: {  // OP_LOSS: Q = G - F nu; output; diagnostics
-#pragma unroll
-                    for (int half = 0; half < 2; ++half) {
-                        const int64_t grow = (int64_t)rank * rows + (half ? r1 : r0);
-                        const T *nu = half ? y1 : y0;
-                        const T *G = half ? G1 : G0;
-                        const T *Frow = F + grow * N;
-                        T *Orow = Out + grow * N;
-                        // velocity indices of this row: grow = z * N1 + y (3D) or grow = z (2D)
-                        const int jz = (int)(grow / N1) - N / 2;
-                        const int jy = (D == 3) ? (int)(grow % N1) - N / 2 : 0;
-                        T s_m = 0, s_mx = 0, s_e2 = 0, s_eta = 0, s_prod = 0;
-                        T mn_f = Frow[0], mx_nu = nu[0], mn_out = T(3.0e38);
-                        bool bad = false, neg = false;
-#pragma unroll
-                        for (int n = 0; n < N; ++n) {
-                            const T f = Frow[n];
-                            const T qv = G[n * rows] - f * nu[n];
-                            T outv;
-                            if (a.out_mode == OUT_EULER) {
-                                outv = f + T(a.dt) * qv;
-                                if (outv < T(0) && T(a.dt) * nu[n] > T(1)) neg = true;
-                            } else {
-                                outv = qv;
-                            }
-                            Orow[n] = outv;
-                            if (!isfinite(outv)) bad = true;
-                            if (a.diag) {
-                                const T jx = T(n - N / 2);
-                                s_m += f;
-                                s_mx += f * jx;
-                                s_e2 += f * jx * jx;
-                                if (f > T(0)) {
-                                    const T lf = log_t<T>(f);
-                                    s_eta += f * lf;
-                                    s_prod += qv * lf;
-                                }
-                                mn_f = f < mn_f ? f : mn_f;
-                                mx_nu = nu[n] > mx_nu ? nu[n] : mx_nu;
-                                mn_out = outv < mn_out ? outv : mn_out;
-                            }
-                        }
-                        if (bad) record_status(a.status, 7);     // EF_ERR_NOT_FINITE
-                        if (neg) record_status(a.status, 6);     // EF_ERR_POSITIVITY
-                        if (a.diag) {
-                            // moments in array-axis order: [1] axis 0, [2] axis 1, [3] axis 2
-                            const double m = (double)s_m;
-                            dsum[0] += m;
-                            if (D == 3) {
-                                dsum[1] += m * jz;
-                                dsum[2] += m * jy;
-                                dsum[3] += (double)s_mx;
-                            } else {
-                                dsum[1] += m * jz;
-                                dsum[2] += (double)s_mx;
-                            }
-                            dsum[4] += (double)s_e2 + m * ((double)jy * jy + (double)jz * jz);
-                            dsum[5] += (double)s_eta;
-                            dsum[6] += (double)s_prod;
-                            dmin_f = fmin(dmin_f, (double)mn_f);
-                            dmax_nu = fmax(dmax_nu, (double)mx_nu);
-                            dmin_out = fmin(dmin_out, (double)mn_out);
-                        }
+                    for (int k = 0; k < H; ++k) {
+                        X0[k] = Is0[r * H + k];
+                        X1[k] = Is1[r * H + k];
                     }
-                } break;
+                    T ya[N], yb[N];
+                    c2r_pair<N, T>(X0, X1, ya, yb, tw);
+                    T *Gr = Gb + r;
+                    if (!last) {
+#pragma unroll
+                        for (int n = 0; n < N; ++n) Gr[n * rows] += ya[n] * yb[n];
+                    } else {
+                        T qv[N];
+#pragma unroll
+                        for (int n = 0; n < N; ++n) qv[n] = Gr[n * rows] + ya[n] * yb[n];
+                        const int64_t grow = (int64_t)rank * rows + r;
+                        emit_row<T, D, N>(a, F + grow * N, Out + grow * N, qv, nullptr, big, grow, dg);
+                    }
+                }
+            } else {
+                for (int q = tid; q < npairs; q += nt) {
+                    const int r0 = q, r1 = q + npairs;
+                    C2<T> X0[H], X1[H];
+#pragma unroll
+                    for (int k = 0; k < H; ++k) {
+                        X0[k] = Is0[r0 * H + k];
+                        X1[k] = Is0[r1 * H + k];
+                    }
+                    T y0[N], y1[N];
+                    c2r_pair<N, T>(X0, X1, y0, y1, tw);
+                    // S and G are stored column-major ([x][row]): consecutive threads own
+                    // consecutive rows, so every access below is conflict free without padding
+                    T *S0 = Sb + r0, *S1 = Sb + r1;
+                    T *G0 = Gb + r0, *G1 = Gb + r1;
+                    const T w = T(op.w);
+                    switch (op.kind) {
+                    case OP_S_SET:
+#pragma unroll
+                        for (int n = 0; n < N; ++n) { S0[n * rows] = w * y0[n]; S1[n * rows] = w * y1[n]; }
+                        break;
+                    case OP_S_ADD:
+#pragma unroll
+                        for (int n = 0; n < N; ++n) { S0[n * rows] += w * y0[n]; S1[n * rows] += w * y1[n]; }
+                        break;
+                    case OP_G_SET:
+#pragma unroll
+                        for (int n = 0; n < N; ++n) { G0[n * rows] = y0[n] * S0[n * rows]; G1[n * rows] = y1[n] * S1[n * rows]; }
+                        break;
+                    case OP_G_ADD:
+#pragma unroll
+                        for (int n = 0; n < N; ++n) { G0[n * rows] += y0[n] * S0[n * rows]; G1[n * rows] += y1[n] * S1[n * rows]; }
+                        break;
+                    case OP_NU_INIT: {          // paired mode, first pass: G = -F nu
+                        bool big = false;
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            const int r = half ? r1 : r0;
+                            const T *nu = half ? y1 : y0;
+                            const T *Frow = F + ((int64_t)rank * rows + r) * N;
+                            T *Gr = Gb + r;
+                            T mx = nu[0];
+#pragma unroll
+                            for (int n = 0; n < N; ++n) {
+                                Gr[n * rows] = -Frow[n] * nu[n];
+                                mx = nu[n] > mx ? nu[n] : mx;
+                                if (T(a.dt) * nu[n] > T(1)) big = true;
+                            }
+                            dg.max_nu = fmax(dg.max_nu, (double)mx);
+                        }
+                        if (big && a.out_mode == OUT_EULER) *s_nubig = 1;
+                    } break;
+                    default: {  // OP_LOSS (single mode, last): Q = G - F nu; output; diagnostics
+#pragma unroll
+                        for (int half = 0; half < 2; ++half) {
+                            const int r = half ? r1 : r0;
+                            const T *nu = half ? y1 : y0;
+                            const int64_t grow = (int64_t)rank * rows + r;
+                            const T *Frow = F + grow * N;
+                            T *Gr = Gb + r;
+                            T qv[N];
+                            T mx = nu[0];
+#pragma unroll
+                            for (int n = 0; n < N; ++n) {
+                                qv[n] = Gr[n * rows] - Frow[n] * nu[n];
+                                mx = nu[n] > mx ? nu[n] : mx;
+                            }
+                            dg.max_nu = fmax(dg.max_nu, (double)mx);
+                            emit_row<T, D, N>(a, Frow, Out + grow * N, qv, nu, false, grow, dg);
+                        }
+                    } break;
+                    }
                 }
             }
             bar.war();
@@ -352,13 +444,13 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 
         // ---------------- per-cell FP64 reduction of the diagnostics
         if (a.diag) {
-            dsum[7] = dmin_f;
-            dsum[8] = dmax_nu;
-            dsum[9] = dmin_out;
+            dg.sum[7] = dg.min_f;
+            dg.sum[8] = dg.max_nu;
+            dg.sum[9] = dg.min_out;
             const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
 #pragma unroll
             for (int k = 0; k < kDiag; ++k) {
-                double v = dsum[k];
+                double v = dg.sum[k];
 #pragma unroll
                 for (int s = 16; s > 0; s >>= 1) {
                     const double u = __shfl_xor_sync(0xffffffffu, v, s);

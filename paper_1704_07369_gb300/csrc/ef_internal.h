@@ -5,18 +5,28 @@
 
 namespace ef {
 
-// One step of the per-cell direction loop.  Each op runs one inverse transform of the spectral
-// multiply M_dir(l) * Fhat(l) (Sec. 4.1, eq. fastAlg with the filter folded into M) and folds the
-// real-space result a(r) into the accumulators:
+// One step of the per-cell direction loop.  Each op runs the inverse transform of one spectral
+// multiply M_dir(l) * Fhat(l) (Sec. 4.1, eq. fastAlg with the filter folded into M), or of two
+// (dir, dir2) for the paired kinds, and folds the real-space results into the accumulators.
+// Single-slab mode (one shared-memory slab, S and G accumulators):
 //   OP_S_SET   S  = w a            OP_S_ADD  S += w a
 //   OP_G_SET   G  = a S            OP_G_ADD  G += a S
 //   OP_LOSS    nu = a;  Q = G - F nu   (the gain/loss split of Sec. 3.1.2, eq. def_A)
-enum OpKind : int { OP_S_SET = 0, OP_S_ADD = 1, OP_G_SET = 2, OP_G_ADD = 3, OP_LOSS = 4 };
+// Paired mode (two slabs, G only):
+//   OP_NU_INIT     nu = a;  G = -F nu       (first op)
+//   OP_PAIR        G += a b                 (a = dir, b = dir2)
+//   OP_PAIR_LAST   Q = G + a b; output      (last op)
+enum OpKind : int {
+    OP_S_SET = 0, OP_S_ADD = 1, OP_G_SET = 2, OP_G_ADD = 3, OP_LOSS = 4, OP_NU_INIT = 5,
+    OP_PAIR = 6, OP_PAIR_LAST = 7
+};
 
 struct Op {
     int dir;        // row of the multiplier table
     int kind;       // OpKind
     double w;       // weight (S ops)
+    int dir2;       // second row (paired kinds)
+    int pad;
 };
 
 enum OutMode : int { OUT_COLLIDE = 0, OUT_EULER = 1 };
@@ -45,6 +55,7 @@ struct CollideArgs {
     int *status;              // device status word
     unsigned long long *counter;  // nullable: dynamic cell queue (zeroed before the launch)
     int prefetch;             // 1: prefetch the next op's multipliers into L1
+    int paired;               // 1: two spectral slabs per CTA and the paired op kinds
 };
 
 // Multiplier table layout for one class: mult[dir][lz][p], p = ly * H + lx (3D) or p = lx (2D),

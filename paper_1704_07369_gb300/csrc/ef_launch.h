@@ -13,7 +13,7 @@ namespace ef {
 #define EF_DECLARE_VARIANT(SUF)                                                                      \
     bool collide_supported_##SUF(int N);                                                             \
     int collide_maxthreads_##SUF(int N);                                                             \
-    size_t collide_smem_##SUF(int N, int planes, int sg_global);                                     \
+    size_t collide_smem_##SUF(int N, int planes, int sg_global, int paired);                         \
     cudaError_t collide_setup_##SUF(int N, size_t smem, int cluster, int tpb, int *max_clusters);    \
     cudaError_t collide_launch_##SUF(int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, \
                                      cudaStream_t s);

@@ -240,13 +240,15 @@ int mode_of(int N, int i) { return i < N / 2 ? i : i - N; }
 struct ClassPlan {
     int N = 0;
     int64_t ncells = 0;                 // batched: cells of this size; uniform plan: 0
-    int cluster = 1, tpb = 32, planes = 0, sg_global = 0, prefetch = 1;
+    int cluster = 1, tpb = 32, planes = 0, sg_global = 0, prefetch = 1, paired = 0;
     double tuned_ms = 0.0;              // autotuner's best time (0 when not tuned)
     size_t smem = 0;
     int max_clusters = 0;
-    int ndir = 0, nops = 0;
+    int ndir = 0, nops = 0;              // op count of the active mode
+    int nops_single = 0, nops_paired = 0;
     void *d_mult = nullptr;
-    ef::Op *d_ops = nullptr;
+    ef::Op *d_ops = nullptr;             // active op list (points into one of the two below)
+    ef::Op *d_ops_single = nullptr, *d_ops_paired = nullptr;
     int64_t *d_cell_off = nullptr, *d_cell_id = nullptr;
     void *d_sg = nullptr;
     int64_t sg_slots = 0;
@@ -294,10 +296,11 @@ int maxthreads_for(int prec, int d, int N)
     return d == 3 ? ef::collide_maxthreads_f64_3d(N) : ef::collide_maxthreads_f64_2d(N);
 }
 
-size_t smem_for(int prec, int d, int N, int planes, int sg)
+size_t smem_for(int prec, int d, int N, int planes, int sg, int paired)
 {
-    if (prec == EF_PREC_F32) return d == 3 ? ef::collide_smem_f32_3d(N, planes, sg) : ef::collide_smem_f32_2d(N, planes, sg);
-    return d == 3 ? ef::collide_smem_f64_3d(N, planes, sg) : ef::collide_smem_f64_2d(N, planes, sg);
+    if (prec == EF_PREC_F32)
+        return d == 3 ? ef::collide_smem_f32_3d(N, planes, sg, paired) : ef::collide_smem_f32_2d(N, planes, sg, paired);
+    return d == 3 ? ef::collide_smem_f64_3d(N, planes, sg, paired) : ef::collide_smem_f64_2d(N, planes, sg, paired);
 }
 
 cudaError_t setup_for(int prec, int d, int N, size_t smem, int cl, int tpb, int *mc)
@@ -315,7 +318,7 @@ cudaError_t launch_for(int prec, int d, int N, const ef::CollideArgs &a, int gri
 }
 
 struct Shape {
-    int cluster, tpb, planes, sg_global;
+    int cluster, tpb, planes, sg_global, paired;
     size_t smem;
     int max_clusters;
 };
@@ -335,26 +338,28 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
     const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
     std::vector<Shape> out;
     for (int sg = 0; sg <= 1 && out.empty(); ++sg) {
-        for (int C : cands) {
-            if (N % C) continue;
-            const int planes = N / C;
-            const int rows = planes * N1;
-            if (rows % 2) continue;
-            const int need = std::max({(NP + C - 1) / C, rows / 2, d == 3 ? planes * H : 1});
-            const int tpb = std::max(64, (need + 31) / 32 * 32);
-            if (tpb > maxthreads_for(ds.prec, d, N)) continue;
-            if ((int64_t)C * tpb < NP) continue;
-            const size_t smem = smem_for(ds.prec, d, N, planes, sg);
-            if ((long)smem > smem_max) continue;
-            int mc = 0;
-            cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, &mc);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                why = cudaGetErrorString(e);
-                continue;
+        for (int paired = 1; paired >= 0; --paired) {
+            for (int C : cands) {
+                if (N % C) continue;
+                const int planes = N / C;
+                const int rows = planes * N1;
+                if (rows % 2) continue;
+                const int need = std::max({(NP + C - 1) / C, rows / 2, d == 3 ? planes * H : 1});
+                const int tpb = std::max(64, (need + 31) / 32 * 32);
+                if (tpb > maxthreads_for(ds.prec, d, N)) continue;
+                if ((int64_t)C * tpb < NP) continue;
+                const size_t smem = smem_for(ds.prec, d, N, planes, sg, paired);
+                if ((long)smem > smem_max) continue;
+                int mc = 0;
+                cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, &mc);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    why = cudaGetErrorString(e);
+                    continue;
+                }
+                if (mc <= 0) continue;
+                out.push_back(Shape{C, tpb, planes, sg, paired, smem, mc});
             }
-            if (mc <= 0) continue;
-            out.push_back(Shape{C, tpb, planes, sg, smem, mc});
         }
     }
     return out;
@@ -366,8 +371,11 @@ void apply_shape(ClassPlan &cp, const Shape &sh)
     cp.tpb = sh.tpb;
     cp.planes = sh.planes;
     cp.sg_global = sh.sg_global;
+    cp.paired = sh.paired;
     cp.smem = sh.smem;
     cp.max_clusters = sh.max_clusters;
+    cp.d_ops = sh.paired ? cp.d_ops_paired : cp.d_ops_single;
+    cp.nops = sh.paired ? cp.nops_paired : cp.nops_single;
 }
 
 std::string device_key()
@@ -390,7 +398,7 @@ std::string tune_key(const Desc &ds, int N)
     return buf;
 }
 
-bool cache_lookup(const std::string &key, int &C, int &tpb, int &sg, int &pf)
+bool cache_lookup(const std::string &key, int &C, int &tpb, int &sg, int &pf, int &pr)
 {
     const char *path = std::getenv("EF_AUTOTUNE_CACHE");
     if (!path) return false;
@@ -402,19 +410,19 @@ bool cache_lookup(const std::string &key, int &C, int &tpb, int &sg, int &pf)
         std::string ln(line);
         const size_t bar = ln.find('|');
         if (bar == std::string::npos || ln.substr(0, bar) != key) continue;
-        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d %d", &C, &tpb, &sg, &pf) == 4) found = true;
+        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d %d %d", &C, &tpb, &sg, &pf, &pr) == 5) found = true;
     }
     std::fclose(f);
     return found;
 }
 
-void cache_store(const std::string &key, int C, int tpb, int sg, int pf, double ms)
+void cache_store(const std::string &key, int C, int tpb, int sg, int pf, int pr, double ms)
 {
     const char *path = std::getenv("EF_AUTOTUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s|%d %d %d %d %.4f\n", key.c_str(), C, tpb, sg, pf, ms);
+    std::fprintf(f, "%s|%d %d %d %d %d %.4f\n", key.c_str(), C, tpb, sg, pf, pr, ms);
     std::fclose(f);
 }
 
@@ -434,10 +442,10 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     const bool tune = ncells_tune > 0 && !(env && env[0] == '0') && shapes.size() > 1;
     if (!tune) return EF_OK;
     const std::string key = tune_key(ds, cp.N);
-    int C = 0, tpb = 0, sg = 0, pf = 1;
-    if (cache_lookup(key, C, tpb, sg, pf)) {
+    int C = 0, tpb = 0, sg = 0, pf = 1, pr = 0;
+    if (cache_lookup(key, C, tpb, sg, pf, pr)) {
         for (const Shape &sh : shapes)
-            if (sh.cluster == C && sh.tpb == tpb && sh.sg_global == sg) {
+            if (sh.cluster == C && sh.tpb == tpb && sh.sg_global == sg && sh.paired == pr) {
                 apply_shape(cp, sh);
                 cp.prefetch = pf;
                 return EF_OK;
@@ -474,8 +482,9 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
             a.Q = Q;
             a.ncells = ncells_tune;
             a.mult = cp.d_mult;
-            a.ops = cp.d_ops;
-            a.nops = cp.nops;
+            a.ops = sh.paired ? cp.d_ops_paired : cp.d_ops_single;
+            a.nops = sh.paired ? cp.nops_paired : cp.nops_single;
+            a.paired = sh.paired;
             a.cluster = sh.cluster;
             a.planes = sh.planes;
             a.sg_global = sh.sg_global;
@@ -510,7 +519,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     apply_shape(cp, best_sh);
     cp.prefetch = best_pf;
     cp.tuned_ms = best;
-    cache_store(key, best_sh.cluster, best_sh.tpb, best_sh.sg_global, best_pf, best);
+    cache_store(key, best_sh.cluster, best_sh.tpb, best_sh.sg_global, best_pf, best_sh.paired, best);
     return EF_OK;
 }
 
@@ -585,23 +594,31 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
     double *loss = &out[(size_t)(2 * ne) * per];      // L(m) = sigma(m)^2 B_fast(m, m)
     for (int g = 0; g < ne; ++g)
         for (int64_t i = 0; i < per; ++i) loss[i] += out[(size_t)g * per + i] * out[(size_t)(ne + g) * per + i];
-    std::vector<ef::Op> ops;
+    // single-slab op list: S = a(Gamma_e); G (+)= a(M_e) S; ...; Q = G - F nu
+    std::vector<ef::Op> ops1, ops2;
     for (int g = 0; g < ne; ++g) {
-        ops.push_back(ef::Op{ne + g, ef::OP_S_SET, 1.0});
-        ops.push_back(ef::Op{g, g == 0 ? ef::OP_G_SET : ef::OP_G_ADD, 1.0});
+        ops1.push_back(ef::Op{ne + g, ef::OP_S_SET, 1.0, 0, 0});
+        ops1.push_back(ef::Op{g, g == 0 ? ef::OP_G_SET : ef::OP_G_ADD, 1.0, 0, 0});
     }
-    ops.push_back(ef::Op{2 * ne, ef::OP_LOSS, 1.0});
-    if ((int)ops.size() > ef::kMaxOps) return fail(EF_ERR_UNSUPPORTED, "too many spectral directions");
+    ops1.push_back(ef::Op{2 * ne, ef::OP_LOSS, 1.0, 0, 0});
+    // paired op list: G = -F nu; G += a(M_e) a(Gamma_e) for each e; the last pair writes Q
+    ops2.push_back(ef::Op{2 * ne, ef::OP_NU_INIT, 1.0, 0, 0});
+    for (int g = 0; g < ne; ++g)
+        ops2.push_back(ef::Op{g, g + 1 == ne ? ef::OP_PAIR_LAST : ef::OP_PAIR, 1.0, ne + g, 0});
+    if ((int)ops1.size() > ef::kMaxOps) return fail(EF_ERR_UNSUPPORTED, "too many spectral directions");
     tab.swap(out);
     cp.ndir = 2 * ne + 1;
-    cp.nops = (int)ops.size();
+    cp.nops_single = (int)ops1.size();
+    cp.nops_paired = (int)ops2.size();
 
     cudaError_t e = cudaSuccess;
     cp.d_mult = ds.prec == EF_PREC_F32 ? upload_table<float>(tab, e) : upload_table<double>(tab, e);
     if (e != cudaSuccess) return cuda_fail(e, "multiplier table");
-    e = cudaMalloc((void **)&cp.d_ops, ops.size() * sizeof(ef::Op));
+    e = cudaMalloc((void **)&cp.d_ops_single, ops1.size() * sizeof(ef::Op));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&cp.d_ops_paired, ops2.size() * sizeof(ef::Op));
     if (e != cudaSuccess) return cuda_fail(e, "op list");
-    e = cudaMemcpy(cp.d_ops, ops.data(), ops.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(cp.d_ops_single, ops1.data(), ops1.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cp.d_ops_paired, ops2.data(), ops2.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "op list copy");
     return choose_shape(ds, cp, cp.ncells > 0 ? std::min<int64_t>(cp.ncells, 512) : 0);
 }
@@ -626,7 +643,8 @@ void destroy_plan(ef_plan_s *p)
     if (!p) return;
     for (ClassPlan &cp : p->classes) {
         cudaFree(cp.d_mult);
-        cudaFree(cp.d_ops);
+        cudaFree(cp.d_ops_single);
+        cudaFree(cp.d_ops_paired);
         cudaFree(cp.d_cell_off);
         cudaFree(cp.d_cell_id);
         cudaFree(cp.d_sg);
@@ -747,6 +765,7 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
         a.status = p->d_status;
         a.counter = multi ? p->d_counters + ci : nullptr;
         a.prefetch = cp.prefetch;
+        a.paired = cp.paired;
         e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, cs);
         if (e != cudaSuccess) return cuda_fail(e, "collide launch");
         if (multi) {
