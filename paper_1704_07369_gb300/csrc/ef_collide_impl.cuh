@@ -166,6 +166,71 @@ __device__ __forceinline__ void emit_row(const CollideArgs &a, const T *Frow, T 
     }
 }
 
+// Stage-A scatter of one inverse-transformed axis-0 pencil into the owners' slabs.  For FP32,
+// lanes 2j and 2j+1 hold the adjacent pencils p, p+1 (p even); one shuffle per z pair lets each
+// lane write both pencils of one z as a single 16-byte store, halving the number of (mostly
+// remote, distributed shared memory) store transactions.
+template <typename T, int N, bool WIDE>
+__device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab, int P, int NP, int pencil,
+                                               cg::cluster_group &cl, unsigned mask)
+{
+    if constexpr (WIDE) {
+        const bool odd = pencil & 1;
+        const int pbase = pencil & ~1;
+#pragma unroll
+        for (int z0 = 0; z0 < N; z0 += 2) {
+            const C2<T> send = odd ? v[z0] : v[z0 + 1];
+            C2<T> recv;
+            recv.x = __shfl_xor_sync(mask, send.x, 1);
+            recv.y = __shfl_xor_sync(mask, send.y, 1);
+            const int z = odd ? z0 + 1 : z0;
+            const C2<T> lo = odd ? recv : v[z0];
+            const C2<T> hi = odd ? v[z0 + 1] : recv;
+            const int owner = z / P, zl = z - owner * P;
+            float4 *dst = reinterpret_cast<float4 *>(cl.map_shared_rank(slab, owner) + (size_t)zl * NP + pbase);
+            *dst = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+    } else {
+#pragma unroll
+        for (int z = 0; z < N; ++z) {
+            const int owner = z / P, zl = z - owner * P;
+            C2<T> *dst = cl.map_shared_rank(slab, owner);
+            dst[(size_t)zl * NP + pencil] = v[z];
+        }
+    }
+}
+
+// The matching gather (forward pass F2): 16-byte loads of both pencils of one z, one shuffle.
+template <typename T, int N, bool WIDE>
+__device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P, int NP, int pencil,
+                                              cg::cluster_group &cl, unsigned mask)
+{
+    if constexpr (WIDE) {
+        const bool odd = pencil & 1;
+        const int pbase = pencil & ~1;
+#pragma unroll
+        for (int z0 = 0; z0 < N; z0 += 2) {
+            const int z = odd ? z0 + 1 : z0;
+            const int owner = z / P, zl = z - owner * P;
+            const float4 w = *reinterpret_cast<const float4 *>(cl.map_shared_rank(slab, owner) + (size_t)zl * NP + pbase);
+            const C2<T> lo = C2<T>{w.x, w.y}, hi = C2<T>{w.z, w.w};
+            const C2<T> send = odd ? lo : hi;
+            C2<T> recv;
+            recv.x = __shfl_xor_sync(mask, send.x, 1);
+            recv.y = __shfl_xor_sync(mask, send.y, 1);
+            v[z0] = odd ? recv : lo;
+            v[z0 + 1] = odd ? hi : recv;
+        }
+    } else {
+#pragma unroll
+        for (int z = 0; z < N; ++z) {
+            const int owner = z / P, zl = z - owner * P;
+            const C2<T> *src = cl.map_shared_rank(slab, owner);
+            v[z] = src[(size_t)zl * NP + pencil];
+        }
+    }
+}
+
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const CollideArgs a)
 {
@@ -173,6 +238,9 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     constexpr int N1 = (D == 3) ? N : 1;
     constexpr int NP = N1 * H;         // spectral columns of one axis-0 plane = pencils
     constexpr int64_t CELL = (int64_t)N * N1 * N;
+    // 16-byte paired pencil stores need FP32 and an even pencil count (so that every slab row
+    // starts on a 16-byte boundary and lane pairs hold pencil pairs)
+    constexpr bool WIDE = sizeof(T) == 4 && NP % 2 == 0;
 
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
@@ -221,6 +289,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     const int64_t cid = blockIdx.x / C;
     const int pencil = rank * nt + tid;            // this thread's spectral column (stage A)
     const bool has_pencil = pencil < NP;
+    const unsigned pmask = __ballot_sync(0xffffffffu, has_pencil);   // pencil pairs are complete: NP, nt even
     const T scale = T(1) / T(CELL);
     const T *Mbase = reinterpret_cast<const T *>(a.mult);
 
@@ -279,12 +348,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
         // ---------------- F2: gather the axis-0 pencil and finish the forward transform
         C2<T> fh[N];
         if (has_pencil) {
-#pragma unroll
-            for (int z = 0; z < N; ++z) {
-                const int owner = z / P, zl = z - owner * P;
-                const C2<T> *src = cl.map_shared_rank(Is0, owner);
-                fh[z] = src[(size_t)zl * NP + pencil];
-            }
+            gather_pencil<T, N, WIDE>(fh, Is0, P, NP, pencil, cl, pmask);
             fft<N, -1, N>(fh, tw);
 #pragma unroll
             for (int z = 0; z < N; ++z) fh[z] = cscale(fh[z], scale);
@@ -307,12 +371,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 #pragma unroll
                     for (int z = 0; z < N; ++z) v[z] = cscale(fh[z], __ldg(M + (size_t)z * NP));
                     fft<N, 1, N>(v, tw);
-#pragma unroll
-                    for (int z = 0; z < N; ++z) {
-                        const int owner = z / P, zl = z - owner * P;
-                        C2<T> *dst = cl.map_shared_rank(slab, owner);
-                        dst[(size_t)zl * NP + pencil] = v[z];
-                    }
+                    scatter_pencil<T, N, WIDE>(v, slab, P, NP, pencil, cl, pmask);
                 }
                 if (a.prefetch && o + 1 < a.nops) {   // pull the next direction's multipliers towards L1
                     const T *Mn = Mbase + (size_t)a.ops[o + 1].dir * N * NP + pencil;

@@ -23,7 +23,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/ef.h"
+#include "ef.h"
 #include "ef_internal.h"
 #include "ef_launch.h"
 
@@ -437,7 +437,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     if (shapes.empty())
         return fail(EF_ERR_UNSUPPORTED, "no launch shape fits N=" + std::to_string(cp.N) + " on this device " + why);
     apply_shape(cp, shapes[0]);
-    cp.prefetch = 1;
+    cp.prefetch = 0;
     const char *env = std::getenv("EF_AUTOTUNE");
     const bool tune = ncells_tune > 0 && !(env && env[0] == '0') && shapes.size() > 1;
     if (!tune) return EF_OK;
@@ -465,7 +465,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best = 1e30;
     Shape best_sh = shapes[0];
-    int best_pf = 1;
+    int best_pf = 0;
     for (size_t i = 0; e == cudaSuccess && i < shapes.size(); ++i) {
         const Shape &sh = shapes[i];
         const int grid = (int)std::min<int64_t>(ncells_tune, sh.max_clusters);
