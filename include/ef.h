@@ -115,6 +115,24 @@ ef_status ef_collide(ef_plan_t plan, const void *F_dev, void *Q_dev, int64_t nce
 ef_status ef_euler_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, double *diag_dev,
                         int64_t ncells, ef_stream_t stream);
 
+/* ef_collide for callers that cannot allocate device memory when they evaluate the operator (a
+ * host framework whose allocator owns all device memory, a real-time loop or callback where an
+ * allocation may block or fail, code that must keep the device footprint fixed after start-up).
+ * The paper has no counterpart: this is a deployment variant of ef_collide, same arithmetic and
+ * same arguments, for a plan from ef_plan_create / ef_plan_create_ex (batched plans:
+ * EF_ERR_INVALID_ARG).  It allocates nothing and calls no allocating routine: its scratch (the
+ * cell-queue counter and the S/G accumulators of the clusters in flight) lives in one 16 MiB
+ * static device array that every GPU loading the library holds until the process exits.
+ *  - The first call on a device looks up that array's device address (cudaGetSymbolAddress);
+ *    make the first call on each device before any stream capture.
+ *  - All calls share the array, which keeps the last call's contents (the counter is cleared on
+ *    the given stream at the start of every call): calls that can overlap on the GPU, e.g. on
+ *    different streams, race and must be serialised by the caller.
+ *  - If one cell's cluster needs more scratch than the array holds (very large N in FP64), the
+ *    call returns EF_ERR_UNSUPPORTED with the sizes in ef_last_error(); otherwise the launch
+ *    uses as many clusters as fit and any ncells is accepted. */
+ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void *Q_dev, int64_t ncells, ef_stream_t stream);
+
 /* Moments and entropy of each cell (layout EF_DIAG_STRIDE, entries [0..7] and [9]; [8] = 0).
  * Q_dev may be null; then [6] = 0 and [9] = 0. */
 ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_dev, double *out_dev,

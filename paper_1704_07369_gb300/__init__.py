@@ -35,7 +35,8 @@ EF_DIAG_STRIDE = 10
 # every symbol include/ef.h declares
 SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
            "ef_collide", "ef_euler_step", "ef_moments_entropy", "ef_plan_status",
-           "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_status_string", "ef_last_error")
+           "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_collide_noalloc",
+           "ef_status_string", "ef_last_error")
 
 
 class EfError(RuntimeError):
@@ -73,6 +74,7 @@ def lib():
         L.ef_plan_create_batched.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_int), dbl, i32, i32, i32, pp]
         L.ef_plan_destroy.argtypes = [vp]
         L.ef_collide.argtypes = [vp, vp, vp, i64, vp]
+        L.ef_collide_noalloc.argtypes = [vp, vp, vp, i64, vp]
         L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
         L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
         L.ef_plan_status.argtypes = [vp, i32, i32]
@@ -140,6 +142,11 @@ def ef_plan_destroy(plan):
 
 def ef_collide(plan, F, Q, ncells, stream=None):
     _check(lib().ef_collide(plan, _ptr(F), _ptr(Q), int(ncells), _stream(stream)))
+
+
+def ef_collide_noalloc(plan, F, Q, ncells, stream=None):
+    """ef_collide without any device allocation (scratch in the library's static device array)."""
+    _check(lib().ef_collide_noalloc(plan, _ptr(F), _ptr(Q), int(ncells), _stream(stream)))
 
 
 def ef_euler_step(plan, F, dt, nsteps, diag, ncells, stream=None):

@@ -25,6 +25,23 @@ EF_DECLARE_VARIANT(f64_3d)
 
 #undef EF_DECLARE_VARIANT
 
+// Read-only view of a uniform plan's single size class, for entry points defined outside
+// ef_plan.cpp (ef_noalloc.cu).  Returns false for a null or batched plan.
+struct PlanView {
+    int prec, d, N;
+    int cluster, tpb, planes, paired, nops, max_clusters;
+    double L;
+    const void *mult;
+    const Op *ops;
+    int *status;
+    int device;
+};
+bool plan_view(const struct ef_plan_s *p, PlanView *out);
+size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired);
+cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
+                           cudaStream_t s);
+void set_last_error(const char *msg);
+
 // moments / entropy (ef_moments.cu)
 cudaError_t moments_launch(int prec, int d, const void *F, const void *Q, const int64_t *cell_off,
                            const int64_t *cell_N, int64_t ncells, int N_uniform, double twoL, double *out,

@@ -978,6 +978,44 @@ ef_status step(ef_plan_s *p, const void *F, void *Q, int64_t ncells, int mode, d
 
 }  // namespace
 
+namespace ef {
+
+bool plan_view(const ef_plan_s *p, PlanView *out)
+{
+    if (!p || !out || p->batched || p->classes.size() != 1) return false;
+    const ClassPlan &cp = p->classes[0];
+    out->prec = p->desc.prec;
+    out->d = p->desc.d;
+    out->N = cp.N;
+    out->cluster = cp.cluster;
+    out->tpb = cp.tpb;
+    out->planes = cp.planes;
+    out->paired = cp.paired;
+    out->nops = cp.nops;
+    out->max_clusters = cp.max_clusters;
+    out->L = p->desc.L;
+    out->mult = cp.d_mult;
+    out->ops = cp.d_ops;
+    out->status = p->d_status;
+    out->device = p->device;
+    return true;
+}
+
+size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired)
+{
+    return smem_for(prec, d, N, planes, sg_global, paired);
+}
+
+cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
+                           cudaStream_t s)
+{
+    return launch_for(prec, d, N, a, grid_clusters, tpb, smem, s);
+}
+
+void set_last_error(const char *msg) { g_last_error = msg; }
+
+}  // namespace ef
+
 extern "C" {
 
 ef_status ef_collide(ef_plan_t p, const void *F, void *Q, int64_t ncells, ef_stream_t stream)
