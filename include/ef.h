@@ -20,7 +20,7 @@
  *   loss term multiplies the grid value F_r (DVM form, eq. QCvr / eq. Qsr).
  * Memory: every F / Q / diag pointer is a DEVICE pointer owned by the caller, contiguous, of the
  *   plan's precision (float for EF_PREC_F32, double for EF_PREC_F64; diagnostics are always
- *   double).  The plan owns its tables, workspace and status word.  No entry point allocates
+ *   double); F and Q must start on a 16-byte boundary (EF_ERR_INVALID_ARG otherwise).  The plan owns its tables, workspace and status word.  No entry point allocates
  *   device memory, synchronises the device or blocks the host except ef_plan_create* /
  *   ef_plan_destroy and ef_plan_status(plan, 1).
  * Streams: operations are enqueued on the given CUDA stream (0 = legacy default stream) and return

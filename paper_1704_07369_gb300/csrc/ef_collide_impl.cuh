@@ -102,23 +102,66 @@ struct Diag {
     }
 };
 
+// Global row I/O: a row is N contiguous values starting on a 16-byte boundary (the caller's
+// buffers are 16-byte aligned and every cell and row offset is a multiple of 4 values), moved with
+// 16-byte vector accesses.
+template <typename T, int N>
+__device__ __forceinline__ void load_row(const T *src, T (&x)[N])
+{
+    if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) {
+            const float4 v = s4[i];
+            x[4 * i] = v.x; x[4 * i + 1] = v.y; x[4 * i + 2] = v.z; x[4 * i + 3] = v.w;
+        }
+    } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
+        const double2 *s2 = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            const double2 v = s2[i];
+            x[2 * i] = v.x; x[2 * i + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int n = 0; n < N; ++n) x[n] = src[n];
+    }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void store_row(T *dst, const T (&x)[N])
+{
+    if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) d4[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+    } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
+        double2 *d2 = reinterpret_cast<double2 *>(dst);
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) d2[i] = make_double2(x[2 * i], x[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int n = 0; n < N; ++n) dst[n] = x[n];
+    }
+}
+
 // Final output of one real row: Q = q, written as Q (collide) or F + dt Q (Euler), with the
 // non-finite / positivity status checks and the diagnostic sums of the row.  nu (nullable) gives
 // the point-wise collision frequency for the positivity test; otherwise nu_big says whether
 // dt nu > 1 anywhere in this CTA's rows.
 template <typename T, int D, int N>
-__device__ __forceinline__ void emit_row(const CollideArgs &a, const T *Frow, T *Orow, const T (&q)[N], const T *nu,
+__device__ __forceinline__ void emit_row(const CollideArgs &a, const T (&fr)[N], T *Orow, T (&q)[N], const T *nu,
                                          bool nu_big, int64_t grow, Diag &dg)
 {
     constexpr int N1 = (D == 3) ? N : 1;
     const int jz = (int)(grow / N1) - N / 2;
     const int jy = (D == 3) ? (int)(grow % N1) - N / 2 : 0;
     T s_m = 0, s_mx = 0, s_e2 = 0, s_eta = 0, s_prod = 0;
-    T mn_f = Frow[0], mn_out = T(3.0e38);
+    T mn_f = fr[0], mn_out = T(3.0e38);
     bool bad = false, neg = false;
 #pragma unroll
     for (int n = 0; n < N; ++n) {
-        const T f = Frow[n];
+        const T f = fr[n];
         const T qv = q[n];
         T outv;
         if (a.out_mode == OUT_EULER) {
@@ -128,7 +171,7 @@ __device__ __forceinline__ void emit_row(const CollideArgs &a, const T *Frow, T 
         } else {
             outv = qv;
         }
-        Orow[n] = outv;
+        q[n] = outv;
         if (!isfinite(outv)) bad = true;
         if (a.diag) {
             const T jx = T(n - N / 2);
@@ -144,6 +187,7 @@ __device__ __forceinline__ void emit_row(const CollideArgs &a, const T *Frow, T 
             mn_out = outv < mn_out ? outv : mn_out;
         }
     }
+    store_row<T, N>(Orow, q);
     if (bad) record_status(a.status, 7);     // EF_ERR_NOT_FINITE
     if (neg) record_status(a.status, 6);     // EF_ERR_POSITIVITY
     if (a.diag) {
@@ -317,11 +361,8 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             const T *src0 = F + ((int64_t)rank * rows + r0) * N;
             const T *src1 = F + ((int64_t)rank * rows + r1) * N;
             T x0[N], x1[N];
-#pragma unroll
-            for (int n = 0; n < N; ++n) {
-                x0[n] = src0[n];
-                x1[n] = src1[n];
-            }
+            load_row<T, N>(src0, x0);
+            load_row<T, N>(src1, x1);
             C2<T> X0[H], X1[H];
             r2c_pair<N, T>(x0, x1, X0, X1, tw);
 #pragma unroll
@@ -421,7 +462,9 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 #pragma unroll
                         for (int n = 0; n < N; ++n) qv[n] = Gr[n * rows] + ya[n] * yb[n];
                         const int64_t grow = (int64_t)rank * rows + r;
-                        emit_row<T, D, N>(a, F + grow * N, Out + grow * N, qv, nullptr, big, grow, dg);
+                        T fr[N];
+                        load_row<T, N>(F + grow * N, fr);
+                        emit_row<T, D, N>(a, fr, Out + grow * N, qv, nullptr, big, grow, dg);
                     }
                 }
             } else {
@@ -463,12 +506,13 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                         for (int half = 0; half < 2; ++half) {
                             const int r = half ? r1 : r0;
                             const T *nu = half ? y1 : y0;
-                            const T *Frow = F + ((int64_t)rank * rows + r) * N;
+                            T fr[N];
+                            load_row<T, N>(F + ((int64_t)rank * rows + r) * N, fr);
                             T *Gr = Gb + r;
                             T mx = nu[0];
 #pragma unroll
                             for (int n = 0; n < N; ++n) {
-                                Gr[n * rows] = -Frow[n] * nu[n];
+                                Gr[n * rows] = -fr[n] * nu[n];
                                 mx = nu[n] > mx ? nu[n] : mx;
                                 if (T(a.dt) * nu[n] > T(1)) big = true;
                             }
@@ -482,17 +526,18 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                             const int r = half ? r1 : r0;
                             const T *nu = half ? y1 : y0;
                             const int64_t grow = (int64_t)rank * rows + r;
-                            const T *Frow = F + grow * N;
+                            T fr[N];
+                            load_row<T, N>(F + grow * N, fr);
                             T *Gr = Gb + r;
                             T qv[N];
                             T mx = nu[0];
 #pragma unroll
                             for (int n = 0; n < N; ++n) {
-                                qv[n] = Gr[n * rows] - Frow[n] * nu[n];
+                                qv[n] = Gr[n * rows] - fr[n] * nu[n];
                                 mx = nu[n] > mx ? nu[n] : mx;
                             }
                             dg.max_nu = fmax(dg.max_nu, (double)mx);
-                            emit_row<T, D, N>(a, Frow, Out + grow * N, qv, nu, false, grow, dg);
+                            emit_row<T, D, N>(a, fr, Out + grow * N, qv, nu, false, grow, dg);
                         }
                     } break;
                     }

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -70,8 +71,8 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
         return EF_ERR_INVALID_ARG;
     }
     if (ncells == 0) return EF_OK;
-    if (!F_dev || !Q_dev || F_dev == Q_dev) {
-        ef::set_last_error("ef_collide_noalloc: null F or Q, or F == Q");
+    if (!F_dev || !Q_dev || F_dev == Q_dev || (((uintptr_t)F_dev | (uintptr_t)Q_dev) % 16)) {
+        ef::set_last_error("ef_collide_noalloc: null, equal or not 16-byte aligned F / Q");
         return EF_ERR_INVALID_ARG;
     }
     int dev = -1;

@@ -16,6 +16,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -1026,6 +1027,7 @@ ef_status ef_collide(ef_plan_t p, const void *F, void *Q, int64_t ncells, ef_str
     if (ncells == 0) return EF_OK;
     if (!F || !Q) return fail(EF_ERR_INVALID_ARG, "null F or Q");
     if (F == Q) return fail(EF_ERR_INVALID_ARG, "F and Q must not overlap");
+    if (((uintptr_t)F | (uintptr_t)Q) % 16) return fail(EF_ERR_INVALID_ARG, "F and Q must be 16-byte aligned");
     ef_status st = check_device(p);
     if (st != EF_OK) return st;
     return step(p, F, Q, ncells, ef::OUT_COLLIDE, 0.0, nullptr, (cudaStream_t)stream);
@@ -1039,6 +1041,7 @@ ef_status ef_euler_step(ef_plan_t p, void *F, double dt, int nsteps, double *dia
     if (p->batched && ncells != p->ncells) return fail(EF_ERR_INVALID_ARG, "ncells differs from the batched plan");
     if (nsteps == 0 || ncells == 0) return EF_OK;
     if (!F) return fail(EF_ERR_INVALID_ARG, "null F");
+    if ((uintptr_t)F % 16) return fail(EF_ERR_INVALID_ARG, "F must be 16-byte aligned");
     ef_status st = check_device(p);
     if (st != EF_OK) return st;
     for (int k = 0; k < nsteps; ++k) {
