@@ -133,6 +133,87 @@ ef_status ef_euler_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, doub
  *    uses as many clusters as fit and any ncells is accepted. */
 ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void *Q_dev, int64_t ncells, ef_stream_t stream);
 
+/* Low-mode features of each cell: the discrete Fourier coefficients Fh_k = N^{-d} sum F E_{-k}
+ * (eq. DFT, index-origin convention of the library's FFTs) at the modes |k| <= EF_FEATURE_K in the
+ * canonical half space (k_last > 0; or k_last = 0 and k_1 > 0; or k_last = k_1 = 0 and k_0 >= 0),
+ * listed in lexicographic order of k.  feat_dev (FP32, caller-owned) receives EF_FEATURE_STRIDE
+ * floats per cell: (re, im) of each mode, then zeros are NOT written (the caller clears the pad).
+ * 3D, K = 6: 463 modes = 925 real degrees of freedom.  With log_input = 1 the transform is taken
+ * of ln(max(F, 1e-30)) instead (used for the entropy-production gate of the surrogate).  Needs
+ * N/2 > EF_FEATURE_K. */
+#define EF_FEATURE_K 6
+#define EF_FEATURE_STRIDE 928
+ef_status ef_features(ef_plan_t plan, const void *F_dev, float *feat_dev, int64_t ncells, int log_input,
+                      ef_stream_t stream);
+
+/* ---------------------------------------------------------------- learned surrogate ---------
+ * A multilayer perceptron with bf16 weights and activations and FP32 accumulation, trained and run
+ * by the library's own tensor-core kernels.  The paper has no counterpart; it serves the
+ * surrogate path that maps a cell's low Fourier modes of F to those of Q^sigma.
+ *
+ * Layers: x -> relu(W_0 x + b_0) -> ... -> W_{L-1} h + b_{L-1} (nlayers = L weight matrices, hidden
+ * width nhidden, no activation on the output).  Feature widths are padded to multiples of 64
+ * inside; batches are multiples of 64.  Parameters are FP32 master copies (Adam, beta = 0.9 /
+ * 0.999, eps = 1e-8) with bf16 working copies.  All pointers are device pointers unless stated. */
+typedef struct ef_mlp_s *ef_mlp_t;
+
+/* He-normal initialisation from a seeded 64-bit Mersenne twister (host), zero biases. */
+ef_status ef_mlp_create(int nin, int nhidden, int nlayers, int nout, int64_t max_batch, uint64_t seed, ef_mlp_t *out);
+ef_status ef_mlp_destroy(ef_mlp_t mlp);
+
+/* info: [0] nin, [1] nhidden, [2] nlayers, [3] nout, [4] number of FP32 parameters (padded layout:
+ * per layer W[out_p][in_p] then b[out_p]), [5] padded nin, [6] padded nout, [7] max batch. */
+ef_status ef_mlp_info(ef_mlp_t mlp, int64_t info[8]);
+
+/* Copy the FP32 parameters to (set = 0) or from (set = 1) a HOST buffer of info[4] floats. */
+ef_status ef_mlp_params(ef_mlp_t mlp, float *host, int set);
+
+/* Y[b][0..padded nout) = mlp(X[b][0..nin)) for b < batch; X row stride ldx >= nin, Y row stride ldy
+ * >= padded nout and even.  batch a multiple of 64, <= max_batch. */
+ef_status ef_mlp_forward(ef_mlp_t mlp, const float *X, int ldx, float *Y, int ldy, int64_t batch, ef_stream_t stream);
+
+/* Mean squared error against T (row stride ldt >= nout) over the nout outputs, each weighted by
+ * wmask[j] (nullable = 1): loss_dev[0] = sum_b sum_j w_j (y - t)^2 / (batch nout); gradients of the
+ * loss into the MLP's gradient buffer and, if grad_dev is not null, copied there (info[4] floats). */
+ef_status ef_mlp_grad(ef_mlp_t mlp, const float *X, int ldx, const float *T, int ldt, const float *wmask,
+                      int64_t batch, float *loss_dev, float *grad_dev, ef_stream_t stream);
+
+/* ef_mlp_grad followed by one Adam step with learning rate lr. */
+ef_status ef_mlp_train_step(ef_mlp_t mlp, const float *X, int ldx, const float *T, int ldt, const float *wmask,
+                            int64_t batch, float lr, float *loss_dev, ef_stream_t stream);
+
+/* The surrogate path (config: learned map from F's low modes to Q^sigma's low modes).  Built on a
+ * uniform plan (whose ef_features define the band) and an MLP with nin = nout = 2 x (feature modes).
+ * Scratch for max_batch cells (features, activations, the fallback list and a full-size Q buffer
+ * for fallback cells) is allocated here, so inference allocates nothing. */
+typedef struct ef_surrogate_s *ef_surrogate_t;
+ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, ef_surrogate_t *out);
+ef_status ef_surrogate_destroy(ef_surrogate_t sur);
+
+/* Fit the column statistics (mean, std) of x = Fh / m and y = Qh / m^2 (m = Fh_0, the zero mode)
+ * from n training samples of features (EF_FEATURE_STRIDE floats each, from ef_features of F and of
+ * Q^sigma[F]); the operator is quadratic, so this normalisation is exact in the density. */
+ef_status ef_surrogate_fit_stats(ef_surrogate_t sur, const float *featF, const float *featQ, int64_t n,
+                                 ef_stream_t stream);
+
+/* Normalised MLP inputs X (and targets Y, if featQ and Y are not null), EF_FEATURE_STRIDE per row. */
+ef_status ef_surrogate_normalize(ef_surrogate_t sur, const float *featF, const float *featQ, float *X, float *Y,
+                                 int64_t n, ef_stream_t stream);
+
+/* Copy the statistics (4 x EF_FEATURE_STRIDE floats: mu, s, nu, t) to (set = 0) / from (set = 1) the host. */
+ef_status ef_surrogate_stats(ef_surrogate_t sur, float *host, int set);
+
+/* Band of Q^sigma for ncells cells (multiple of 64, <= max_batch): qfeat (EF_FEATURE_STRIDE per
+ * cell, ef_features layout) receives the prediction, or the plain operator's band where the
+ * prediction is not trusted.  flags (int per cell): 1 = a gate failed (non-finite, input outside
+ * +-8 training standard deviations, or positive band entropy production sum Q ln F, which the
+ * discrete H-theorem forbids), 2 = audited (a seeded fraction audit_fraction of cells, drawn from
+ * seed), 4 = audited and the prediction missed the plain band by more than tol in relative L2,
+ * 8 = plain result used, 16 = fell back because an audited cell of the batch missed tol (then the
+ * whole batch uses the plain operator).  Everything stays on the device: no host synchronisation. */
+ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat, int *flags, int64_t ncells,
+                             float audit_fraction, uint64_t seed, float tol, ef_stream_t stream);
+
 /* Moments and entropy of each cell (layout EF_DIAG_STRIDE, entries [0..7] and [9]; [8] = 0).
  * Q_dev may be null; then [6] = 0 and [9] = 0. */
 ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_dev, double *out_dev,

@@ -36,7 +36,13 @@ EF_DIAG_STRIDE = 10
 SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
            "ef_collide", "ef_euler_step", "ef_moments_entropy", "ef_plan_status",
            "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_collide_noalloc",
+           "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_params",
+           "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
+           "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
+           "ef_surrogate_stats", "ef_surrogate_infer",
            "ef_status_string", "ef_last_error")
+EF_FEATURE_K = 6
+EF_FEATURE_STRIDE = 928
 
 
 class EfError(RuntimeError):
@@ -75,6 +81,20 @@ def lib():
         L.ef_plan_destroy.argtypes = [vp]
         L.ef_collide.argtypes = [vp, vp, vp, i64, vp]
         L.ef_collide_noalloc.argtypes = [vp, vp, vp, i64, vp]
+        L.ef_features.argtypes = [vp, vp, vp, i64, i32, vp]
+        L.ef_mlp_create.argtypes = [i32, i32, i32, i32, i64, ctypes.c_uint64, pp]
+        L.ef_mlp_destroy.argtypes = [vp]
+        L.ef_mlp_info.argtypes = [vp, ctypes.POINTER(i64)]
+        L.ef_mlp_params.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+        L.ef_mlp_forward.argtypes = [vp, vp, i32, vp, i32, i64, vp]
+        L.ef_mlp_grad.argtypes = [vp, vp, i32, vp, i32, vp, i64, vp, vp, vp]
+        L.ef_mlp_train_step.argtypes = [vp, vp, i32, vp, i32, vp, i64, ctypes.c_float, vp, vp]
+        L.ef_surrogate_create.argtypes = [vp, vp, i64, pp]
+        L.ef_surrogate_destroy.argtypes = [vp]
+        L.ef_surrogate_fit_stats.argtypes = [vp, vp, vp, i64, vp]
+        L.ef_surrogate_normalize.argtypes = [vp, vp, vp, vp, vp, i64, vp]
+        L.ef_surrogate_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+        L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
         L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
         L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
         L.ef_plan_status.argtypes = [vp, i32, i32]
@@ -147,6 +167,107 @@ def ef_collide(plan, F, Q, ncells, stream=None):
 def ef_collide_noalloc(plan, F, Q, ncells, stream=None):
     """ef_collide without any device allocation (scratch in the library's static device array)."""
     _check(lib().ef_collide_noalloc(plan, _ptr(F), _ptr(Q), int(ncells), _stream(stream)))
+
+
+def ef_features(plan, F, feat, ncells, log_input=0, stream=None):
+    _check(lib().ef_features(plan, _ptr(F), _ptr(feat), int(ncells), int(log_input), _stream(stream)))
+
+
+class MLP:
+    """Owning wrapper of an ``ef_mlp_t`` (bf16 tensor-core MLP with FP32 master weights)."""
+
+    def __init__(self, nin, nhidden, nlayers, nout, max_batch, seed=0):
+        self.handle = ctypes.c_void_p()
+        _check(lib().ef_mlp_create(nin, nhidden, nlayers, nout, int(max_batch), int(seed), ctypes.byref(self.handle)))
+        info = (ctypes.c_int64 * 8)()
+        _check(lib().ef_mlp_info(self.handle, info))
+        self.nin, self.nhidden, self.nlayers, self.nout, self.nparams, self.ninp, self.noutp, self.max_batch = list(info)
+
+    def params(self):
+        import numpy as np
+        out = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().ef_mlp_params(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0))
+        return out
+
+    def set_params(self, host):
+        import numpy as np
+        host = np.ascontiguousarray(host, dtype=np.float32)
+        _check(lib().ef_mlp_params(self.handle, host.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    def forward(self, X, Y, batch, stream=None):
+        _check(lib().ef_mlp_forward(self.handle, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), int(batch), _stream(stream)))
+
+    def grad(self, X, T, batch, loss, grad=None, wmask=None, stream=None):
+        _check(lib().ef_mlp_grad(self.handle, _ptr(X), X.stride(0), _ptr(T), T.stride(0), _ptr(wmask), int(batch),
+                                 _ptr(loss), _ptr(grad), _stream(stream)))
+
+    def train_step(self, X, T, batch, lr, loss, wmask=None, stream=None):
+        _check(lib().ef_mlp_train_step(self.handle, _ptr(X), X.stride(0), _ptr(T), T.stride(0), _ptr(wmask),
+                                       int(batch), float(lr), _ptr(loss), _stream(stream)))
+
+    def layout(self):
+        """[(W offset, out_p, in_p, b offset)] of the padded FP32 parameter vector."""
+        din = [self.ninp] + [(self.nhidden + 63) // 64 * 64] * (self.nlayers - 1)
+        dout = [(self.nhidden + 63) // 64 * 64] * (self.nlayers - 1) + [self.noutp]
+        out, off = [], 0
+        for i, o in zip(din, dout):
+            out.append((off, o, i, off + o * i))
+            off += o * i + o
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ef_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """Owning wrapper of an ``ef_surrogate_t`` (keeps its plan and MLP alive)."""
+
+    def __init__(self, plan, mlp, max_batch):
+        self.plan, self.mlp = plan, mlp
+        self.handle = ctypes.c_void_p()
+        _check(lib().ef_surrogate_create(plan.handle, mlp.handle, int(max_batch), ctypes.byref(self.handle)))
+        self.max_batch = int(max_batch)
+
+    def fit_stats(self, featF, featQ, n, stream=None):
+        _check(lib().ef_surrogate_fit_stats(self.handle, _ptr(featF), _ptr(featQ), int(n), _stream(stream)))
+
+    def normalize(self, featF, featQ, X, Y, n, stream=None):
+        _check(lib().ef_surrogate_normalize(self.handle, _ptr(featF), _ptr(featQ), _ptr(X), _ptr(Y), int(n),
+                                            _stream(stream)))
+
+    def stats(self):
+        import numpy as np
+        out = np.zeros(4 * EF_FEATURE_STRIDE, dtype=np.float32)
+        _check(lib().ef_surrogate_stats(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0))
+        return out
+
+    def set_stats(self, host):
+        import numpy as np
+        host = np.ascontiguousarray(host, dtype=np.float32)
+        _check(lib().ef_surrogate_stats(self.handle, host.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    def infer(self, F, qfeat, flags, ncells, audit_fraction=0.05, seed=0, tol=1e-3, stream=None):
+        _check(lib().ef_surrogate_infer(self.handle, _ptr(F), _ptr(qfeat), _ptr(flags), int(ncells),
+                                        float(audit_fraction), int(seed), float(tol), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ef_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ef_euler_step(plan, F, dt, nsteps, diag, ncells, stream=None):

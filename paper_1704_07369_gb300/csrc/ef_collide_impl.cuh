@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
     const T scale = T(1) / T(CELL);
     const T *Mbase = reinterpret_cast<const T *>(a.mult);
 
+    const int64_t ncells = a.dev_ncells ? (int64_t)*a.dev_ncells : a.ncells;
     int64_t c = cid - nclusters;
     for (;;) {
         if (a.counter) {            // dynamic: the cluster takes the next unclaimed cell
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
         } else {
             c += nclusters;
         }
-        if (c >= a.ncells) break;
+        if (c >= ncells) break;
         const int64_t coff = a.cell_off ? a.cell_off[c] : c * CELL;
         const int64_t cglob = a.cell_id ? a.cell_id[c] : c;
         const T *F = reinterpret_cast<const T *>(a.F) + coff;
@@ -363,6 +364,13 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             T x0[N], x1[N];
             load_row<T, N>(src0, x0);
             load_row<T, N>(src1, x1);
+            if (a.log_input) {
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    x0[n] = log_t<T>(x0[n] > T(1e-30) ? x0[n] : T(1e-30));
+                    x1[n] = log_t<T>(x1[n] > T(1e-30) ? x1[n] : T(1e-30));
+                }
+            }
             C2<T> X0[H], X1[H];
             r2c_pair<N, T>(x0, x1, X0, X1, tw);
 #pragma unroll
@@ -395,6 +403,20 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             for (int z = 0; z < N; ++z) fh[z] = cscale(fh[z], scale);
         }
         bar.war();
+
+        if (a.out_mode == OUT_FEATURES) {      // low-mode features only (surrogate input / target)
+            if (has_pencil) {
+#pragma unroll
+                for (int z = 0; z < N; ++z) {
+                    const int j = a.fidx[z * NP + pencil];
+                    if (j >= 0) {
+                        a.feat[cglob * a.fstride + 2 * j] = (float)fh[z].x;
+                        a.feat[cglob * a.fstride + 2 * j + 1] = (float)fh[z].y;
+                    }
+                }
+            }
+            continue;
+        }
 
         Diag dg;
         dg.reset();

@@ -29,7 +29,7 @@ struct Op {
     int pad;
 };
 
-enum OutMode : int { OUT_COLLIDE = 0, OUT_EULER = 1 };
+enum OutMode : int { OUT_COLLIDE = 0, OUT_EULER = 1, OUT_FEATURES = 2 };
 
 constexpr int kMaxOps = 512;
 constexpr int kDiag = 10;
@@ -56,6 +56,12 @@ struct CollideArgs {
     unsigned long long *counter;  // nullable: dynamic cell queue (zeroed before the launch)
     int prefetch;             // 1: prefetch the next op's multipliers into L1
     int paired;               // 1: two spectral slabs per CTA and the paired op kinds
+    // OUT_FEATURES: write the forward transform at the listed modes instead of colliding
+    float *feat;              // [cell_id][fstride] (re, im) pairs
+    const int *fidx;          // [N * NP]: feature slot of spectral element (lz, p), or -1
+    int fstride;
+    int log_input;            // 1: transform ln(max(F, tiny)) instead of F
+    const long long *dev_ncells;  // nullable: cell count read from device memory at kernel start
 };
 
 // Multiplier table layout for one class: mult[dir][lz][p], p = ly * H + lx (3D) or p = lx (2D),

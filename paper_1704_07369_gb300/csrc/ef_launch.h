@@ -29,10 +29,12 @@ EF_DECLARE_VARIANT(f64_3d)
 // ef_plan.cpp (ef_noalloc.cu).  Returns false for a null or batched plan.
 struct PlanView {
     int prec, d, N;
-    int cluster, tpb, planes, paired, nops, max_clusters;
+    int cluster, tpb, planes, paired, nops, max_clusters, sg_global, nfeat;
+    size_t smem;
     double L;
     const void *mult;
     const Op *ops;
+    const int *fidx;
     int *status;
     int device;
 };

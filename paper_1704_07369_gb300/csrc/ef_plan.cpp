@@ -246,10 +246,12 @@ struct ClassPlan {
     size_t smem = 0;
     int max_clusters = 0;
     int ndir = 0, nops = 0;              // op count of the active mode
+    int nfeat = 0;                       // complex feature modes
     int nops_single = 0, nops_paired = 0;
     void *d_mult = nullptr;
     ef::Op *d_ops = nullptr;             // active op list (points into one of the two below)
     ef::Op *d_ops_single = nullptr, *d_ops_paired = nullptr;
+    int *d_fidx = nullptr;               // feature slot per spectral element (|k| <= EF_FEATURE_K)
     int64_t *d_cell_off = nullptr, *d_cell_id = nullptr;
     void *d_sg = nullptr;
     int64_t sg_slots = 0;
@@ -621,6 +623,34 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
     e = cudaMemcpy(cp.d_ops_single, ops1.data(), ops1.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cp.d_ops_paired, ops2.data(), ops2.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "op list copy");
+    // feature slots: modes with |k| <= EF_FEATURE_K in the canonical half space (k2 > 0, or
+    // k2 = 0 and k1 > 0, or k2 = k1 = 0 and k0 >= 0), in lexicographic order of (k0, k1, k2)
+    {
+        std::vector<int> fidx((size_t)per, -1);
+        const int K = EF_FEATURE_K;
+        int slot = 0;
+        for (int k0 = -K; k0 <= K; ++k0)
+            for (int k1 = -K; k1 <= K; ++k1)
+                for (int k2 = 0; k2 <= K; ++k2) {
+                    if (k0 * k0 + k1 * k1 + k2 * k2 > K * K) continue;
+                    if (!(k2 > 0 || (k2 == 0 && (k1 > 0 || (k1 == 0 && k0 >= 0))))) continue;
+                    if (d == 2 && k2 != 0) continue;
+                    if (N / 2 <= K) continue;          // grid too small for the band
+                    const int lz = (k0 + N) % N;
+                    int p;
+                    if (d == 3) {
+                        p = ((k1 + N) % N) * H + k2;
+                    } else {                           // 2D: axis 0 = k0, half axis = k1
+                        if (k1 < 0) continue;
+                        p = k1;
+                    }
+                    fidx[(size_t)lz * NP + p] = slot++;
+                }
+        e = cudaMalloc((void **)&cp.d_fidx, fidx.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(cp.d_fidx, fidx.data(), fidx.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "feature table");
+        cp.nfeat = slot;
+    }
     return choose_shape(ds, cp, cp.ncells > 0 ? std::min<int64_t>(cp.ncells, 512) : 0);
 }
 
@@ -645,6 +675,7 @@ void destroy_plan(ef_plan_s *p)
     for (ClassPlan &cp : p->classes) {
         cudaFree(cp.d_mult);
         cudaFree(cp.d_ops_single);
+        cudaFree(cp.d_fidx);
         cudaFree(cp.d_ops_paired);
         cudaFree(cp.d_cell_off);
         cudaFree(cp.d_cell_id);
@@ -994,6 +1025,10 @@ bool plan_view(const ef_plan_s *p, PlanView *out)
     out->paired = cp.paired;
     out->nops = cp.nops;
     out->max_clusters = cp.max_clusters;
+    out->sg_global = cp.sg_global;
+    out->nfeat = cp.nfeat;
+    out->smem = cp.smem;
+    out->fidx = cp.d_fidx;
     out->L = p->desc.L;
     out->mult = cp.d_mult;
     out->ops = cp.d_ops;
@@ -1064,6 +1099,53 @@ ef_status ef_moments_entropy(ef_plan_t p, const void *F, const void *Q, double *
     cudaError_t e = ef::moments_launch(p->desc.prec == EF_PREC_F32 ? 0 : 1, p->desc.d, F, Q, p->d_all_off, p->d_all_N,
                                        ncells, p->desc.N, 2.0 * p->desc.L, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+    return EF_OK;
+}
+
+ef_status ef_features(ef_plan_t p, const void *F, float *feat, int64_t ncells, int log_input, ef_stream_t stream)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (ncells < 0) return fail(EF_ERR_INVALID_ARG, "ncells < 0");
+    if (p->batched && ncells != p->ncells) return fail(EF_ERR_INVALID_ARG, "ncells differs from the batched plan");
+    if (ncells == 0) return EF_OK;
+    if (!F || !feat) return fail(EF_ERR_INVALID_ARG, "null F or feat");
+    if ((uintptr_t)F % 16) return fail(EF_ERR_INVALID_ARG, "F must be 16-byte aligned");
+    for (const ClassPlan &cp : p->classes)
+        if (cp.nfeat == 0) return fail(EF_ERR_UNSUPPORTED, "N too small for the feature band");
+    ef_status st = check_device(p);
+    if (st != EF_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Desc &ds = p->desc;
+    for (ClassPlan &cp : p->classes) {
+        const int64_t n = p->batched ? cp.ncells : ncells;
+        if (n <= 0) continue;
+        const int grid = (int)std::min<int64_t>(n, cp.max_clusters);
+        st = ensure_sg(p, cp, grid);
+        if (st != EF_OK) return st;
+        ef::CollideArgs a{};
+        a.F = F;
+        a.Q = nullptr;
+        a.cell_off = cp.d_cell_off;
+        a.cell_id = cp.d_cell_id;
+        a.ncells = n;
+        a.mult = cp.d_mult;
+        a.ops = cp.d_ops;
+        a.nops = cp.nops;
+        a.cluster = cp.cluster;
+        a.planes = cp.planes;
+        a.sg_global = cp.sg_global;
+        a.sg_ws = cp.d_sg;
+        a.out_mode = ef::OUT_FEATURES;
+        a.h = 2.0 * ds.L / cp.N;
+        a.status = p->d_status;
+        a.paired = cp.paired;
+        a.feat = feat;
+        a.fidx = cp.d_fidx;
+        a.fstride = EF_FEATURE_STRIDE;
+        a.log_input = log_input ? 1 : 0;
+        cudaError_t e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, s);
+        if (e != cudaSuccess) return cuda_fail(e, "features launch");
+    }
     return EF_OK;
 }
 

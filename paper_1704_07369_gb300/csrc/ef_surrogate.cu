@@ -1,0 +1,394 @@
+// ef_surrogate.cu -- the learned surrogate path: low Fourier modes of F -> MLP -> low modes of
+// Q^sigma, with per-cell gates, a seeded plain-operator audit and device-side fallback.
+//
+// Normalisation (the operator is quadratic, Q[a F] = a^2 Q[F]): with m = Fh_0 the zero mode,
+//   x_j = (Fh_j / m - mu_j) / s_j,        y_j = (Qh_j / m^2 - nu_j) / t_j,
+// column statistics (mu, s, nu, t) fitted on the training set.  The prediction sets Qh_0 = 0 (mass
+// conservation, Theorem 1).
+// Gates, every cell: finite prediction; every normalised input within +-x_max (inside the
+// training envelope); band entropy production P = 2 N^3 sum_{k != 0} Re(Qh_k conj(Lh_k)) <= 0 with
+// Lh the low modes of ln F (the discrete H-theorem, Theorem 1, restricted to the band).  A
+// seeded fraction of cells is also audited against the plain operator.  Gate failures and audited
+// cells get the plain operator's band; if any audited cell misses the tolerance, every remaining
+// cell falls back too.  No host synchronisation: counts and lists stay on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ef.h"
+#include "ef_launch.h"
+
+namespace {
+
+constexpr int kStride = EF_FEATURE_STRIDE;
+
+ef_status sfail(ef_status s, const std::string &m)
+{
+    ef::set_last_error(m.c_str());
+    return s;
+}
+
+ef_status scuda(cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    ef::set_last_error(m.c_str());
+    return e == cudaErrorMemoryAllocation ? EF_ERR_OOM : EF_ERR_CUDA;
+}
+
+int sgrid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+// column statistics of x = featF / m and y = featQ / m^2 over n samples
+__global__ void stats_kernel(const float *featF, const float *featQ, int64_t n, int nf, int idx0, float *mu, float *sd,
+                             float *nu, float *td)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nf) return;
+    double sx = 0, sxx = 0, sy = 0, syy = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double m = featF[i * kStride + 2 * idx0];
+        const double x = featF[i * kStride + j] / m;
+        const double y = featQ[i * kStride + j] / (m * m);
+        sx += x;
+        sxx += x * x;
+        sy += y;
+        syy += y * y;
+    }
+    const double mx = sx / n, my = sy / n;
+    const double vx = fmax(sxx / n - mx * mx, 0.0), vy = fmax(syy / n - my * my, 0.0);
+    mu[j] = (float)mx;
+    nu[j] = (float)my;
+    sd[j] = (float)(vx > 1e-24 ? sqrt(vx) : 1.0);
+    td[j] = (float)(vy > 1e-24 ? sqrt(vy) : 1.0);
+}
+
+__global__ void normalize_kernel(const float *featF, const float *featQ, int64_t n, int nf, int idx0, const float *mu,
+                                 const float *sd, const float *nu, const float *td, float *X, float *Y)
+{
+    const int64_t total = n * nf;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / nf;
+        const int j = (int)(q % nf);
+        const float m = featF[i * kStride + 2 * idx0];
+        X[i * kStride + j] = (featF[i * kStride + j] / m - mu[j]) / sd[j];
+        if (featQ && Y) Y[i * kStride + j] = (featQ[i * kStride + j] / (m * m) - nu[j]) / td[j];
+    }
+}
+
+__device__ __forceinline__ float hash_unit(uint64_t seed, int64_t i)
+{
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (float)((z >> 40) * (1.0 / 16777216.0));
+}
+
+// one warp per cell: decode, gates, audit draw, compaction of the cells that need the plain path
+__global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *featF, const float *featL, int64_t n, int nf,
+                                   int idx0, const float *nu, const float *td, const float *Xn, float xmax, float N3,
+                                   float audit_frac, uint64_t seed, float *qfeat, int *flags, unsigned long long *count,
+                                   int64_t *list_off, int64_t *list_id, int64_t cell)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const float m = featF[i * kStride + 2 * idx0];
+    float prod = 0.f;
+    bool bad = false;
+    for (int j = lane; j < nf; j += 32) {
+        float q = (Ypred[i * ldy + j] * td[j] + nu[j]) * m * m;
+        if (j / 2 == idx0) q = 0.f;                       // Qh_0 = 0
+        if (!isfinite(q)) bad = true;
+        if (fabsf(Xn[i * kStride + j]) > xmax) bad = true;
+        qfeat[i * kStride + j] = q;
+        // Re(q conj(l)) accumulates re*re + im*im over the (re, im) pair
+        prod += q * featL[i * kStride + j];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        prod += __shfl_xor_sync(0xffffffffu, prod, o);
+        bad |= __shfl_xor_sync(0xffffffffu, (int)bad, o) != 0;
+    }
+    if (lane == 0) {
+        prod *= 2.f * N3;
+        int f = 0;
+        if (bad || !(prod <= 0.f)) f |= 1;
+        if (hash_unit(seed, i) < audit_frac) f |= 2;
+        flags[i] = f;
+        if (f) {
+            const unsigned long long k = atomicAdd(count, 1ULL);
+            list_off[k] = i * cell;
+            list_id[k] = i;
+        }
+    }
+}
+
+// merge the plain band of the listed cells into the output; audited cells compare first
+__global__ void merge_kernel(const unsigned long long *count, const int64_t *list_id, const float *qplain, float *qfeat, int nf,
+                             float tol, int *flags, int *untrusted)
+{
+    const int lane = threadIdx.x & 31;
+    const long long k = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (k >= *count) return;
+    const int64_t i = list_id[k];
+    const int f = flags[i];
+    float num = 0.f, den = 0.f;
+    for (int j = lane; j < nf; j += 32) {
+        const float p = qplain[i * kStride + j];
+        const float d = qfeat[i * kStride + j] - p;
+        num += d * d;
+        den += p * p;
+        qfeat[i * kStride + j] = p;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        int nf2 = f | 8;                                  // plain result used
+        if ((f & 2) && num > tol * tol * den) {
+            nf2 |= 4;
+            atomicOr(untrusted, 1);
+        }
+        flags[i] = nf2;
+    }
+}
+
+// second round: when the audit failed, list every cell that still carries a prediction
+__global__ void relist_kernel(const int *untrusted, int64_t n, int *flags, unsigned long long *count, int64_t *list_off,
+                              int64_t *list_id, int64_t cell)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !*untrusted) return;
+    if (flags[i] & 8) return;
+    flags[i] |= 16;                                       // fell back because the batch was untrusted
+    const unsigned long long k = atomicAdd(count, 1ULL);
+    list_off[k] = i * cell;
+    list_id[k] = i;
+}
+
+}  // namespace
+
+struct ef_surrogate_s {
+    ef_plan_t plan;
+    ef_mlp_t mlp;
+    int64_t max_batch;
+    int nf, idx0, noutp;
+    float *mu = nullptr, *sd = nullptr, *nu = nullptr, *td = nullptr;
+    float *featF = nullptr, *featL = nullptr, *X = nullptr, *Y = nullptr, *qplain = nullptr;
+    void *Qs = nullptr;
+    int *untrusted = nullptr;
+    unsigned long long *count = nullptr;
+    int64_t *list_off = nullptr, *list_id = nullptr;
+    float xmax = 8.f;
+};
+
+namespace {
+
+void sur_free(ef_surrogate_s *s)
+{
+    if (!s) return;
+    cudaFree(s->mu);
+    cudaFree(s->sd);
+    cudaFree(s->nu);
+    cudaFree(s->td);
+    cudaFree(s->featF);
+    cudaFree(s->featL);
+    cudaFree(s->X);
+    cudaFree(s->Y);
+    cudaFree(s->qplain);
+    cudaFree(s->Qs);
+    cudaFree(s->untrusted);
+    cudaFree(s->count);
+    cudaFree(s->list_off);
+    cudaFree(s->list_id);
+    delete s;
+}
+
+// feature slot of k = 0: the canonical-half ordering of ef_features, K = EF_FEATURE_K
+int zero_slot(int d)
+{
+    const int K = EF_FEATURE_K;
+    int slot = 0;
+    for (int k0 = -K; k0 <= K; ++k0)
+        for (int k1 = -K; k1 <= K; ++k1)
+            for (int k2 = 0; k2 <= K; ++k2) {
+                if (k0 * k0 + k1 * k1 + k2 * k2 > K * K) continue;
+                if (!(k2 > 0 || (k2 == 0 && (k1 > 0 || (k1 == 0 && k0 >= 0))))) continue;
+                if (d == 2 && (k2 != 0 || k1 < 0)) continue;
+                if (k0 == 0 && k1 == 0 && k2 == 0) return slot;
+                ++slot;
+            }
+    return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, ef_surrogate_t *out)
+{
+    if (!out) return sfail(EF_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    ef::PlanView v;
+    if (!ef::plan_view(plan, &v)) return sfail(EF_ERR_INVALID_ARG, "surrogate needs a uniform plan");
+    if (!mlp) return sfail(EF_ERR_INVALID_ARG, "null mlp");
+    if (v.nfeat == 0) return sfail(EF_ERR_UNSUPPORTED, "N too small for the feature band");
+    if (v.sg_global) return sfail(EF_ERR_UNSUPPORTED, "surrogate fallback needs a shared-memory accumulator shape");
+    int64_t info[8];
+    ef_status st = ef_mlp_info(mlp, info);
+    if (st != EF_OK) return st;
+    const int nf = 2 * v.nfeat;
+    if (info[0] != nf || info[3] != nf) return sfail(EF_ERR_INVALID_ARG, "mlp widths must equal 2 x feature modes");
+    if (max_batch < 64 || max_batch % 64 || max_batch > info[7])
+        return sfail(EF_ERR_INVALID_ARG, "max_batch: multiple of 64, at most the mlp's max batch");
+    ef_surrogate_s *s = new ef_surrogate_s();
+    s->plan = plan;
+    s->mlp = mlp;
+    s->max_batch = max_batch;
+    s->nf = nf;
+    s->noutp = (int)info[6];
+    s->idx0 = zero_slot(v.d);
+    const int64_t cell = v.d == 3 ? (int64_t)v.N * v.N * v.N : (int64_t)v.N * v.N;
+    const size_t el = v.prec == EF_PREC_F32 ? 4 : 8;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t b) {
+        if (e == cudaSuccess) e = cudaMalloc(p, b);
+        if (e == cudaSuccess) e = cudaMemset(*p, 0, b);
+    };
+    alloc((void **)&s->mu, kStride * 4);
+    alloc((void **)&s->sd, kStride * 4);
+    alloc((void **)&s->nu, kStride * 4);
+    alloc((void **)&s->td, kStride * 4);
+    alloc((void **)&s->featF, (size_t)max_batch * kStride * 4);
+    alloc((void **)&s->featL, (size_t)max_batch * kStride * 4);
+    alloc((void **)&s->X, (size_t)max_batch * kStride * 4);
+    alloc((void **)&s->Y, (size_t)max_batch * s->noutp * 4);
+    alloc((void **)&s->qplain, (size_t)max_batch * kStride * 4);
+    alloc((void **)&s->Qs, (size_t)max_batch * cell * el);
+    alloc((void **)&s->untrusted, 4);
+    alloc((void **)&s->count, 8);
+    alloc((void **)&s->list_off, (size_t)max_batch * 8);
+    alloc((void **)&s->list_id, (size_t)max_batch * 8);
+    if (e != cudaSuccess) {
+        sur_free(s);
+        return scuda(e, "surrogate allocation");
+    }
+    // identity normalisation until fitted
+    std::vector<float> one(kStride, 1.f);
+    cudaMemcpy(s->sd, one.data(), kStride * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->td, one.data(), kStride * 4, cudaMemcpyHostToDevice);
+    *out = s;
+    return EF_OK;
+}
+
+ef_status ef_surrogate_destroy(ef_surrogate_t s)
+{
+    if (!s) return sfail(EF_ERR_INVALID_ARG, "null surrogate");
+    sur_free(s);
+    return EF_OK;
+}
+
+ef_status ef_surrogate_fit_stats(ef_surrogate_t s, const float *featF, const float *featQ, int64_t n, ef_stream_t stream)
+{
+    if (!s || !featF || !featQ || n <= 0) return sfail(EF_ERR_INVALID_ARG, "bad surrogate statistics arguments");
+    stats_kernel<<<(s->nf + 127) / 128, 128, 0, (cudaStream_t)stream>>>(featF, featQ, n, s->nf, s->idx0, s->mu, s->sd,
+                                                                          s->nu, s->td);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EF_OK : scuda(e, "stats");
+}
+
+ef_status ef_surrogate_normalize(ef_surrogate_t s, const float *featF, const float *featQ, float *X, float *Y, int64_t n,
+                                 ef_stream_t stream)
+{
+    if (!s || !featF || !X || n < 0) return sfail(EF_ERR_INVALID_ARG, "bad normalisation arguments");
+    if (n == 0) return EF_OK;
+    normalize_kernel<<<sgrid(n * s->nf), 256, 0, (cudaStream_t)stream>>>(featF, featQ, n, s->nf, s->idx0, s->mu, s->sd,
+                                                                          s->nu, s->td, X, Y);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? EF_OK : scuda(e, "normalise");
+}
+
+ef_status ef_surrogate_stats(ef_surrogate_t s, float *host4, int set)
+{
+    if (!s || !host4) return sfail(EF_ERR_INVALID_ARG, "null surrogate or buffer");
+    float *d[4] = {s->mu, s->sd, s->nu, s->td};
+    for (int k = 0; k < 4; ++k) {
+        cudaError_t e = set ? cudaMemcpy(d[k], host4 + k * kStride, kStride * 4, cudaMemcpyHostToDevice)
+                            : cudaMemcpy(host4 + k * kStride, d[k], kStride * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return scuda(e, "surrogate stats copy");
+    }
+    return EF_OK;
+}
+
+ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int *flags, int64_t ncells, float audit_fraction,
+                             uint64_t seed, float tol, ef_stream_t stream)
+{
+    if (!s || !F || !qfeat || !flags) return sfail(EF_ERR_INVALID_ARG, "null argument");
+    if (ncells < 0 || ncells > s->max_batch || ncells % 64) return sfail(EF_ERR_INVALID_ARG, "ncells: multiple of 64, <= max_batch");
+    if (ncells == 0) return EF_OK;
+    if (!(audit_fraction >= 0.f && audit_fraction <= 1.f) || !(tol > 0.f)) return sfail(EF_ERR_INVALID_ARG, "bad audit fraction or tolerance");
+    ef::PlanView v;
+    if (!ef::plan_view(s->plan, &v)) return sfail(EF_ERR_INVALID_ARG, "bad plan");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t cell = v.d == 3 ? (int64_t)v.N * v.N * v.N : (int64_t)v.N * v.N;
+    ef_status r = ef_features(s->plan, F, s->featF, ncells, 0, stream);
+    if (r != EF_OK) return r;
+    r = ef_features(s->plan, F, s->featL, ncells, 1, stream);
+    if (r != EF_OK) return r;
+    r = ef_surrogate_normalize(s, s->featF, nullptr, s->X, nullptr, ncells, stream);
+    if (r != EF_OK) return r;
+    r = ef_mlp_forward(s->mlp, s->X, kStride, s->Y, s->noutp, ncells, stream);
+    if (r != EF_OK) return r;
+    cudaError_t e = cudaMemsetAsync(s->count, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->untrusted, 0, 4, st);
+    if (e != cudaSuccess) return scuda(e, "surrogate reset");
+    decode_gate_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(
+        s->Y, s->noutp, s->featF, s->featL, ncells, s->nf, s->idx0, s->nu, s->td, s->X, s->xmax, (float)cell,
+        audit_fraction, seed, qfeat, flags, s->count, s->list_off, s->list_id, cell);
+    for (int round = 0; round < 2; ++round) {
+        // plain operator on the listed cells (count read on the device), then their band
+        ef::CollideArgs a{};
+        a.F = F;
+        a.Q = s->Qs;
+        a.cell_off = s->list_off;
+        a.cell_id = s->list_id;
+        a.ncells = ncells;
+        a.dev_ncells = reinterpret_cast<const long long *>(s->count);
+        a.mult = v.mult;
+        a.ops = v.ops;
+        a.nops = v.nops;
+        a.cluster = v.cluster;
+        a.planes = v.planes;
+        a.paired = v.paired;
+        a.out_mode = ef::OUT_COLLIDE;
+        a.h = 2.0 * v.L / v.N;
+        a.status = v.status;
+        const int grid = (int)std::min<int64_t>(ncells, v.max_clusters);
+        e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, v.smem, st);
+        if (e != cudaSuccess) return scuda(e, "fallback collide");
+        ef::CollideArgs f = a;
+        f.F = s->Qs;
+        f.Q = nullptr;
+        f.out_mode = ef::OUT_FEATURES;
+        f.feat = s->qplain;
+        f.fidx = v.fidx;
+        f.fstride = kStride;
+        e = ef::collide_launch(v.prec, v.d, v.N, f, grid, v.tpb, v.smem, st);
+        if (e != cudaSuccess) return scuda(e, "fallback features");
+        merge_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(s->count, s->list_id, s->qplain, qfeat, s->nf,
+                                                                            tol, flags, s->untrusted);
+        if (round == 0) {
+            e = cudaMemsetAsync(s->count, 0, 8, st);
+            if (e != cudaSuccess) return scuda(e, "surrogate reset");
+            relist_kernel<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(s->untrusted, ncells, flags, s->count,
+                                                                            s->list_off, s->list_id, cell);
+        }
+    }
+    e = cudaGetLastError();
+    return e == cudaSuccess ? EF_OK : scuda(e, "surrogate infer");
+}
+
+}  // extern "C"

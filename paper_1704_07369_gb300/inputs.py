@@ -100,3 +100,40 @@ def ragged_sizes(ncells: int, choices=(24, 32, 40, 48), seed: int = 1234) -> np.
 def pack(cells) -> np.ndarray:
     """Concatenate cells back to back (cell-major, C order)."""
     return np.concatenate([np.ascontiguousarray(c).ravel() for c in cells])
+
+
+def bkw_family_params(ncells: int, seed: int = 4321, d: int = 3):
+    """Per-cell (t0, rho, theta, u) of the BKW family, drawn exactly as bkw_family_cells does."""
+    t0 = np.empty(ncells)
+    rho = np.empty(ncells)
+    theta = np.empty(ncells)
+    u = np.empty((ncells, d))
+    for i in range(ncells):
+        rng = np.random.default_rng(seed + i)
+        t0[i] = rng.uniform(0.5, 10.0)
+        rho[i] = rng.uniform(0.5, 2.0)
+        theta[i] = rng.uniform(0.5, 2.0)
+        u[i] = _ball(rng, d, 1.0)
+    return t0, rho, theta, u
+
+
+def bkw_family_torch(N: int, L: float, ncells: int, seed: int = 4321, device="cuda", dtype=None, out=None):
+    """bkw_family_cells evaluated on a torch device (same draws, same formula), [ncells, N, N, N]."""
+    import torch
+    dtype = dtype or torch.float32
+    t0, rho, theta, u = bkw_family_params(ncells, seed, 3)
+    h = 2.0 * L / N
+    v1 = (torch.arange(N, device=device, dtype=torch.float64) - N // 2) * h
+    if out is None:
+        out = torch.empty((ncells, N, N, N), device=device, dtype=dtype)
+    tt = torch.as_tensor(t0 * rho, device=device)
+    S = 1.0 - 2.0 * torch.exp(-tt / 6.0) / 5.0
+    for i in range(ncells):
+        x = (v1 - float(u[i, 0])) ** 2
+        y = (v1 - float(u[i, 1])) ** 2
+        z = (v1 - float(u[i, 2])) ** 2
+        v2 = (x[:, None, None] + y[None, :, None] + z[None, None, :]) / float(theta[i])
+        s = S[i]
+        f = torch.exp(-v2 / (2 * s)) / (2 * np.pi * s) ** 1.5 * ((5 * s - 3) / (2 * s) + (1 - s) / (2 * s * s) * v2)
+        out[i] = (float(rho[i]) * float(theta[i]) ** -1.5 * f).to(dtype)
+    return out

@@ -1,0 +1,111 @@
+"""Training and use of the learned surrogate through the C ABI (argument marshalling only).
+
+The surrogate maps a cell's low Fourier modes of F (|k| <= EF_FEATURE_K) to the same modes of
+Q^sigma[F].  Training data are produced by the library itself (ef_collide on seeded BKW-family
+cells, then ef_features of F and of Q); the network is trained by the library's tensor-core MLP
+kernels (ef_mlp_train_step); inference goes through ef_surrogate_infer, which gates every cell,
+audits a seeded fraction against the plain operator and falls back on the device.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import (EF_FEATURE_STRIDE, EF_KERNEL_HARD_SPHERE, EF_PREC_F32, MLP, Plan, Surrogate, ef_features)
+from . import inputs
+
+
+def make_plan(kernel=EF_KERNEL_HARD_SPHERE, N=32, L=8.0, R=32, prec=EF_PREC_F32):
+    return Plan(3, N, L, kernel, R, prec)
+
+
+def features_of_family(plan, ncells, seed, chunk=2048, device="cuda"):
+    """(featF, featQ) [ncells, EF_FEATURE_STRIDE] of BKW-family cells and of Q^sigma of them."""
+    N, L = plan.N, plan.L
+    featF = torch.zeros(ncells, EF_FEATURE_STRIDE, device=device)
+    featQ = torch.zeros(ncells, EF_FEATURE_STRIDE, device=device)
+    F = torch.empty(chunk, N, N, N, device=device)
+    Q = torch.empty_like(F)
+    for c0 in range(0, ncells, chunk):
+        n = min(chunk, ncells - c0)
+        inputs.bkw_family_torch(N, L, n, seed + c0, device=device, out=F[:n])
+        plan.collide(F, Q, ncells=n)
+        ef_features(plan.handle, F, featF[c0:c0 + n], n)
+        ef_features(plan.handle, Q, featQ[c0:c0 + n], n)
+    torch.cuda.synchronize()
+    return featF, featQ
+
+
+def loss_mask(nfeat_floats, zero_slot, device="cuda"):
+    """Weights of the MSE: 1 everywhere except the zero mode (Qh_0 = 0 by mass conservation)."""
+    w = torch.ones(nfeat_floats, device=device)
+    w[2 * zero_slot:2 * zero_slot + 2] = 0.0
+    return w
+
+
+def zero_slot(K=6):
+    slot = 0
+    for k0 in range(-K, K + 1):
+        for k1 in range(-K, K + 1):
+            for k2 in range(0, K + 1):
+                if k0 * k0 + k1 * k1 + k2 * k2 > K * K:
+                    continue
+                if not (k2 > 0 or (k2 == 0 and (k1 > 0 or (k1 == 0 and k0 >= 0)))):
+                    continue
+                if (k0, k1, k2) == (0, 0, 0):
+                    return slot
+                slot += 1
+    raise ValueError
+
+
+class Trainer:
+    """Fits the normalisation, then trains the MLP with Adam and a cosine learning-rate decay."""
+
+    def __init__(self, plan, nhidden=512, nlayers=4, batch=1024, max_infer_batch=16384, seed=0):
+        self.plan = plan
+        self.nf = 2 * 463
+        self.batch = batch
+        self.mlp = MLP(self.nf, nhidden, nlayers, self.nf, max(batch, max_infer_batch), seed=seed)
+        self.sur = Surrogate(plan, self.mlp, max_infer_batch)
+        self.wmask = loss_mask(self.nf, zero_slot())
+
+    def fit(self, featF, featQ, epochs=20, lr0=1e-3, lr1=1e-5, seed=0, log=None):
+        n = featF.shape[0] // self.batch * self.batch
+        self.sur.fit_stats(featF, featQ, featF.shape[0])
+        X = torch.zeros(featF.shape[0], EF_FEATURE_STRIDE, device=featF.device)
+        Y = torch.zeros_like(X)
+        self.sur.normalize(featF, featQ, X, Y, featF.shape[0])
+        loss = torch.zeros(1, device=featF.device)
+        g = torch.Generator(device="cpu")
+        g.manual_seed(seed)
+        steps = epochs * (n // self.batch)
+        hist = []
+        step = 0
+        for ep in range(epochs):
+            perm = torch.randperm(featF.shape[0], generator=g)[:n].to(featF.device)
+            Xs, Ys = X[perm], Y[perm]
+            tot = torch.zeros(1, device=featF.device)
+            for b0 in range(0, n, self.batch):
+                lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * step / max(1, steps)))
+                self.mlp.train_step(Xs[b0:b0 + self.batch], Ys[b0:b0 + self.batch], self.batch, lr, loss,
+                                    wmask=self.wmask)
+                tot += loss
+                step += 1
+            hist.append(float(tot.item()) / (n // self.batch))
+            if log:
+                log(ep, hist[-1])
+        return hist
+
+    def predict(self, F, ncells, audit_fraction=0.0, seed=0, tol=1e-3):
+        q = torch.zeros(ncells, EF_FEATURE_STRIDE, device=F.device)
+        flags = torch.zeros(ncells, dtype=torch.int32, device=F.device)
+        self.sur.infer(F, q, flags, ncells, audit_fraction, seed, tol)
+        return q, flags
+
+
+def band_rel_l2(pred, ref, nf=926):
+    """Per-cell relative L2 error over the band (FP32 feature rows)."""
+    d = (pred[:, :nf] - ref[:, :nf]).double()
+    return torch.sqrt((d * d).sum(1) / (ref[:, :nf].double() ** 2).sum(1))

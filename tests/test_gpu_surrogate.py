@@ -1,0 +1,136 @@
+"""GPU tests of the surrogate path: low-mode features against the oracle's DFT, the tensor-core
+MLP (forward and gradients) against the FP64 oracle MLP with the same bf16 roundings, training
+that lowers the loss, and the gate / audit / fallback logic of ef_surrogate_infer."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_1704_07369_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+import paper_1704_07369_gb300 as ef  # noqa: E402
+from paper_1704_07369_gb300 import surrogate as S  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ef.build()
+    ef.lib()
+
+
+def _modes(K=6):
+    out = []
+    for k0 in range(-K, K + 1):
+        for k1 in range(-K, K + 1):
+            for k2 in range(0, K + 1):
+                if k0 * k0 + k1 * k1 + k2 * k2 > K * K:
+                    continue
+                if not (k2 > 0 or (k2 == 0 and (k1 > 0 or (k1 == 0 and k0 >= 0)))):
+                    continue
+                out.append((k0, k1, k2))
+    return out
+
+
+@pytest.mark.parametrize("prec", [ef.EF_PREC_F64, ef.EF_PREC_F32])
+def test_features_match_oracle_dft(prec):
+    N, L = 16, 8.0
+    cells = [inputs.mixture_cell(3, N, L, 70 + i) for i in range(3)]
+    dt = torch.float64 if prec == ef.EF_PREC_F64 else torch.float32
+    plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, prec)
+    F = torch.tensor(np.stack(cells), dtype=dt, device="cuda")
+    feat = torch.zeros(3, ef.EF_FEATURE_STRIDE, device="cuda")
+    featL = torch.zeros_like(feat)
+    ef.ef_features(plan.handle, F, feat, 3)
+    ef.ef_features(plan.handle, F, featL, 3, log_input=1)
+    torch.cuda.synchronize()
+    modes = _modes()
+    assert len(modes) == 463
+    for i, c in enumerate(cells):
+        for field, got in ((c, feat[i]), (np.log(np.maximum(c, 1e-30)), featL[i])):
+            Fh = oracle.dft(field)
+            ref = np.array([Fh[k0 % N, k1 % N, k2 % N] * (-1) ** (k0 + k1 + k2) for k0, k1, k2 in modes])
+            g = got.cpu().numpy()[:926].reshape(-1, 2)
+            g = g[:, 0] + 1j * g[:, 1]
+            assert np.abs(g - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_mlp_forward_and_gradients_match_oracle():
+    rng = np.random.default_rng(5)
+    nin, nh, nl, nout, B = 100, 64, 3, 70, 128
+    net = ef.MLP(nin, nh, nl, nout, B, seed=11)
+    layers = omlp.unpack(net.params(), net.layout())
+    X = rng.normal(size=(B, nin)).astype(np.float32)
+    T = rng.normal(size=(B, nout)).astype(np.float32)
+    w = rng.uniform(0.5, 1.5, nout).astype(np.float32)
+    Xd = torch.tensor(X, device="cuda")
+    Td = torch.tensor(T, device="cuda")
+    wd = torch.tensor(w, device="cuda")
+    Y = torch.zeros(B, net.noutp, device="cuda")
+    net.forward(Xd, Y, B)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(net.nparams, device="cuda")
+    net.grad(Xd, Td, B, loss, grad, wmask=wd)
+    torch.cuda.synchronize()
+    Xp = np.zeros((B, net.ninp))
+    Xp[:, :nin] = X
+    y_ref, _ = omlp.forward(layers, Xp, bf=True)
+    y = Y.cpu().numpy()
+    assert np.sqrt(((y - y_ref) ** 2).sum() / (y_ref ** 2).sum()) <= 1e-4
+    l_ref, g_ref = omlp.loss_and_grads(layers, Xp, T.astype(np.float64), nout, wmask=w, bf=True)
+    assert abs(loss.item() - l_ref) <= 1e-4 * l_ref
+    gh = grad.cpu().numpy()
+    for (woff, o, i, boff), (dW, db) in zip(net.layout(), g_ref):
+        gW = gh[woff:woff + o * i].reshape(o, i)
+        gb = gh[boff:boff + o]
+        assert np.sqrt(((gW - dW) ** 2).sum() / (dW ** 2).sum()) <= 2e-3
+        assert np.sqrt(((gb - db) ** 2).sum() / (db ** 2).sum()) <= 2e-3
+
+
+def test_mlp_training_reduces_loss():
+    rng = np.random.default_rng(6)
+    nin, nh, nout, B = 64, 128, 32, 256
+    net = ef.MLP(nin, nh, 3, nout, B, seed=3)
+    A = rng.normal(size=(nin, nout)) / 8
+    X = rng.normal(size=(B, nin)).astype(np.float32)
+    T = np.tanh(X @ A).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    losses = []
+    for _ in range(300):
+        net.train_step(Xd, Td, B, 2e-3, loss)
+        losses.append(loss.item())
+    assert losses[-1] < 0.05 * losses[0]
+
+
+def test_surrogate_audit_and_fallback_paths():
+    """audit 1.0: every cell gets the plain band bit for bit; a tolerance no prediction can meet
+    makes the audited cells fail and the whole batch fall back."""
+    N, L, n = 16, 8.0, 128
+    plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F32)
+    net = ef.MLP(926, 64, 3, 926, n, seed=1)
+    sur = ef.Surrogate(plan, net, n)
+    F = inputs.bkw_family_torch(N, L, n, seed=77)
+    Q = torch.empty_like(F)
+    plan.collide(F, Q, ncells=n)
+    ref = torch.zeros(n, ef.EF_FEATURE_STRIDE, device="cuda")
+    ef.ef_features(plan.handle, Q, ref, n)
+    fF = torch.zeros_like(ref)
+    ef.ef_features(plan.handle, F, fF, n)
+    sur.fit_stats(fF, ref, n)
+    q = torch.zeros_like(ref)
+    flags = torch.zeros(n, dtype=torch.int32, device="cuda")
+    sur.infer(F, q, flags, n, audit_fraction=1.0, seed=5, tol=1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(q[:, :926], ref[:, :926])
+    assert bool(((flags & 8) != 0).all())
+    sur.infer(F, q, flags, n, audit_fraction=0.25, seed=9, tol=1e-12)
+    torch.cuda.synchronize()
+    f = flags.cpu().numpy()
+    assert ((f & 2) != 0).sum() > 0 and ((f & 4) != 0).sum() > 0
+    assert ((f & 8) != 0).all()
+    assert torch.equal(q[:, :926], ref[:, :926])

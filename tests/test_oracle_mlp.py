@@ -1,0 +1,41 @@
+"""Pin of the FP64 oracle MLP: its backpropagation (bf16 emulation off) equals central finite
+differences of its own forward pass, and its bf16 rounding matches the bfloat16 format."""
+import numpy as np
+
+from oracle import mlp
+
+
+def _layers(rng, dims):
+    return [(rng.normal(size=(o, i)) / np.sqrt(i), rng.normal(size=o) * 0.1) for i, o in zip(dims[:-1], dims[1:])]
+
+
+def test_backprop_matches_finite_differences():
+    rng = np.random.default_rng(3)
+    layers = _layers(rng, [7, 6, 5, 4])
+    X = rng.normal(size=(5, 7))
+    T = rng.normal(size=(5, 4))
+    w = rng.uniform(0.5, 2.0, 3)
+    loss, grads = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False)
+    eps = 1e-6
+    for li, (W, b) in enumerate(layers):
+        for arr, g in ((W, grads[li][0]), (b, grads[li][1])):
+            it = np.nditer(arr, flags=["multi_index"])
+            for _ in it:
+                idx = it.multi_index
+                old = arr[idx]
+                arr[idx] = old + eps
+                lp, _ = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False)
+                arr[idx] = old - eps
+                lm, _ = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False)
+                arr[idx] = old
+                assert abs((lp - lm) / (2 * eps) - g[idx]) <= 1e-7 * max(1.0, abs(g[idx]))
+
+
+def test_bf16_rounding():
+    # exactly representable values stay; halfway cases round to even; relative error <= 2^-9
+    assert mlp.bf16(np.array([1.0, -2.5, 0.15625]))[0] == 1.0
+    one_plus_half_ulp = 1.0 + 2.0 ** -8            # halfway between 1 and 1 + 2^-7 -> even (1.0)
+    assert mlp.bf16(np.array([one_plus_half_ulp]))[0] == 1.0
+    assert mlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    x = np.random.default_rng(0).normal(size=10000)
+    assert np.max(np.abs(mlp.bf16(x) - x) / np.abs(x)) <= 2.0 ** -8
