@@ -190,15 +190,18 @@ typedef struct ef_surrogate_s *ef_surrogate_t;
 ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, ef_surrogate_t *out);
 ef_status ef_surrogate_destroy(ef_surrogate_t sur);
 
-/* Fit the column statistics (mean, std) of x = Fh / m and y = Qh / m^2 (m = Fh_0, the zero mode)
- * from n training samples of features (EF_FEATURE_STRIDE floats each, from ef_features of F and of
- * Q^sigma[F]); the operator is quadratic, so this normalisation is exact in the density. */
-ef_status ef_surrogate_fit_stats(ef_surrogate_t sur, const float *featF, const float *featQ, int64_t n,
-                                 ef_stream_t stream);
+/* Fit the normalisation from n training samples: features of F and of Q^sigma[F] (ef_features,
+ * EF_FEATURE_STRIDE floats each) and the cells' moments (ef_moments_entropy, EF_DIAG_STRIDE doubles
+ * each).  With m = Fh_0 and u = momentum / mass, each mode is de-translated and mass-normalised,
+ * x_k = Fh_k e^{i pi k.u/L} / m and y_k = Qh_k e^{i pi k.u/L} / m^2 (the operator is quadratic in F and
+ * commutes with velocity shifts up to aliasing); then per-column mean and std of x, per-column mean
+ * of y and one global scale of y.  Xt, Yt: caller scratch of n x EF_FEATURE_STRIDE floats. */
+ef_status ef_surrogate_fit_stats(ef_surrogate_t sur, const float *featF, const float *featQ, const double *mom,
+                                 float *Xt, float *Yt, int64_t n, ef_stream_t stream);
 
 /* Normalised MLP inputs X (and targets Y, if featQ and Y are not null), EF_FEATURE_STRIDE per row. */
-ef_status ef_surrogate_normalize(ef_surrogate_t sur, const float *featF, const float *featQ, float *X, float *Y,
-                                 int64_t n, ef_stream_t stream);
+ef_status ef_surrogate_normalize(ef_surrogate_t sur, const float *featF, const float *featQ, const double *mom,
+                                 float *X, float *Y, int64_t n, ef_stream_t stream);
 
 /* Copy the statistics (4 x EF_FEATURE_STRIDE floats: mu, s, nu, t) to (set = 0) / from (set = 1) the host. */
 ef_status ef_surrogate_stats(ef_surrogate_t sur, float *host, int set);

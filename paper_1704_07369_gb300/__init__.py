@@ -91,8 +91,8 @@ def lib():
         L.ef_mlp_train_step.argtypes = [vp, vp, i32, vp, i32, vp, i64, ctypes.c_float, vp, vp]
         L.ef_surrogate_create.argtypes = [vp, vp, i64, pp]
         L.ef_surrogate_destroy.argtypes = [vp]
-        L.ef_surrogate_fit_stats.argtypes = [vp, vp, vp, i64, vp]
-        L.ef_surrogate_normalize.argtypes = [vp, vp, vp, vp, vp, i64, vp]
+        L.ef_surrogate_fit_stats.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+        L.ef_surrogate_normalize.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         L.ef_surrogate_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
         L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
@@ -236,12 +236,13 @@ class Surrogate:
         _check(lib().ef_surrogate_create(plan.handle, mlp.handle, int(max_batch), ctypes.byref(self.handle)))
         self.max_batch = int(max_batch)
 
-    def fit_stats(self, featF, featQ, n, stream=None):
-        _check(lib().ef_surrogate_fit_stats(self.handle, _ptr(featF), _ptr(featQ), int(n), _stream(stream)))
+    def fit_stats(self, featF, featQ, mom, Xt, Yt, n, stream=None):
+        _check(lib().ef_surrogate_fit_stats(self.handle, _ptr(featF), _ptr(featQ), _ptr(mom), _ptr(Xt), _ptr(Yt),
+                                            int(n), _stream(stream)))
 
-    def normalize(self, featF, featQ, X, Y, n, stream=None):
-        _check(lib().ef_surrogate_normalize(self.handle, _ptr(featF), _ptr(featQ), _ptr(X), _ptr(Y), int(n),
-                                            _stream(stream)))
+    def normalize(self, featF, featQ, mom, X, Y, n, stream=None):
+        _check(lib().ef_surrogate_normalize(self.handle, _ptr(featF), _ptr(featQ), _ptr(mom), _ptr(X), _ptr(Y),
+                                            int(n), _stream(stream)))
 
     def stats(self):
         import numpy as np

@@ -1,9 +1,10 @@
 // ef_surrogate.cu -- the learned surrogate path: low Fourier modes of F -> MLP -> low modes of
 // Q^sigma, with per-cell gates, a seeded plain-operator audit and device-side fallback.
 //
-// Normalisation (the operator is quadratic, Q[a F] = a^2 Q[F]): with m = Fh_0 the zero mode,
-//   x_j = (Fh_j / m - mu_j) / s_j,        y_j = (Qh_j / m^2 - nu_j) / t_j,
-// column statistics (mu, s, nu, t) fitted on the training set.  The prediction sets Qh_0 = 0 (mass
+// Normalisation (the operator is quadratic, Q[a F] = a^2 Q[F], and commutes with velocity shifts):
+// with m = Fh_0 the zero mode and u the mean velocity (momentum / mass),
+//   x_k = (Fh_k e^{i pi k.u/L} / m - mu_k) / s_k,      y_k = (Qh_k e^{i pi k.u/L} / m^2 - nu_k) / t,
+// column statistics (mu, s, nu) and one output scale t fitted on the training set.  The prediction sets Qh_0 = 0 (mass
 // conservation, Theorem 1).
 // Gates, every cell: finite prediction; every normalised input within +-x_max (inside the
 // training envelope); band entropy production P = 2 N^3 sum_{k != 0} Re(Qh_k conj(Lh_k)) <= 0 with
@@ -40,17 +41,43 @@ ef_status scuda(cudaError_t e, const char *what)
 
 int sgrid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
-// column statistics of x = featF / m and y = featQ / m^2 over n samples
-__global__ void stats_kernel(const float *featF, const float *featQ, int64_t n, int nf, int idx0, float *mu, float *sd,
-                             float *nu, float *td)
+// De-translated, mass-normalised features: with m = Fh_0 and u = momentum / mass the mean velocity,
+//   x~_k = Fh_k exp(+i pi k.u / L) / m,     y~_k = Qh_k exp(+i pi k.u / L) / m^2
+// (a velocity shift by u multiplies mode k by exp(-i pi k.u / L); the operator commutes with it up
+// to aliasing, so the network sees the family without its bulk velocity).  One thread per mode.
+__global__ void prep_kernel(const float *featF, const float *featQ, const double *mom, const int *kvec, int64_t n,
+                            int nmodes, int idx0, float pi_over_L, float *Xt, float *Yt)
+{
+    const int64_t total = n * nmodes;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / nmodes;
+        const int j = (int)(q % nmodes);
+        const double *mi = mom + i * EF_DIAG_STRIDE;
+        const float ux = (float)(mi[1] / mi[0]), uy = (float)(mi[2] / mi[0]), uz = (float)(mi[3] / mi[0]);
+        const float ph = pi_over_L * (kvec[3 * j] * ux + kvec[3 * j + 1] * uy + kvec[3 * j + 2] * uz);
+        float sn, cs;
+        sincosf(ph, &sn, &cs);
+        const float m = featF[i * kStride + 2 * idx0];
+        const float fr = featF[i * kStride + 2 * j], fi = featF[i * kStride + 2 * j + 1];
+        Xt[i * kStride + 2 * j] = (fr * cs - fi * sn) / m;
+        Xt[i * kStride + 2 * j + 1] = (fr * sn + fi * cs) / m;
+        if (featQ && Yt) {
+            const float qr = featQ[i * kStride + 2 * j], qi = featQ[i * kStride + 2 * j + 1];
+            Yt[i * kStride + 2 * j] = (qr * cs - qi * sn) / (m * m);
+            Yt[i * kStride + 2 * j + 1] = (qr * sn + qi * cs) / (m * m);
+        }
+    }
+}
+
+// column mean / std of the prepared inputs and outputs; the output scale is one global RMS
+__global__ void stats_kernel(const float *Xt, const float *Yt, int64_t n, int nf, float *mu, float *sd, float *nu,
+                             float *colvar)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nf) return;
     double sx = 0, sxx = 0, sy = 0, syy = 0;
     for (int64_t i = 0; i < n; ++i) {
-        const double m = featF[i * kStride + 2 * idx0];
-        const double x = featF[i * kStride + j] / m;
-        const double y = featQ[i * kStride + j] / (m * m);
+        const double x = Xt[i * kStride + j], y = Yt[i * kStride + j];
         sx += x;
         sxx += x * x;
         sy += y;
@@ -61,19 +88,26 @@ __global__ void stats_kernel(const float *featF, const float *featQ, int64_t n, 
     mu[j] = (float)mx;
     nu[j] = (float)my;
     sd[j] = (float)(vx > 1e-24 ? sqrt(vx) : 1.0);
-    td[j] = (float)(vy > 1e-24 ? sqrt(vy) : 1.0);
+    colvar[j] = (float)vy;
 }
 
-__global__ void normalize_kernel(const float *featF, const float *featQ, int64_t n, int nf, int idx0, const float *mu,
-                                 const float *sd, const float *nu, const float *td, float *X, float *Y)
+__global__ void scale_kernel(const float *colvar, int nf, float *td)
+{
+    double acc = 0.0;
+    for (int j = 0; j < nf; ++j) acc += colvar[j];
+    const float t = (float)(acc > 0 ? sqrt(acc / nf) : 1.0);
+    for (int j = 0; j < kStride; ++j) td[j] = t;
+}
+
+__global__ void standardize_kernel(float *X, float *Y, int64_t n, int nf, const float *mu, const float *sd, const float *nu,
+                                   const float *td)
 {
     const int64_t total = n * nf;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = q / nf;
         const int j = (int)(q % nf);
-        const float m = featF[i * kStride + 2 * idx0];
-        X[i * kStride + j] = (featF[i * kStride + j] / m - mu[j]) / sd[j];
-        if (featQ && Y) Y[i * kStride + j] = (featQ[i * kStride + j] / (m * m) - nu[j]) / td[j];
+        X[i * kStride + j] = (X[i * kStride + j] - mu[j]) / sd[j];
+        if (Y) Y[i * kStride + j] = (Y[i * kStride + j] - nu[j]) / td[j];
     }
 }
 
@@ -87,25 +121,33 @@ __device__ __forceinline__ float hash_unit(uint64_t seed, int64_t i)
 }
 
 // one warp per cell: decode, gates, audit draw, compaction of the cells that need the plain path
-__global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *featF, const float *featL, int64_t n, int nf,
-                                   int idx0, const float *nu, const float *td, const float *Xn, float xmax, float N3,
-                                   float audit_frac, uint64_t seed, float *qfeat, int *flags, unsigned long long *count,
-                                   int64_t *list_off, int64_t *list_id, int64_t cell)
+__global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *featF, const float *featL, const double *mom,
+                                   const int *kvec, float pi_over_L, int64_t n, int nf, int idx0, const float *nu,
+                                   const float *td, const float *Xn, float xmax, float N3, float audit_frac, uint64_t seed,
+                                   float *qfeat, int *flags, unsigned long long *count, int64_t *list_off,
+                                   int64_t *list_id, int64_t cell)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const float m = featF[i * kStride + 2 * idx0];
+    const double *mi = mom + i * EF_DIAG_STRIDE;
+    const float ux = (float)(mi[1] / mi[0]), uy = (float)(mi[2] / mi[0]), uz = (float)(mi[3] / mi[0]);
     float prod = 0.f;
     bool bad = false;
-    for (int j = lane; j < nf; j += 32) {
-        float q = (Ypred[i * ldy + j] * td[j] + nu[j]) * m * m;
-        if (j / 2 == idx0) q = 0.f;                       // Qh_0 = 0
-        if (!isfinite(q)) bad = true;
-        if (fabsf(Xn[i * kStride + j]) > xmax) bad = true;
-        qfeat[i * kStride + j] = q;
-        // Re(q conj(l)) accumulates re*re + im*im over the (re, im) pair
-        prod += q * featL[i * kStride + j];
+    for (int jm = lane; jm < nf / 2; jm += 32) {
+        const float yr = (Ypred[i * ldy + 2 * jm] * td[2 * jm] + nu[2 * jm]) * m * m;
+        const float yi = (Ypred[i * ldy + 2 * jm + 1] * td[2 * jm + 1] + nu[2 * jm + 1]) * m * m;
+        const float ph = pi_over_L * (kvec[3 * jm] * ux + kvec[3 * jm + 1] * uy + kvec[3 * jm + 2] * uz);
+        float sn, cs;
+        sincosf(ph, &sn, &cs);
+        float qr = yr * cs + yi * sn, qi = yi * cs - yr * sn;      // times exp(-i ph)
+        if (jm == idx0) qr = qi = 0.f;                             // Qh_0 = 0
+        if (!isfinite(qr) || !isfinite(qi)) bad = true;
+        if (fabsf(Xn[i * kStride + 2 * jm]) > xmax || fabsf(Xn[i * kStride + 2 * jm + 1]) > xmax) bad = true;
+        qfeat[i * kStride + 2 * jm] = qr;
+        qfeat[i * kStride + 2 * jm + 1] = qi;
+        prod += qr * featL[i * kStride + 2 * jm] + qi * featL[i * kStride + 2 * jm + 1];   // Re(q conj(l))
     }
     for (int o = 16; o > 0; o >>= 1) {
         prod += __shfl_xor_sync(0xffffffffu, prod, o);
@@ -176,7 +218,10 @@ struct ef_surrogate_s {
     ef_mlp_t mlp;
     int64_t max_batch;
     int nf, idx0, noutp;
-    float *mu = nullptr, *sd = nullptr, *nu = nullptr, *td = nullptr;
+    float *mu = nullptr, *sd = nullptr, *nu = nullptr, *td = nullptr, *colvar = nullptr;
+    int *kvec = nullptr;
+    double *mom = nullptr;
+    float pi_over_L = 0.f;
     float *featF = nullptr, *featL = nullptr, *X = nullptr, *Y = nullptr, *qplain = nullptr;
     void *Qs = nullptr;
     int *untrusted = nullptr;
@@ -194,6 +239,9 @@ void sur_free(ef_surrogate_s *s)
     cudaFree(s->sd);
     cudaFree(s->nu);
     cudaFree(s->td);
+    cudaFree(s->colvar);
+    cudaFree(s->kvec);
+    cudaFree(s->mom);
     cudaFree(s->featF);
     cudaFree(s->featL);
     cudaFree(s->X);
@@ -207,21 +255,24 @@ void sur_free(ef_surrogate_s *s)
     delete s;
 }
 
-// feature slot of k = 0: the canonical-half ordering of ef_features, K = EF_FEATURE_K
-int zero_slot(int d)
+// the feature modes in ef_features order (canonical half, K = EF_FEATURE_K); returns the slot of 0
+int mode_list(int d, std::vector<int> &kv)
 {
     const int K = EF_FEATURE_K;
-    int slot = 0;
+    int zero = -1;
+    kv.clear();
     for (int k0 = -K; k0 <= K; ++k0)
         for (int k1 = -K; k1 <= K; ++k1)
             for (int k2 = 0; k2 <= K; ++k2) {
                 if (k0 * k0 + k1 * k1 + k2 * k2 > K * K) continue;
                 if (!(k2 > 0 || (k2 == 0 && (k1 > 0 || (k1 == 0 && k0 >= 0))))) continue;
                 if (d == 2 && (k2 != 0 || k1 < 0)) continue;
-                if (k0 == 0 && k1 == 0 && k2 == 0) return slot;
-                ++slot;
+                if (k0 == 0 && k1 == 0 && k2 == 0) zero = (int)kv.size() / 3;
+                kv.push_back(k0);
+                kv.push_back(k1);
+                kv.push_back(k2);
             }
-    return -1;
+    return zero;
 }
 
 }  // namespace
@@ -250,7 +301,9 @@ ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, e
     s->max_batch = max_batch;
     s->nf = nf;
     s->noutp = (int)info[6];
-    s->idx0 = zero_slot(v.d);
+    std::vector<int> kv;
+    s->idx0 = mode_list(v.d, kv);
+    s->pi_over_L = (float)(3.14159265358979323846 / v.L);
     const int64_t cell = v.d == 3 ? (int64_t)v.N * v.N * v.N : (int64_t)v.N * v.N;
     const size_t el = v.prec == EF_PREC_F32 ? 4 : 8;
     cudaError_t e = cudaSuccess;
@@ -262,6 +315,9 @@ ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, e
     alloc((void **)&s->sd, kStride * 4);
     alloc((void **)&s->nu, kStride * 4);
     alloc((void **)&s->td, kStride * 4);
+    alloc((void **)&s->colvar, kStride * 4);
+    alloc((void **)&s->kvec, kv.size() * 4);
+    alloc((void **)&s->mom, (size_t)max_batch * EF_DIAG_STRIDE * 8);
     alloc((void **)&s->featF, (size_t)max_batch * kStride * 4);
     alloc((void **)&s->featL, (size_t)max_batch * kStride * 4);
     alloc((void **)&s->X, (size_t)max_batch * kStride * 4);
@@ -275,6 +331,11 @@ ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, e
     if (e != cudaSuccess) {
         sur_free(s);
         return scuda(e, "surrogate allocation");
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(s->kvec, kv.data(), kv.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        sur_free(s);
+        return scuda(e, "surrogate mode table");
     }
     // identity normalisation until fitted
     std::vector<float> one(kStride, 1.f);
@@ -291,22 +352,30 @@ ef_status ef_surrogate_destroy(ef_surrogate_t s)
     return EF_OK;
 }
 
-ef_status ef_surrogate_fit_stats(ef_surrogate_t s, const float *featF, const float *featQ, int64_t n, ef_stream_t stream)
+ef_status ef_surrogate_fit_stats(ef_surrogate_t s, const float *featF, const float *featQ, const double *mom, float *Xt,
+                                 float *Yt, int64_t n, ef_stream_t stream)
 {
-    if (!s || !featF || !featQ || n <= 0) return sfail(EF_ERR_INVALID_ARG, "bad surrogate statistics arguments");
-    stats_kernel<<<(s->nf + 127) / 128, 128, 0, (cudaStream_t)stream>>>(featF, featQ, n, s->nf, s->idx0, s->mu, s->sd,
-                                                                          s->nu, s->td);
+    if (!s || !featF || !featQ || !mom || !Xt || !Yt || n <= 0) return sfail(EF_ERR_INVALID_ARG, "bad surrogate statistics arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nm = s->nf / 2;
+    prep_kernel<<<sgrid(n * nm), 256, 0, st>>>(featF, featQ, mom, s->kvec, n, nm, s->idx0, s->pi_over_L, Xt, Yt);
+    stats_kernel<<<(s->nf + 127) / 128, 128, 0, st>>>(Xt, Yt, n, s->nf, s->mu, s->sd, s->nu, s->colvar);
+    scale_kernel<<<1, 1, 0, st>>>(s->colvar, s->nf, s->td);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EF_OK : scuda(e, "stats");
 }
 
-ef_status ef_surrogate_normalize(ef_surrogate_t s, const float *featF, const float *featQ, float *X, float *Y, int64_t n,
-                                 ef_stream_t stream)
+ef_status ef_surrogate_normalize(ef_surrogate_t s, const float *featF, const float *featQ, const double *mom, float *X,
+                                 float *Y, int64_t n, ef_stream_t stream)
 {
-    if (!s || !featF || !X || n < 0) return sfail(EF_ERR_INVALID_ARG, "bad normalisation arguments");
+    if (!s || !featF || !mom || !X || n < 0) return sfail(EF_ERR_INVALID_ARG, "bad normalisation arguments");
     if (n == 0) return EF_OK;
-    normalize_kernel<<<sgrid(n * s->nf), 256, 0, (cudaStream_t)stream>>>(featF, featQ, n, s->nf, s->idx0, s->mu, s->sd,
-                                                                          s->nu, s->td, X, Y);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nm = s->nf / 2;
+    const bool withY = featQ && Y;
+    prep_kernel<<<sgrid(n * nm), 256, 0, st>>>(featF, withY ? featQ : nullptr, mom, s->kvec, n, nm, s->idx0, s->pi_over_L,
+                                               X, withY ? Y : nullptr);
+    standardize_kernel<<<sgrid(n * s->nf), 256, 0, st>>>(X, withY ? Y : nullptr, n, s->nf, s->mu, s->sd, s->nu, s->td);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EF_OK : scuda(e, "normalise");
 }
@@ -338,7 +407,9 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
     if (r != EF_OK) return r;
     r = ef_features(s->plan, F, s->featL, ncells, 1, stream);
     if (r != EF_OK) return r;
-    r = ef_surrogate_normalize(s, s->featF, nullptr, s->X, nullptr, ncells, stream);
+    r = ef_moments_entropy(s->plan, F, nullptr, s->mom, ncells, stream);
+    if (r != EF_OK) return r;
+    r = ef_surrogate_normalize(s, s->featF, nullptr, s->mom, s->X, nullptr, ncells, stream);
     if (r != EF_OK) return r;
     r = ef_mlp_forward(s->mlp, s->X, kStride, s->Y, s->noutp, ncells, stream);
     if (r != EF_OK) return r;
@@ -346,7 +417,8 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
     if (e == cudaSuccess) e = cudaMemsetAsync(s->untrusted, 0, 4, st);
     if (e != cudaSuccess) return scuda(e, "surrogate reset");
     decode_gate_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(
-        s->Y, s->noutp, s->featF, s->featL, ncells, s->nf, s->idx0, s->nu, s->td, s->X, s->xmax, (float)cell,
+        s->Y, s->noutp, s->featF, s->featL, s->mom, s->kvec, s->pi_over_L, ncells, s->nf, s->idx0, s->nu, s->td, s->X,
+        s->xmax, (float)cell,
         audit_fraction, seed, qfeat, flags, s->count, s->list_off, s->list_id, cell);
     for (int round = 0; round < 2; ++round) {
         // plain operator on the listed cells (count read on the device), then their band

@@ -126,14 +126,17 @@ def bkw_family_torch(N: int, L: float, ncells: int, seed: int = 4321, device="cu
     v1 = (torch.arange(N, device=device, dtype=torch.float64) - N // 2) * h
     if out is None:
         out = torch.empty((ncells, N, N, N), device=device, dtype=dtype)
-    tt = torch.as_tensor(t0 * rho, device=device)
-    S = 1.0 - 2.0 * torch.exp(-tt / 6.0) / 5.0
-    for i in range(ncells):
-        x = (v1 - float(u[i, 0])) ** 2
-        y = (v1 - float(u[i, 1])) ** 2
-        z = (v1 - float(u[i, 2])) ** 2
-        v2 = (x[:, None, None] + y[None, :, None] + z[None, None, :]) / float(theta[i])
-        s = S[i]
-        f = torch.exp(-v2 / (2 * s)) / (2 * np.pi * s) ** 1.5 * ((5 * s - 3) / (2 * s) + (1 - s) / (2 * s * s) * v2)
-        out[i] = (float(rho[i]) * float(theta[i]) ** -1.5 * f).to(dtype)
+    for c0 in range(0, ncells, 256):
+        c1 = min(ncells, c0 + 256)
+        uu = torch.as_tensor(u[c0:c1], device=device)
+        th = torch.as_tensor(theta[c0:c1], device=device)[:, None, None, None]
+        rh = torch.as_tensor(rho[c0:c1], device=device)[:, None, None, None]
+        S = 1.0 - 2.0 * torch.exp(-torch.as_tensor(t0[c0:c1] * rho[c0:c1], device=device) / 6.0) / 5.0
+        S = S[:, None, None, None]
+        x = (v1[None, :] - uu[:, 0:1]) ** 2
+        y = (v1[None, :] - uu[:, 1:2]) ** 2
+        z = (v1[None, :] - uu[:, 2:3]) ** 2
+        v2 = (x[:, :, None, None] + y[:, None, :, None] + z[:, None, None, :]) / th
+        f = torch.exp(-v2 / (2 * S)) / (2 * np.pi * S) ** 1.5 * ((5 * S - 3) / (2 * S) + (1 - S) / (2 * S * S) * v2)
+        out[c0:c1] = (rh * th ** -1.5 * f).to(dtype)
     return out

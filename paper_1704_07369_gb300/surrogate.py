@@ -13,7 +13,8 @@ import math
 import numpy as np
 import torch
 
-from . import (EF_FEATURE_STRIDE, EF_KERNEL_HARD_SPHERE, EF_PREC_F32, MLP, Plan, Surrogate, ef_features)
+from . import (EF_DIAG_STRIDE, EF_FEATURE_STRIDE, EF_KERNEL_HARD_SPHERE, EF_PREC_F32, MLP, Plan, Surrogate,
+               ef_features, ef_moments_entropy)
 from . import inputs
 
 
@@ -22,10 +23,12 @@ def make_plan(kernel=EF_KERNEL_HARD_SPHERE, N=32, L=8.0, R=32, prec=EF_PREC_F32)
 
 
 def features_of_family(plan, ncells, seed, chunk=2048, device="cuda"):
-    """(featF, featQ) [ncells, EF_FEATURE_STRIDE] of BKW-family cells and of Q^sigma of them."""
+    """(featF, featQ, mom): features [ncells, EF_FEATURE_STRIDE] of BKW-family cells and of Q^sigma
+    of them, and the cells' moments [ncells, EF_DIAG_STRIDE] (FP64)."""
     N, L = plan.N, plan.L
     featF = torch.zeros(ncells, EF_FEATURE_STRIDE, device=device)
     featQ = torch.zeros(ncells, EF_FEATURE_STRIDE, device=device)
+    mom = torch.zeros(ncells, EF_DIAG_STRIDE, dtype=torch.float64, device=device)
     F = torch.empty(chunk, N, N, N, device=device)
     Q = torch.empty_like(F)
     for c0 in range(0, ncells, chunk):
@@ -34,8 +37,9 @@ def features_of_family(plan, ncells, seed, chunk=2048, device="cuda"):
         plan.collide(F, Q, ncells=n)
         ef_features(plan.handle, F, featF[c0:c0 + n], n)
         ef_features(plan.handle, Q, featQ[c0:c0 + n], n)
+        ef_moments_entropy(plan.handle, F, None, mom[c0:c0 + n], n)
     torch.cuda.synchronize()
-    return featF, featQ
+    return featF, featQ, mom
 
 
 def loss_mask(nfeat_floats, zero_slot, device="cuda"):
@@ -71,12 +75,12 @@ class Trainer:
         self.sur = Surrogate(plan, self.mlp, max_infer_batch)
         self.wmask = loss_mask(self.nf, zero_slot())
 
-    def fit(self, featF, featQ, epochs=20, lr0=1e-3, lr1=1e-5, seed=0, log=None):
+    def fit(self, featF, featQ, mom, epochs=20, lr0=1e-3, lr1=1e-5, seed=0, log=None):
         n = featF.shape[0] // self.batch * self.batch
-        self.sur.fit_stats(featF, featQ, featF.shape[0])
         X = torch.zeros(featF.shape[0], EF_FEATURE_STRIDE, device=featF.device)
         Y = torch.zeros_like(X)
-        self.sur.normalize(featF, featQ, X, Y, featF.shape[0])
+        self.sur.fit_stats(featF, featQ, mom, X, Y, featF.shape[0])
+        self.sur.normalize(featF, featQ, mom, X, Y, featF.shape[0])
         loss = torch.zeros(1, device=featF.device)
         g = torch.Generator(device="cpu")
         g.manual_seed(seed)

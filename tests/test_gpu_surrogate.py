@@ -121,7 +121,10 @@ def test_surrogate_audit_and_fallback_paths():
     ef.ef_features(plan.handle, Q, ref, n)
     fF = torch.zeros_like(ref)
     ef.ef_features(plan.handle, F, fF, n)
-    sur.fit_stats(fF, ref, n)
+    mom = torch.zeros(n, ef.EF_DIAG_STRIDE, dtype=torch.float64, device="cuda")
+    ef.ef_moments_entropy(plan.handle, F, None, mom, n)
+    Xt, Yt = torch.zeros_like(ref), torch.zeros_like(ref)
+    sur.fit_stats(fF, ref, mom, Xt, Yt, n)
     q = torch.zeros_like(ref)
     flags = torch.zeros(n, dtype=torch.int32, device="cuda")
     sur.infer(F, q, flags, n, audit_fraction=1.0, seed=5, tol=1e-3)
