@@ -172,15 +172,16 @@ ef_status ef_mlp_params(ef_mlp_t mlp, float *host, int set);
  * >= padded nout and even.  batch a multiple of 64, <= max_batch. */
 ef_status ef_mlp_forward(ef_mlp_t mlp, const float *X, int ldx, float *Y, int ldy, int64_t batch, ef_stream_t stream);
 
-/* Mean squared error against T (row stride ldt >= nout) over the nout outputs, each weighted by
- * wmask[j] (nullable = 1): loss_dev[0] = sum_b sum_j w_j (y - t)^2 / (batch nout); gradients of the
- * loss into the MLP's gradient buffer and, if grad_dev is not null, copied there (info[4] floats). */
+/* Mean squared error against T (row stride ldt >= nout) over the nout outputs, weighted by
+ * wmask[j] (per output, nullable = 1) and rowweight[b] (per sample, nullable = 1):
+ * loss_dev[0] = sum_b sum_j w_j r_b (y - t)^2 / (batch nout); gradients of the loss into the MLP's
+ * gradient buffer and, if grad_dev is not null, copied there (info[4] floats). */
 ef_status ef_mlp_grad(ef_mlp_t mlp, const float *X, int ldx, const float *T, int ldt, const float *wmask,
-                      int64_t batch, float *loss_dev, float *grad_dev, ef_stream_t stream);
+                      const float *rowweight, int64_t batch, float *loss_dev, float *grad_dev, ef_stream_t stream);
 
 /* ef_mlp_grad followed by one Adam step with learning rate lr. */
 ef_status ef_mlp_train_step(ef_mlp_t mlp, const float *X, int ldx, const float *T, int ldt, const float *wmask,
-                            int64_t batch, float lr, float *loss_dev, ef_stream_t stream);
+                            const float *rowweight, int64_t batch, float lr, float *loss_dev, ef_stream_t stream);
 
 /* The surrogate path (config: learned map from F's low modes to Q^sigma's low modes).  Built on a
  * uniform plan (whose ef_features define the band) and an MLP with nin = nout = 2 x (feature modes).
@@ -195,9 +196,11 @@ ef_status ef_surrogate_destroy(ef_surrogate_t sur);
  * each).  With m = Fh_0 and u = momentum / mass, each mode is de-translated and mass-normalised,
  * x_k = Fh_k e^{i pi k.u/L} / m and y_k = Qh_k e^{i pi k.u/L} / m^2 (the operator is quadratic in F and
  * commutes with velocity shifts up to aliasing); then per-column mean and std of x, per-column mean
- * of y and one global scale of y.  Xt, Yt: caller scratch of n x EF_FEATURE_STRIDE floats. */
+ * of y and one global scale of y.  Xt, Yt: caller scratch of n x EF_FEATURE_STRIDE floats.  If
+ * rowweight (n floats) is not null it receives per-sample loss weights proportional to 1 / |y_b|^2
+ * (mean 1), which make the training loss the per-cell relative error. */
 ef_status ef_surrogate_fit_stats(ef_surrogate_t sur, const float *featF, const float *featQ, const double *mom,
-                                 float *Xt, float *Yt, int64_t n, ef_stream_t stream);
+                                 float *Xt, float *Yt, float *rowweight, int64_t n, ef_stream_t stream);
 
 /* Normalised MLP inputs X (and targets Y, if featQ and Y are not null), EF_FEATURE_STRIDE per row. */
 ef_status ef_surrogate_normalize(ef_surrogate_t sur, const float *featF, const float *featQ, const double *mom,

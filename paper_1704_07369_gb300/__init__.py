@@ -87,11 +87,11 @@ def lib():
         L.ef_mlp_info.argtypes = [vp, ctypes.POINTER(i64)]
         L.ef_mlp_params.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_mlp_forward.argtypes = [vp, vp, i32, vp, i32, i64, vp]
-        L.ef_mlp_grad.argtypes = [vp, vp, i32, vp, i32, vp, i64, vp, vp, vp]
-        L.ef_mlp_train_step.argtypes = [vp, vp, i32, vp, i32, vp, i64, ctypes.c_float, vp, vp]
+        L.ef_mlp_grad.argtypes = [vp, vp, i32, vp, i32, vp, vp, i64, vp, vp, vp]
+        L.ef_mlp_train_step.argtypes = [vp, vp, i32, vp, i32, vp, vp, i64, ctypes.c_float, vp, vp]
         L.ef_surrogate_create.argtypes = [vp, vp, i64, pp]
         L.ef_surrogate_destroy.argtypes = [vp]
-        L.ef_surrogate_fit_stats.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
+        L.ef_surrogate_fit_stats.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp]
         L.ef_surrogate_normalize.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         L.ef_surrogate_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
@@ -197,13 +197,13 @@ class MLP:
     def forward(self, X, Y, batch, stream=None):
         _check(lib().ef_mlp_forward(self.handle, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0), int(batch), _stream(stream)))
 
-    def grad(self, X, T, batch, loss, grad=None, wmask=None, stream=None):
-        _check(lib().ef_mlp_grad(self.handle, _ptr(X), X.stride(0), _ptr(T), T.stride(0), _ptr(wmask), int(batch),
-                                 _ptr(loss), _ptr(grad), _stream(stream)))
+    def grad(self, X, T, batch, loss, grad=None, wmask=None, rowweight=None, stream=None):
+        _check(lib().ef_mlp_grad(self.handle, _ptr(X), X.stride(0), _ptr(T), T.stride(0), _ptr(wmask),
+                                 _ptr(rowweight), int(batch), _ptr(loss), _ptr(grad), _stream(stream)))
 
-    def train_step(self, X, T, batch, lr, loss, wmask=None, stream=None):
+    def train_step(self, X, T, batch, lr, loss, wmask=None, rowweight=None, stream=None):
         _check(lib().ef_mlp_train_step(self.handle, _ptr(X), X.stride(0), _ptr(T), T.stride(0), _ptr(wmask),
-                                       int(batch), float(lr), _ptr(loss), _stream(stream)))
+                                       _ptr(rowweight), int(batch), float(lr), _ptr(loss), _stream(stream)))
 
     def layout(self):
         """[(W offset, out_p, in_p, b offset)] of the padded FP32 parameter vector."""
@@ -236,9 +236,9 @@ class Surrogate:
         _check(lib().ef_surrogate_create(plan.handle, mlp.handle, int(max_batch), ctypes.byref(self.handle)))
         self.max_batch = int(max_batch)
 
-    def fit_stats(self, featF, featQ, mom, Xt, Yt, n, stream=None):
+    def fit_stats(self, featF, featQ, mom, Xt, Yt, n, rowweight=None, stream=None):
         _check(lib().ef_surrogate_fit_stats(self.handle, _ptr(featF), _ptr(featQ), _ptr(mom), _ptr(Xt), _ptr(Yt),
-                                            int(n), _stream(stream)))
+                                            _ptr(rowweight), int(n), _stream(stream)))
 
     def normalize(self, featF, featQ, mom, X, Y, n, stream=None):
         _check(lib().ef_surrogate_normalize(self.handle, _ptr(featF), _ptr(featQ), _ptr(mom), _ptr(X), _ptr(Y),

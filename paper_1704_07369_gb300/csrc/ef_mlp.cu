@@ -185,8 +185,8 @@ __global__ void pack_input_kernel(const float *X, int ldx, int nin, int ninp, in
 
 // MSE loss over the first nout outputs (optionally weighted): loss = sum w_j (y - t)^2 / (B n_w),
 // dY = 2 w_j (y - t) / (B n_w) in bf16 [B][noutp] and [noutp][B] (pad rows zero).
-__global__ void mse_kernel(const float *Y, int ldy_pred, const float *T, int ldt, const float *wmask, int nout, int noutp,
-                           int64_t B, float inv_count, bf16 *dY, bf16 *dYT, float *loss)
+__global__ void mse_kernel(const float *Y, int ldy_pred, const float *T, int ldt, const float *wmask, const float *roww,
+                           int nout, int noutp, int64_t B, float inv_count, bf16 *dY, bf16 *dYT, float *loss)
 {
     float acc = 0.f;
     const int64_t total = B * noutp;
@@ -195,7 +195,7 @@ __global__ void mse_kernel(const float *Y, int ldy_pred, const float *T, int ldt
         const int j = (int)(i % noutp);
         float g = 0.f;
         if (j < nout) {
-            const float w = wmask ? wmask[j] : 1.f;
+            const float w = (wmask ? wmask[j] : 1.f) * (roww ? roww[b] : 1.f);
             const float d = Y[b * ldy_pred + j] - T[b * ldt + j];
             acc += w * d * d;
             g = 2.f * w * d * inv_count;
@@ -502,8 +502,8 @@ ef_status ef_mlp_forward(ef_mlp_t n, const float *X, int ldx, float *Y, int ldy,
 }
 
 // loss and gradients (into the MLP's gradient buffer); optionally the Adam update
-static ef_status mlp_grad_impl(ef_mlp_s *n, const float *X, int ldx, const float *T, int ldt, const float *wmask, int64_t B,
-                               float *loss_dev, cudaStream_t s)
+static ef_status mlp_grad_impl(ef_mlp_s *n, const float *X, int ldx, const float *T, int ldt, const float *wmask,
+                               const float *roww, int64_t B, float *loss_dev, cudaStream_t s)
 {
     pack_input_kernel<<<grid_for(B * n->ninp), 256, 0, s>>>(X, ldx, n->nin, n->ninp, B, n->Xb, n->XbT);
     // forward (last layer's fp32 output into dA as scratch)
@@ -514,7 +514,7 @@ static ef_status mlp_grad_impl(ef_mlp_s *n, const float *X, int ldx, const float
     (void)nw;
     cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(float), s);
     if (e != cudaSuccess) return cuda_err(e, "loss reset");
-    mse_kernel<<<grid_for(B * n->noutp), 256, 0, s>>>(n->dA, n->noutp, T, ldt, wmask, n->nout, n->noutp, B,
+    mse_kernel<<<grid_for(B * n->noutp), 256, 0, s>>>(n->dA, n->noutp, T, ldt, wmask, roww, n->nout, n->noutp, B,
                                                        1.f / ((float)B * (float)n->nout), n->dY, n->dYT, loss_dev);
     // backward
     for (int l = n->nl - 1; l >= 0; --l) {
@@ -554,14 +554,14 @@ static ef_status mlp_grad_impl(ef_mlp_s *n, const float *X, int ldx, const float
     return EF_OK;
 }
 
-ef_status ef_mlp_grad(ef_mlp_t n, const float *X, int ldx, const float *T, int ldt, const float *wmask, int64_t B,
-                      float *loss_dev, float *grad_dev, ef_stream_t stream)
+ef_status ef_mlp_grad(ef_mlp_t n, const float *X, int ldx, const float *T, int ldt, const float *wmask,
+                      const float *rowweight, int64_t B, float *loss_dev, float *grad_dev, ef_stream_t stream)
 {
     if (!n || !X || !T || !loss_dev) return mlp_fail(EF_ERR_INVALID_ARG, "null argument");
     if (B <= 0 || B % 64 || B > n->max_batch) return mlp_fail(EF_ERR_INVALID_ARG, "batch must be a multiple of 64 <= max_batch");
     if (ldx < n->nin || ldt < n->nout) return mlp_fail(EF_ERR_INVALID_ARG, "ldx >= nin, ldt >= nout");
     cudaStream_t s = (cudaStream_t)stream;
-    ef_status st = mlp_grad_impl(n, X, ldx, T, ldt, wmask, B, loss_dev, s);
+    ef_status st = mlp_grad_impl(n, X, ldx, T, ldt, wmask, rowweight, B, loss_dev, s);
     if (st != EF_OK) return st;
     if (grad_dev) {
         cudaError_t e = cudaMemcpyAsync(grad_dev, n->g, n->nparams * 4, cudaMemcpyDeviceToDevice, s);
@@ -570,10 +570,10 @@ ef_status ef_mlp_grad(ef_mlp_t n, const float *X, int ldx, const float *T, int l
     return EF_OK;
 }
 
-ef_status ef_mlp_train_step(ef_mlp_t n, const float *X, int ldx, const float *T, int ldt, const float *wmask, int64_t B,
-                            float lr, float *loss_dev, ef_stream_t stream)
+ef_status ef_mlp_train_step(ef_mlp_t n, const float *X, int ldx, const float *T, int ldt, const float *wmask,
+                            const float *rowweight, int64_t B, float lr, float *loss_dev, ef_stream_t stream)
 {
-    ef_status st = ef_mlp_grad(n, X, ldx, T, ldt, wmask, B, loss_dev, nullptr, stream);
+    ef_status st = ef_mlp_grad(n, X, ldx, T, ldt, wmask, rowweight, B, loss_dev, nullptr, stream);
     if (st != EF_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     n->step += 1;

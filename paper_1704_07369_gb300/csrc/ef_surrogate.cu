@@ -99,6 +99,31 @@ __global__ void scale_kernel(const float *colvar, int nf, float *td)
     for (int j = 0; j < kStride; ++j) td[j] = t;
 }
 
+// per-sample weights 1 / (|y_b|^2 / nf), then normalised to mean 1 by the caller's second pass
+__global__ void rowweight_kernel(const float *Yt, int64_t n, int nf, float *rw)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = 0.0;
+    for (int j = 0; j < nf; ++j) acc += (double)Yt[i * kStride + j] * Yt[i * kStride + j];
+    rw[i] = (float)(1.0 / (acc / nf + 1e-30));
+}
+
+__global__ void rowweight_norm_kernel(int64_t n, float *rw)
+{
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += rw[i];
+    __shared__ double red[256];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+        if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+        __syncthreads();
+    }
+    const float scale = (float)(n / red[0]);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) rw[i] *= scale;
+}
+
 __global__ void standardize_kernel(float *X, float *Y, int64_t n, int nf, const float *mu, const float *sd, const float *nu,
                                    const float *td)
 {
@@ -353,7 +378,7 @@ ef_status ef_surrogate_destroy(ef_surrogate_t s)
 }
 
 ef_status ef_surrogate_fit_stats(ef_surrogate_t s, const float *featF, const float *featQ, const double *mom, float *Xt,
-                                 float *Yt, int64_t n, ef_stream_t stream)
+                                 float *Yt, float *rowweight, int64_t n, ef_stream_t stream)
 {
     if (!s || !featF || !featQ || !mom || !Xt || !Yt || n <= 0) return sfail(EF_ERR_INVALID_ARG, "bad surrogate statistics arguments");
     cudaStream_t st = (cudaStream_t)stream;
@@ -361,6 +386,10 @@ ef_status ef_surrogate_fit_stats(ef_surrogate_t s, const float *featF, const flo
     prep_kernel<<<sgrid(n * nm), 256, 0, st>>>(featF, featQ, mom, s->kvec, n, nm, s->idx0, s->pi_over_L, Xt, Yt);
     stats_kernel<<<(s->nf + 127) / 128, 128, 0, st>>>(Xt, Yt, n, s->nf, s->mu, s->sd, s->nu, s->colvar);
     scale_kernel<<<1, 1, 0, st>>>(s->colvar, s->nf, s->td);
+    if (rowweight) {
+        rowweight_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Yt, n, s->nf, rowweight);
+        rowweight_norm_kernel<<<1, 256, 0, st>>>(n, rowweight);
+    }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EF_OK : scuda(e, "stats");
 }

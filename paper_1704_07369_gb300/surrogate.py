@@ -79,7 +79,8 @@ class Trainer:
         n = featF.shape[0] // self.batch * self.batch
         X = torch.zeros(featF.shape[0], EF_FEATURE_STRIDE, device=featF.device)
         Y = torch.zeros_like(X)
-        self.sur.fit_stats(featF, featQ, mom, X, Y, featF.shape[0])
+        rw = torch.zeros(featF.shape[0], device=featF.device)
+        self.sur.fit_stats(featF, featQ, mom, X, Y, featF.shape[0], rowweight=rw)
         self.sur.normalize(featF, featQ, mom, X, Y, featF.shape[0])
         loss = torch.zeros(1, device=featF.device)
         g = torch.Generator(device="cpu")
@@ -89,12 +90,12 @@ class Trainer:
         step = 0
         for ep in range(epochs):
             perm = torch.randperm(featF.shape[0], generator=g)[:n].to(featF.device)
-            Xs, Ys = X[perm], Y[perm]
+            Xs, Ys, Rs = X[perm], Y[perm], rw[perm]
             tot = torch.zeros(1, device=featF.device)
             for b0 in range(0, n, self.batch):
                 lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * step / max(1, steps)))
                 self.mlp.train_step(Xs[b0:b0 + self.batch], Ys[b0:b0 + self.batch], self.batch, lr, loss,
-                                    wmask=self.wmask)
+                                    wmask=self.wmask, rowweight=Rs[b0:b0 + self.batch])
                 tot += loss
                 step += 1
             hist.append(float(tot.item()) / (n // self.batch))
