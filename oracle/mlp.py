@@ -3,10 +3,11 @@
 TEST INFRASTRUCTURE (same rules as the rest of ``oracle/``).
 
 x -> relu(W_0 x + b_0) -> ... -> W_{L-1} h + b_{L-1}; loss = sum_j w_j (y_j - t_j)^2 / (B n_out).
-With ``bf16=True`` the values the library stores in bfloat16 (inputs, weights, hidden activations,
-output and hidden gradients) are rounded to bfloat16 (round to nearest even) at the same points, so
-the comparison isolates accumulation order; with ``bf16=False`` it is exact FP64 backpropagation,
-pinned against central finite differences in the tests.
+With ``bf16=True`` the values the library stores in bfloat16 are rounded the same way (round to
+nearest even): weights to bf16; every layer input (features and hidden activations) to the split
+pair bf16(a) + bf16(a - bf16(a)); output and hidden gradients to bf16.  The comparison then isolates
+accumulation order.  With ``bf16=False`` it is exact FP64 backpropagation, pinned against central
+finite differences in the tests.
 """
 from __future__ import annotations
 
@@ -19,6 +20,13 @@ def bf16(x: np.ndarray) -> np.ndarray:
     u = f.view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def split(x: np.ndarray) -> np.ndarray:
+    """The library's split-precision layer input: bf16(x) + bf16(x - bf16(x)) (FP32 differences)."""
+    hi = bf16(x)
+    lo = bf16(np.asarray(x, dtype=np.float32).astype(np.float64) - hi)
+    return hi + lo
 
 
 def unpack(params: np.ndarray, layout):
@@ -34,14 +42,15 @@ def unpack(params: np.ndarray, layout):
 def forward(layers, X, bf=True):
     """Returns (y, cache) for a batch X [B, n_in_padded]."""
     r = bf16 if bf else (lambda v: np.asarray(v, dtype=np.float64))
-    h = r(X)
+    sp = split if bf else (lambda v: np.asarray(v, dtype=np.float64))
+    h = sp(X)
     cache = [h]
     pres = []
     for li, (W, b) in enumerate(layers):
         pre = h @ r(W).T + b
         pres.append(pre)
         if li + 1 < len(layers):
-            h = r(np.maximum(pre, 0.0))
+            h = sp(np.maximum(pre, 0.0).astype(np.float32) if bf else np.maximum(pre, 0.0))
             cache.append(h)
         else:
             h = pre

@@ -6,6 +6,10 @@
 // and an FP32 accumulator, on the tensor cores (mma.sync m16n8k16 bf16), 64 x 64 block tiles,
 // cp.async double buffering and ldmatrix fragment loads.  Backward products use the transposed
 // copies the forward pass and the optimizer write alongside (activations^T, W^T).
+// Split precision: every layer input a (the features and each hidden activation) is stored as two
+// bf16 halves, hi = bf16(a) and lo = bf16(a - hi), side by side, and multiplied against the weights
+// duplicated [bf16(W) | bf16(W)], so that a forward product sees a to about 16 mantissa bits while
+// both tensor-core operands stay bf16.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -63,6 +67,7 @@ struct GemmArgs {
     int ldcb;
     bf16 *CbT;          // nullable bf16 transposed out [N][ldcbt]
     int ldcbt;
+    int lo_off;         // > 0: also write the low halves a - bf16(a) at column / row + lo_off
 };
 
 // 4 warps in 2 x 2, each 32 x 32 (2 m16 x 4 n8 tiles).  M % 64 == N % 64 == K % 32 == 0.
@@ -152,11 +157,21 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const GemmArgs g)
                     v0 = fmaxf(v0, 0.f);
                     v1 = fmaxf(v1, 0.f);
                 }
-                if (g.Cb)
-                    *reinterpret_cast<__nv_bfloat162 *>(g.Cb + (size_t)row * g.ldcb + col) = __floats2bfloat162_rn(v0, v1);
+                const bf16 h0 = __float2bfloat16(v0), h1 = __float2bfloat16(v1);
+                const bf16 l0 = __float2bfloat16(v0 - __bfloat162float(h0)), l1 = __float2bfloat16(v1 - __bfloat162float(h1));
+                if (g.Cb) {
+                    *reinterpret_cast<__nv_bfloat162 *>(g.Cb + (size_t)row * g.ldcb + col) = __halves2bfloat162(h0, h1);
+                    if (g.lo_off)
+                        *reinterpret_cast<__nv_bfloat162 *>(g.Cb + (size_t)row * g.ldcb + g.lo_off + col) =
+                            __halves2bfloat162(l0, l1);
+                }
                 if (g.CbT) {
-                    g.CbT[(size_t)col * g.ldcbt + row] = __float2bfloat16(v0);
-                    g.CbT[(size_t)(col + 1) * g.ldcbt + row] = __float2bfloat16(v1);
+                    g.CbT[(size_t)col * g.ldcbt + row] = h0;
+                    g.CbT[(size_t)(col + 1) * g.ldcbt + row] = h1;
+                    if (g.lo_off) {
+                        g.CbT[(size_t)(g.lo_off + col) * g.ldcbt + row] = l0;
+                        g.CbT[(size_t)(g.lo_off + col + 1) * g.ldcbt + row] = l1;
+                    }
                 }
             }
 }
@@ -169,7 +184,8 @@ cudaError_t gemm(const GemmArgs &g, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// X (fp32 [B][ldx], first nin used) -> bf16 [B][ninp] and its transpose [ninp][B]; pad zeroed.
+// X (fp32 [B][ldx], first nin used) -> split bf16 [B][2 ninp] (hi | lo) and its transpose
+// [2 ninp][B]; pad zeroed.
 __global__ void pack_input_kernel(const float *X, int ldx, int nin, int ninp, int64_t B, bf16 *Xb, bf16 *XbT)
 {
     const int64_t total = B * ninp;
@@ -178,8 +194,23 @@ __global__ void pack_input_kernel(const float *X, int ldx, int nin, int ninp, in
         const int j = (int)(i % ninp);
         const float v = j < nin ? X[b * ldx + j] : 0.f;
         const bf16 h = __float2bfloat16(v);
-        Xb[i] = h;
-        if (XbT) XbT[(size_t)j * B + b] = h;
+        const bf16 l = __float2bfloat16(v - __bfloat162float(h));
+        Xb[b * 2 * ninp + j] = h;
+        Xb[b * 2 * ninp + ninp + j] = l;
+        if (XbT) {
+            XbT[(size_t)j * B + b] = h;
+            XbT[(size_t)(ninp + j) * B + b] = l;
+        }
+    }
+}
+
+// g[o][k] = dW2[o][k] + dW2[o][in + k]: the weight gradient of the tied hi / lo halves
+__global__ void fold_split_kernel(const float *dW2, int out, int in, float *g)
+{
+    const int64_t n = (int64_t)out * in;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(i / in), k = (int)(i % in);
+        g[i] = dW2[(size_t)o * 2 * in + k] + dW2[(size_t)o * 2 * in + in + k];
     }
 }
 
@@ -262,7 +293,8 @@ __global__ void adam_kernel(float *p, const float *g, float *m, float *v, int64_
         if (Wb) {
             const int o = (int)(i / in), k = (int)(i % in);
             const bf16 h = __float2bfloat16(pi);
-            Wb[i] = h;
+            Wb[(size_t)o * 2 * in + k] = h;
+            Wb[(size_t)o * 2 * in + in + k] = h;
             WbT[(size_t)k * out + o] = h;
         }
     }
@@ -274,7 +306,8 @@ __global__ void refresh_bf16_kernel(const float *p, int out, int in, bf16 *Wb, b
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int o = (int)(i / in), k = (int)(i % in);
         const bf16 h = __float2bfloat16(p[i]);
-        Wb[i] = h;
+        Wb[(size_t)o * 2 * in + k] = h;
+        Wb[(size_t)o * 2 * in + in + k] = h;
         WbT[(size_t)k * out + o] = h;
     }
 }
@@ -301,6 +334,7 @@ struct ef_mlp_s {
     std::vector<float *> pre;       // [B][out_l]
     std::vector<bf16 *> act, actT;  // [B][out_l], [out_l][B] (hidden layers)
     float *dA = nullptr;            // [B][max out] fp32
+    float *dW2 = nullptr;           // [max out][2 max in] fp32: gradient of the split halves
     bf16 *dY = nullptr, *dYT = nullptr;
     int64_t step = 0;
     int device = 0;
@@ -336,6 +370,7 @@ void mlp_free(ef_mlp_s *n)
     for (auto q : n->act) cudaFree(q);
     for (auto q : n->actT) cudaFree(q);
     cudaFree(n->dA);
+    cudaFree(n->dW2);
     cudaFree(n->dY);
     cudaFree(n->dYT);
     delete n;
@@ -347,21 +382,22 @@ ef_status mlp_forward_packed(ef_mlp_s *n, int64_t B, float *Yout, int ldy, bool 
     for (int l = 0; l < n->nl; ++l) {
         GemmArgs g{};
         g.A = l == 0 ? n->Xb : n->act[l - 1];
-        g.lda = n->din[l];
+        g.lda = 2 * n->din[l];
         g.B = n->Wb[l];
-        g.ldb = n->din[l];
+        g.ldb = 2 * n->din[l];
         g.M = (int)B;
         g.N = n->dout[l];
-        g.K = n->din[l];
+        g.K = 2 * n->din[l];
         g.bias = n->p + n->boff[l];
         const bool last = l + 1 == n->nl;
         g.relu = last ? 0 : 1;
         g.Cf = last ? Yout : n->pre[l];
         g.ldcf = last ? ldy : n->dout[l];
         g.Cb = last ? nullptr : n->act[l];
-        g.ldcb = n->dout[l];
+        g.ldcb = 2 * n->dout[l];
         g.CbT = (last || !keep_T) ? nullptr : n->actT[l];
         g.ldcbt = (int)B;
+        g.lo_off = n->dout[l];
         cudaError_t e = gemm(g, s);
         if (e != cudaSuccess) return cuda_err(e, "mlp gemm");
     }
@@ -424,15 +460,16 @@ ef_status ef_mlp_create(int nin, int nhidden, int nlayers, int nout, int64_t max
     n->actT.assign(nlayers, nullptr);
     int maxd = 0;
     for (int l = 0; l < nlayers; ++l) {
-        alloc((void **)&n->Wb[l], (size_t)n->dout[l] * n->din[l] * 2);
+        alloc((void **)&n->Wb[l], (size_t)n->dout[l] * 2 * n->din[l] * 2);
         alloc((void **)&n->WbT[l], (size_t)n->dout[l] * n->din[l] * 2);
         alloc((void **)&n->pre[l], (size_t)max_batch * n->dout[l] * 4);
-        alloc((void **)&n->act[l], (size_t)max_batch * n->dout[l] * 2);
-        alloc((void **)&n->actT[l], (size_t)max_batch * n->dout[l] * 2);
+        alloc((void **)&n->act[l], (size_t)max_batch * 2 * n->dout[l] * 2);
+        alloc((void **)&n->actT[l], (size_t)max_batch * 2 * n->dout[l] * 2);
         maxd = std::max(maxd, std::max(n->dout[l], n->din[l]));
     }
-    alloc((void **)&n->Xb, (size_t)max_batch * n->ninp * 2);
-    alloc((void **)&n->XbT, (size_t)max_batch * n->ninp * 2);
+    alloc((void **)&n->Xb, (size_t)max_batch * 2 * n->ninp * 2);
+    alloc((void **)&n->XbT, (size_t)max_batch * 2 * n->ninp * 2);
+    alloc((void **)&n->dW2, (size_t)maxd * 2 * maxd * 4);
     alloc((void **)&n->dA, (size_t)max_batch * maxd * 4);
     alloc((void **)&n->dY, (size_t)max_batch * maxd * 2);
     alloc((void **)&n->dYT, (size_t)max_batch * maxd * 2);
@@ -526,12 +563,13 @@ static ef_status mlp_grad_impl(ef_mlp_s *n, const float *X, int ldx, const float
         g.B = l == 0 ? n->XbT : n->actT[l - 1];
         g.ldb = (int)B;
         g.M = out;
-        g.N = in;
+        g.N = 2 * in;
         g.K = (int)B;
-        g.Cf = n->g + n->woff[l];
-        g.ldcf = in;
+        g.Cf = n->dW2;
+        g.ldcf = 2 * in;
         e = gemm(g, s);
         if (e != cudaSuccess) return cuda_err(e, "mlp grad gemm");
+        fold_split_kernel<<<grid_for((int64_t)out * in), 256, 0, s>>>(n->dW2, out, in, n->g + n->woff[l]);
         rowsum_kernel<<<out, 256, 0, s>>>(n->dYT, B, out, n->g + n->boff[l]);
         if (l == 0) break;
         // dA_{l-1} = dPre_l W_l:  M = B, N = in, K = out; A = dPre [B][out], B = W^T [in][out]

@@ -39,3 +39,11 @@ def test_bf16_rounding():
     assert mlp.bf16(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
     x = np.random.default_rng(0).normal(size=10000)
     assert np.max(np.abs(mlp.bf16(x) - x) / np.abs(x)) <= 2.0 ** -8
+
+
+def test_split_precision_pair():
+    x = np.random.default_rng(1).normal(size=10000).astype(np.float32).astype(np.float64)
+    y = mlp.split(x)
+    assert np.max(np.abs(y - x) / np.abs(x)) <= 2.0 ** -16
+    hi = mlp.bf16(x)
+    assert np.all(mlp.bf16(y - hi) == y - hi)      # the low half is itself a bf16 value
