@@ -364,13 +364,6 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             T x0[N], x1[N];
             load_row<T, N>(src0, x0);
             load_row<T, N>(src1, x1);
-            if (a.log_input) {
-#pragma unroll
-                for (int n = 0; n < N; ++n) {
-                    x0[n] = log_t<T>(x0[n] > T(1e-30) ? x0[n] : T(1e-30));
-                    x1[n] = log_t<T>(x1[n] > T(1e-30) ? x1[n] : T(1e-30));
-                }
-            }
             C2<T> X0[H], X1[H];
             r2c_pair<N, T>(x0, x1, X0, X1, tw);
 #pragma unroll
@@ -403,20 +396,6 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             for (int z = 0; z < N; ++z) fh[z] = cscale(fh[z], scale);
         }
         bar.war();
-
-        if (a.out_mode == OUT_FEATURES) {      // low-mode features only (surrogate input / target)
-            if (has_pencil) {
-#pragma unroll
-                for (int z = 0; z < N; ++z) {
-                    const int j = a.fidx[z * NP + pencil];
-                    if (j >= 0) {
-                        a.feat[cglob * a.fstride + 2 * j] = (float)fh[z].x;
-                        a.feat[cglob * a.fstride + 2 * j + 1] = (float)fh[z].y;
-                    }
-                }
-            }
-            continue;
-        }
 
         Diag dg;
         dg.reset();
@@ -618,41 +597,72 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 
 // ------------------------------------------------------------------ moments kernel ---------
 
-// One CTA per cell: FP64 moments / entropy of F (and entropy production with Q).
+// One CTA per cell: moments / entropy of F (and entropy production with Q), FP64 across the cell.
+// A warp walks rows (lanes along the contiguous axis, coalesced); each lane sums its values in T
+// over a run of at most 16 rows (at most 32 terms) and folds the run into FP64 accumulators, the
+// same split as the fused diagnostics of the collide kernel (no per-point FP64 work: the FP64 pipe
+// is a small fraction of the FP32 one).
 template <typename T, int D>
 __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, const int64_t *cell_off,
                                                       const int64_t *cell_N, int64_t ncells, int N_uniform,
                                                       double h_uniform_times_N, double *out)
 {
     __shared__ double red[8][kDiag];
+    constexpr int kRun = 16;
+    T big;
+    if constexpr (sizeof(T) == 4) big = T(3.0e38f);
+    else big = T(1.0e300);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int64_t c = blockIdx.x; c < ncells; c += gridDim.x) {
         const int N = cell_N ? (int)cell_N[c] : N_uniform;
-        const int64_t cell = (D == 3) ? (int64_t)N * N * N : (int64_t)N * N;
-        const int64_t coff = cell_off ? cell_off[c] : c * cell;
+        const int nrows = (D == 3) ? N * N : N;
+        const int64_t coff = cell_off ? cell_off[c] : c * (int64_t)nrows * N;
         const double h = h_uniform_times_N / N;
         double s[kDiag];
         for (int k = 0; k < kDiag; ++k) s[k] = 0.0;
-        double mn = 1e300, mq = 1e300;
-        for (int64_t i = threadIdx.x; i < cell; i += blockDim.x) {
-            const double f = (double)F[coff + i];
-            const int jx = (int)(i % N) - N / 2;
-            const int jy = (int)((i / N) % N) - N / 2;
-            const int jz = (D == 3) ? (int)(i / ((int64_t)N * N)) - N / 2 : 0;
-            s[0] += f;
-            if (D == 3) { s[1] += f * jz; s[2] += f * jy; s[3] += f * jx; }
-            else { s[1] += f * jy; s[2] += f * jx; }
-            s[4] += f * ((double)jx * jx + (double)jy * jy + (double)jz * jz);
-            if (f > 0) {
-                const double lf = log(f);
-                s[5] += f * lf;
-                if (Q) s[6] += (double)Q[coff + i] * lf;
+        T mn = big, mq = big;
+        T p0 = 0, pz = 0, py = 0, px = 0, pe = 0, peta = 0, pprod = 0;
+        int run = 0;
+        for (int r = warp; r < nrows; r += nw) {
+            const T jz = (D == 3) ? T(r / N - N / 2) : T(0);
+            const T jy = (D == 3) ? T(r % N - N / 2) : T(r - N / 2);
+            const T *Fr = F + coff + (int64_t)r * N;
+            const T *Qr = Q ? Q + coff + (int64_t)r * N : nullptr;
+            for (int x = lane; x < N; x += 32) {
+                const T f = Fr[x];
+                const T jx = T(x - N / 2);
+                p0 += f;
+                pz += f * jz;
+                py += f * jy;
+                px += f * jx;
+                pe += f * (jx * jx + jy * jy + jz * jz);
+                if (f > T(0)) {
+                    const T lf = log_t<T>(f);
+                    peta += f * lf;
+                    if (Qr) pprod += Qr[x] * lf;
+                }
+                mn = f < mn ? f : mn;
+                if (Qr) mq = Qr[x] < mq ? Qr[x] : mq;
             }
-            mn = fmin(mn, f);
-            if (Q) mq = fmin(mq, (double)Q[coff + i]);
+            if (++run == kRun || r + nw >= nrows) {
+                s[0] += (double)p0;
+                if (D == 3) {
+                    s[1] += (double)pz;
+                    s[2] += (double)py;
+                    s[3] += (double)px;
+                } else {
+                    s[1] += (double)py;
+                    s[2] += (double)px;
+                }
+                s[4] += (double)pe;
+                s[5] += (double)peta;
+                s[6] += (double)pprod;
+                p0 = pz = py = px = pe = peta = pprod = T(0);
+                run = 0;
+            }
         }
-        s[7] = mn;
-        s[9] = Q ? mq : 0.0;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        s[7] = (double)mn;
+        s[9] = Q ? (double)mq : 0.0;
         for (int k = 0; k < kDiag; ++k) {
             double v = s[k];
             for (int sh = 16; sh > 0; sh >>= 1) {
@@ -665,8 +675,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, co
         if (threadIdx.x < kDiag) {
             const int k = threadIdx.x;
             double v = red[0][k];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                v = (k == 7 || k == 9) ? fmin(v, red[w][k]) : v + red[w][k];
+            for (int w = 1; w < nw; ++w) v = (k == 7 || k == 9) ? fmin(v, red[w][k]) : v + red[w][k];
             const double hd = (D == 3) ? h * h * h : h * h;
             if (k == 0 || k == 5) v *= hd;
             else if (k >= 1 && k <= 3) v *= hd * h;

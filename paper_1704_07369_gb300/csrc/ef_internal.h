@@ -29,7 +29,7 @@ struct Op {
     int pad;
 };
 
-enum OutMode : int { OUT_COLLIDE = 0, OUT_EULER = 1, OUT_FEATURES = 2 };
+enum OutMode : int { OUT_COLLIDE = 0, OUT_EULER = 1 };
 
 constexpr int kMaxOps = 512;
 constexpr int kDiag = 10;
@@ -56,12 +56,24 @@ struct CollideArgs {
     unsigned long long *counter;  // nullable: dynamic cell queue (zeroed before the launch)
     int prefetch;             // 1: prefetch the next op's multipliers into L1
     int paired;               // 1: two spectral slabs per CTA and the paired op kinds
-    // OUT_FEATURES: write the forward transform at the listed modes instead of colliding
-    float *feat;              // [cell_id][fstride] (re, im) pairs
-    const int *fidx;          // [N * NP]: feature slot of spectral element (lz, p), or -1
-    int fstride;
-    int log_input;            // 1: transform ln(max(F, tiny)) instead of F
     const long long *dev_ncells;  // nullable: cell count read from device memory at kernel start
+};
+
+// Arguments of the low-mode feature kernel (one launch per size class).
+struct FeatArgs {
+    const void *F;                           // cells of N^d values (element type of the plan), 16-byte aligned
+    const int64_t *cell_off;                 // nullable: element offset of cell c (default c * N^d)
+    const int64_t *cell_id;                  // nullable: output row of cell c (default c)
+    int64_t ncells;                          // cells (upper bound when dev_ncells is set)
+    const unsigned long long *dev_ncells;    // nullable: number of cells, read on the device
+    int log_input;                           // field 0 is ln max(F, 1e-30) instead of F
+    float *feat;                             // [row][fstride]: field 0, (re, im) per slot
+    float *featL;                            // nullable: field 1 = modes of ln max(F, 1e-30)
+    int fstride;
+    double *mom;                             // nullable: [row][kDiag] moments of F (no Q entries)
+    double h;                                // grid spacing 2L/N
+    const int *modes;                        // device [nmodes][3]: (k_axis0, k_axis1, k_axis2); 2D: (0, k0, k1)
+    int nmodes;
 };
 
 // Multiplier table layout for one class: mult[dir][lz][p], p = ly * H + lx (3D) or p = lx (2D),

@@ -29,12 +29,12 @@ EF_DECLARE_VARIANT(f64_3d)
 // ef_plan.cpp (ef_noalloc.cu).  Returns false for a null or batched plan.
 struct PlanView {
     int prec, d, N;
-    int cluster, tpb, planes, paired, nops, max_clusters, sg_global, nfeat;
+    int cluster, tpb, planes, paired, nops, max_clusters, sg_global, nfeat;   // nfeat: band modes
     size_t smem;
     double L;
     const void *mult;
     const Op *ops;
-    const int *fidx;
+    const int *modes;         // device [nfeat][3] band modes (FeatArgs::modes)
     int *status;
     int device;
 };
@@ -43,6 +43,17 @@ size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paire
 cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
                            cudaStream_t s);
 void set_last_error(const char *msg);
+
+// low-mode features (ef_features_f32.cu / ef_features_f64.cu): nf = 1 or 2 fields; the grid is
+// capped at the CTAs that fit on the device at once (persistent over cells)
+bool features_fits(int prec, int d, int N, int nf);
+cudaError_t features_launch(int prec, int d, int N, const FeatArgs &a, cudaStream_t s);
+#define EF_DECLARE_FEAT(SUF)                                                                          \
+    bool features_fits_##SUF(int d, int N, int nf);                                                   \
+    cudaError_t features_launch_##SUF(int d, int N, const FeatArgs &a, cudaStream_t s);
+EF_DECLARE_FEAT(f32)
+EF_DECLARE_FEAT(f64)
+#undef EF_DECLARE_FEAT
 
 // moments / entropy (ef_moments.cu)
 cudaError_t moments_launch(int prec, int d, const void *F, const void *Q, const int64_t *cell_off,

@@ -251,7 +251,7 @@ struct ClassPlan {
     void *d_mult = nullptr;
     ef::Op *d_ops = nullptr;             // active op list (points into one of the two below)
     ef::Op *d_ops_single = nullptr, *d_ops_paired = nullptr;
-    int *d_fidx = nullptr;               // feature slot per spectral element (|k| <= EF_FEATURE_K)
+    int *d_modes = nullptr;              // band modes [nfeat][3] (|k| <= EF_FEATURE_K), feature slot order
     int64_t *d_cell_off = nullptr, *d_cell_id = nullptr;
     void *d_sg = nullptr;
     int64_t sg_slots = 0;
@@ -624,32 +624,31 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
     if (e == cudaSuccess) e = cudaMemcpy(cp.d_ops_paired, ops2.data(), ops2.size() * sizeof(ef::Op), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "op list copy");
     // feature slots: modes with |k| <= EF_FEATURE_K in the canonical half space (k2 > 0, or
-    // k2 = 0 and k1 > 0, or k2 = k1 = 0 and k0 >= 0), in lexicographic order of (k0, k1, k2)
-    {
-        std::vector<int> fidx((size_t)per, -1);
+    // k2 = 0 and k1 > 0, or k2 = k1 = 0 and k0 >= 0), in lexicographic order of (k0, k1, k2);
+    // stored as (k_axis0, k_axis1, k_axis2) for 3D and (0, k0, k1) for 2D (k2 = 0)
+    if (N / 2 > EF_FEATURE_K) {
+        std::vector<int> modes;
         const int K = EF_FEATURE_K;
-        int slot = 0;
         for (int k0 = -K; k0 <= K; ++k0)
             for (int k1 = -K; k1 <= K; ++k1)
                 for (int k2 = 0; k2 <= K; ++k2) {
                     if (k0 * k0 + k1 * k1 + k2 * k2 > K * K) continue;
                     if (!(k2 > 0 || (k2 == 0 && (k1 > 0 || (k1 == 0 && k0 >= 0))))) continue;
                     if (d == 2 && k2 != 0) continue;
-                    if (N / 2 <= K) continue;          // grid too small for the band
-                    const int lz = (k0 + N) % N;
-                    int p;
                     if (d == 3) {
-                        p = ((k1 + N) % N) * H + k2;
-                    } else {                           // 2D: axis 0 = k0, half axis = k1
-                        if (k1 < 0) continue;
-                        p = k1;
+                        modes.push_back(k0);
+                        modes.push_back(k1);
+                        modes.push_back(k2);
+                    } else {
+                        modes.push_back(0);
+                        modes.push_back(k0);
+                        modes.push_back(k1);
                     }
-                    fidx[(size_t)lz * NP + p] = slot++;
                 }
-        e = cudaMalloc((void **)&cp.d_fidx, fidx.size() * sizeof(int));
-        if (e == cudaSuccess) e = cudaMemcpy(cp.d_fidx, fidx.data(), fidx.size() * sizeof(int), cudaMemcpyHostToDevice);
+        e = cudaMalloc((void **)&cp.d_modes, modes.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(cp.d_modes, modes.data(), modes.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "feature table");
-        cp.nfeat = slot;
+        cp.nfeat = (int)modes.size() / 3;
     }
     return choose_shape(ds, cp, cp.ncells > 0 ? std::min<int64_t>(cp.ncells, 512) : 0);
 }
@@ -675,7 +674,7 @@ void destroy_plan(ef_plan_s *p)
     for (ClassPlan &cp : p->classes) {
         cudaFree(cp.d_mult);
         cudaFree(cp.d_ops_single);
-        cudaFree(cp.d_fidx);
+        cudaFree(cp.d_modes);
         cudaFree(cp.d_ops_paired);
         cudaFree(cp.d_cell_off);
         cudaFree(cp.d_cell_id);
@@ -1028,13 +1027,34 @@ bool plan_view(const ef_plan_s *p, PlanView *out)
     out->sg_global = cp.sg_global;
     out->nfeat = cp.nfeat;
     out->smem = cp.smem;
-    out->fidx = cp.d_fidx;
+    out->modes = cp.d_modes;
     out->L = p->desc.L;
     out->mult = cp.d_mult;
     out->ops = cp.d_ops;
     out->status = p->d_status;
     out->device = p->device;
     return true;
+}
+
+bool features_fits(int prec, int d, int N, int nf)
+{
+    return prec == EF_PREC_F32 ? features_fits_f32(d, N, nf) : features_fits_f64(d, N, nf);
+}
+
+cudaError_t features_launch(int prec, int d, int N, const FeatArgs &a, cudaStream_t s)
+{
+    if (a.featL && !features_fits(prec, d, N, 2)) {
+        // both fields do not fit in one CTA's shared memory: one launch per field
+        FeatArgs a0 = a, a1 = a;
+        a0.featL = nullptr;
+        a1.featL = nullptr;
+        a1.feat = a.featL;
+        a1.log_input = 1;
+        a1.mom = nullptr;
+        cudaError_t e = features_launch(prec, d, N, a0, s);
+        return e != cudaSuccess ? e : features_launch(prec, d, N, a1, s);
+    }
+    return prec == EF_PREC_F32 ? features_launch_f32(d, N, a, s) : features_launch_f64(d, N, a, s);
 }
 
 size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired)
@@ -1119,31 +1139,18 @@ ef_status ef_features(ef_plan_t p, const void *F, float *feat, int64_t ncells, i
     for (ClassPlan &cp : p->classes) {
         const int64_t n = p->batched ? cp.ncells : ncells;
         if (n <= 0) continue;
-        const int grid = (int)std::min<int64_t>(n, cp.max_clusters);
-        st = ensure_sg(p, cp, grid);
-        if (st != EF_OK) return st;
-        ef::CollideArgs a{};
+        ef::FeatArgs a{};
         a.F = F;
-        a.Q = nullptr;
         a.cell_off = cp.d_cell_off;
         a.cell_id = cp.d_cell_id;
         a.ncells = n;
-        a.mult = cp.d_mult;
-        a.ops = cp.d_ops;
-        a.nops = cp.nops;
-        a.cluster = cp.cluster;
-        a.planes = cp.planes;
-        a.sg_global = cp.sg_global;
-        a.sg_ws = cp.d_sg;
-        a.out_mode = ef::OUT_FEATURES;
-        a.h = 2.0 * ds.L / cp.N;
-        a.status = p->d_status;
-        a.paired = cp.paired;
-        a.feat = feat;
-        a.fidx = cp.d_fidx;
-        a.fstride = EF_FEATURE_STRIDE;
         a.log_input = log_input ? 1 : 0;
-        cudaError_t e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, s);
+        a.feat = feat;
+        a.fstride = EF_FEATURE_STRIDE;
+        a.h = 2.0 * ds.L / cp.N;
+        a.modes = cp.d_modes;
+        a.nmodes = cp.nfeat;
+        cudaError_t e = ef::features_launch(ds.prec, ds.d, cp.N, a, s);
         if (e != cudaSuccess) return cuda_fail(e, "features launch");
     }
     return EF_OK;

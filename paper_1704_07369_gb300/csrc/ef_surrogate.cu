@@ -432,17 +432,25 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
     if (!ef::plan_view(s->plan, &v)) return sfail(EF_ERR_INVALID_ARG, "bad plan");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t cell = v.d == 3 ? (int64_t)v.N * v.N * v.N : (int64_t)v.N * v.N;
-    ef_status r = ef_features(s->plan, F, s->featF, ncells, 0, stream);
-    if (r != EF_OK) return r;
-    r = ef_features(s->plan, F, s->featL, ncells, 1, stream);
-    if (r != EF_OK) return r;
-    r = ef_moments_entropy(s->plan, F, nullptr, s->mom, ncells, stream);
-    if (r != EF_OK) return r;
-    r = ef_surrogate_normalize(s, s->featF, nullptr, s->mom, s->X, nullptr, ncells, stream);
+    if ((uintptr_t)F % 16) return sfail(EF_ERR_INVALID_ARG, "F must be 16-byte aligned");
+    // one pass over the cells: band modes of F and of ln F, and the moments of F
+    ef::FeatArgs fa{};
+    fa.F = F;
+    fa.ncells = ncells;
+    fa.feat = s->featF;
+    fa.featL = s->featL;
+    fa.fstride = kStride;
+    fa.mom = s->mom;
+    fa.h = 2.0 * v.L / v.N;
+    fa.modes = v.modes;
+    fa.nmodes = v.nfeat;
+    cudaError_t e = ef::features_launch(v.prec, v.d, v.N, fa, st);
+    if (e != cudaSuccess) return scuda(e, "surrogate features");
+    ef_status r = ef_surrogate_normalize(s, s->featF, nullptr, s->mom, s->X, nullptr, ncells, stream);
     if (r != EF_OK) return r;
     r = ef_mlp_forward(s->mlp, s->X, kStride, s->Y, s->noutp, ncells, stream);
     if (r != EF_OK) return r;
-    cudaError_t e = cudaMemsetAsync(s->count, 0, 8, st);
+    e = cudaMemsetAsync(s->count, 0, 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->untrusted, 0, 4, st);
     if (e != cudaSuccess) return scuda(e, "surrogate reset");
     decode_gate_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(
@@ -470,14 +478,18 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
         const int grid = (int)std::min<int64_t>(ncells, v.max_clusters);
         e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, v.smem, st);
         if (e != cudaSuccess) return scuda(e, "fallback collide");
-        ef::CollideArgs f = a;
-        f.F = s->Qs;
-        f.Q = nullptr;
-        f.out_mode = ef::OUT_FEATURES;
-        f.feat = s->qplain;
-        f.fidx = v.fidx;
-        f.fstride = kStride;
-        e = ef::collide_launch(v.prec, v.d, v.N, f, grid, v.tpb, v.smem, st);
+        ef::FeatArgs qa{};
+        qa.F = s->Qs;
+        qa.cell_off = s->list_off;
+        qa.cell_id = s->list_id;
+        qa.ncells = ncells;
+        qa.dev_ncells = s->count;
+        qa.feat = s->qplain;
+        qa.fstride = kStride;
+        qa.h = 2.0 * v.L / v.N;
+        qa.modes = v.modes;
+        qa.nmodes = v.nfeat;
+        e = ef::features_launch(v.prec, v.d, v.N, qa, st);
         if (e != cudaSuccess) return scuda(e, "fallback features");
         merge_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(s->count, s->list_id, s->qplain, qfeat, s->nf,
                                                                             tol, flags, s->untrusted);

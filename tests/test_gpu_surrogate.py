@@ -36,27 +36,35 @@ def _modes(K=6):
     return out
 
 
-@pytest.mark.parametrize("prec", [ef.EF_PREC_F64, ef.EF_PREC_F32])
-def test_features_match_oracle_dft(prec):
-    N, L = 16, 8.0
-    cells = [inputs.mixture_cell(3, N, L, 70 + i) for i in range(3)]
+@pytest.mark.parametrize("d,N,prec", [(3, 16, ef.EF_PREC_F64), (3, 16, ef.EF_PREC_F32), (3, 24, ef.EF_PREC_F32),
+                                       (3, 40, ef.EF_PREC_F64), (3, 48, ef.EF_PREC_F32), (3, 64, ef.EF_PREC_F32),
+                                       (2, 32, ef.EF_PREC_F64), (2, 64, ef.EF_PREC_F32)])
+def test_features_match_oracle_dft(d, N, prec):
+    """Band modes |k| <= 6 of F and of ln F (index-origin convention: the paper's Fh_k times
+    (-1)^{sum k}) against the oracle's DFT: the direct sum for small grids, NumPy's FFT with the
+    paper's phase for the large ones."""
+    L = 8.0
+    ncell = 3
+    cells = [inputs.mixture_cell(d, N, L, 70 + i) for i in range(ncell)]
     dt = torch.float64 if prec == ef.EF_PREC_F64 else torch.float32
-    plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, prec)
+    plan = ef.Plan(d, N, L, ef.EF_KERNEL_HARD_SPHERE if d == 3 else ef.EF_KERNEL_MAXWELL, 32 if d == 3 else 16, prec)
     F = torch.tensor(np.stack(cells), dtype=dt, device="cuda")
-    feat = torch.zeros(3, ef.EF_FEATURE_STRIDE, device="cuda")
+    feat = torch.zeros(ncell, ef.EF_FEATURE_STRIDE, device="cuda")
     featL = torch.zeros_like(feat)
-    ef.ef_features(plan.handle, F, feat, 3)
-    ef.ef_features(plan.handle, F, featL, 3, log_input=1)
+    ef.ef_features(plan.handle, F, feat, ncell)
+    ef.ef_features(plan.handle, F, featL, ncell, log_input=1)
     torch.cuda.synchronize()
-    modes = _modes()
-    assert len(modes) == 463
+    modes = _modes() if d == 3 else [(k0, k1) for k0 in range(-6, 7) for k1 in range(0, 7)
+                                     if k0 * k0 + k1 * k1 <= 36 and (k1 > 0 or k0 >= 0)]
+    assert len(modes) == (463 if d == 3 else 57)
     for i, c in enumerate(cells):
+        c = F[i].double().cpu().numpy()          # the values the kernel read
         for field, got in ((c, feat[i]), (np.log(np.maximum(c, 1e-30)), featL[i])):
-            Fh = oracle.dft(field)
-            ref = np.array([Fh[k0 % N, k1 % N, k2 % N] * (-1) ** (k0 + k1 + k2) for k0, k1, k2 in modes])
-            g = got.cpu().numpy()[:926].reshape(-1, 2)
+            Fh = oracle.dft(field) if N <= 24 or d == 2 else oracle.dft_fft(field)
+            ref = np.array([Fh[tuple(k % N for k in m)] * (-1) ** sum(m) for m in modes])
+            g = got.cpu().numpy()[:2 * len(modes)].reshape(-1, 2)
             g = g[:, 0] + 1j * g[:, 1]
-            assert np.abs(g - ref).max() <= 2e-6 * np.abs(ref).max()
+            assert np.abs(g - ref).max() <= 2e-6 * np.abs(ref).max(), (i, np.abs(g - ref).max() / np.abs(ref).max())
 
 
 def test_mlp_forward_and_gradients_match_oracle():
