@@ -12,6 +12,12 @@ Metric: collision evaluations per second counted as cell grid points, sum_cells 
 Timing: W warm-up steps, then K steps between CUDA events on the launching stream, bracketed by a
 barrier and device synchronisation; max over ranks.  The inputs (about 0.9 GB) exceed the L2.
 
+After the timed steps (N = 1 only) the "surrogate" object compares the learned surrogate with the
+plain operator on 16384-cell batches (N = 32, hard-sphere and Maxwell kernels): throughput of both
+on the same resident batch, and the accuracy of the band the surrogate path delivers, under three
+audit policies (none; any audited miss sends the whole batch to the plain operator; more than 5%
+of audited cells missing does).  --no-surrogate skips it.
+
 --impl reference times the FP64 CPU oracle (direct O(R N^6) sum of the paper's operator) on the
 host cores, on a bounded sample of the same workload.
 """
@@ -338,12 +344,117 @@ def run_ours(args, world, rank, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "cells_per_s": args.cells * world / step_s, "status": int(st), "roofline": roof,
             "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch * args.steps}
+    if not args.no_surrogate and world == 1:
+        line["surrogate"] = surrogate_leg(args, device)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     elif not args.no_cpu_baseline:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------ surrogate leg ----------
+
+SUR_N = 32
+SUR_CELLS = 16384
+SUR_TRAIN = 204800
+SUR_TOL = 1e-3
+SUR_AUDIT = 0.02
+SUR_BATCH = 512
+SUR_LR = 7e-4
+
+
+def _quantiles(e):
+    import torch
+    e = e.double()
+    return {"mean": float(e.mean()), "p50": float(e.median()), "p90": float(torch.quantile(e, 0.9)),
+            "p99": float(torch.quantile(e, 0.99)), "max": float(e.max()),
+            "frac_le_tol": float((e <= SUR_TOL).double().mean())}
+
+
+def surrogate_leg(args, device):
+    """Surrogate vs plain on batches of 16384 BKW-family cells (3D, N = 32, L = 8), for the
+    hard-sphere and Maxwell kernels: the network (926 -> 512 x 3 -> 926, bf16 weights, FP32
+    accumulation) is trained on 204800 cells generated by the library, then plain-operator and
+    surrogate-with-fallback throughput are timed on the same resident batch, and the band of Q
+    the surrogate path delivers is compared cell by cell with the plain FP32 band (all cells) and
+    the FP64 band (first 1024 cells)."""
+    import torch
+
+    import paper_1704_07369_gb300 as ef
+    from paper_1704_07369_gb300 import inputs
+    from paper_1704_07369_gb300 import surrogate as S
+
+    out = {"workload": "3D BKW family (t0~U[0.5,10], rho~U[0.5,2], theta~U[0.5,2], |u|<=1), N=32, L=8, R=32, "
+                       "FP32 plain operator vs bf16 MLP surrogate with gates, audit and fallback",
+           "cells": SUR_CELLS, "train_cells": SUR_TRAIN, "epochs": args.sur_epochs, "batch": SUR_BATCH,
+           "lr": SUR_LR, "tol": SUR_TOL, "inputs": "926 band floats + theta + relative entropy",
+           "audit_fraction": SUR_AUDIT, "metric": "band rel-L2 per cell, modes |k|<=6", "kernels": {}}
+    F = torch.empty(SUR_CELLS, SUR_N, SUR_N, SUR_N, device=device)
+    Q = torch.empty_like(F)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for kern, name in ((ef.EF_KERNEL_HARD_SPHERE, "hard_sphere"), (ef.EF_KERNEL_MAXWELL, "maxwell")):
+        plan = S.make_plan(kern, N=SUR_N, L=L_BOX)
+        t0 = time.perf_counter()
+        fF, fQ, fM = S.features_of_family(plan, SUR_TRAIN, seed=1000)
+        data_s = time.perf_counter() - t0
+        tr = S.Trainer(plan, batch=SUR_BATCH, max_infer_batch=SUR_CELLS, seed=0)
+        t0 = time.perf_counter()
+        hist = tr.fit(fF, fQ, fM, epochs=args.sur_epochs, lr0=SUR_LR, warmup=0.05)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del fF, fQ, fM
+        inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 9_000_000, device=device, out=F)
+        # references: plain FP32 band of every cell, FP64 band of the first 1024
+        plan.collide(F, Q, ncells=SUR_CELLS)
+        ref = torch.zeros(SUR_CELLS, ef.EF_FEATURE_STRIDE, device=device)
+        ef.ef_features(plan.handle, Q, ref, SUR_CELLS)
+        n64 = 1024
+        plan64 = S.make_plan(kern, N=SUR_N, L=L_BOX, prec=ef.EF_PREC_F64)
+        F64 = F[:n64].double()
+        Q64 = torch.empty_like(F64)
+        plan64.collide(F64, Q64, ncells=n64)
+        ref64 = torch.zeros(n64, ef.EF_FEATURE_STRIDE, device=device)
+        ef.ef_features(plan64.handle, Q64, ref64, n64)
+        del F64, Q64
+
+        def timed(fn, reps):
+            for i in range(3):
+                fn(i)
+            torch.cuda.synchronize()
+            ev[0].record()
+            for i in range(reps):
+                fn(100 + i)
+            ev[1].record()
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / reps
+
+        reps = max(3, min(args.steps, 10))
+        plain_ms = timed(lambda i: plan.collide(F, Q, ncells=SUR_CELLS), reps)
+        res = {"plain_ms": plain_ms, "plain_cells_per_s": SUR_CELLS / plain_ms * 1e3,
+               "train": {"data_s": data_s, "train_s": train_s, "final_loss": hist[-1]}, "policies": {}}
+        q = torch.zeros(SUR_CELLS, ef.EF_FEATURE_STRIDE, device=device)
+        flags = torch.zeros(SUR_CELLS, dtype=torch.int32, device=device)
+        for pname, audit, max_miss in (("no_audit", 0.0, 0.0), ("audit_strict", SUR_AUDIT, 0.0),
+                                       ("audit_tolerant", SUR_AUDIT, 0.05)):
+            tr.sur.set_policy(max_miss_fraction=max_miss)
+            ms = timed(lambda i: tr.sur.infer(F, q, flags, SUR_CELLS, audit, i, SUR_TOL), reps)
+            f = flags.cpu().numpy()
+            e = S.band_rel_l2(q, ref)
+            e64 = S.band_rel_l2(q[:n64], ref64)
+            res["policies"][pname] = {
+                "audit_fraction": audit, "max_miss_fraction": max_miss, "ms": ms,
+                "cells_per_s": SUR_CELLS / ms * 1e3, "speedup_vs_plain": plain_ms / ms,
+                "gated": int(((f & 1) != 0).sum()), "audited": int(((f & 2) != 0).sum()),
+                "audit_misses": int(((f & 4) != 0).sum()), "plain_used": int(((f & 8) != 0).sum()),
+                "batch_fallback": bool(((f & 16) != 0).any()),
+                "band_rel_l2_vs_fp32_plain": _quantiles(e), "band_rel_l2_vs_fp64_first1024": _quantiles(e64)}
+        tr.sur.set_policy(0.0)
+        out["kernels"][name] = res
+        del tr, plan, plan64, ref, ref64, q, flags
+        torch.cuda.empty_cache()
+    return out
 
 
 def ef_kernel_hash():
@@ -366,6 +477,8 @@ def main():
     ap.add_argument("--cells", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-epochs", type=int, default=300)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world, rank, local = dist_setup(args)

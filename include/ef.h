@@ -183,8 +183,9 @@ ef_status ef_mlp_grad(ef_mlp_t mlp, const float *X, int ldx, const float *T, int
 ef_status ef_mlp_train_step(ef_mlp_t mlp, const float *X, int ldx, const float *T, int ldt, const float *wmask,
                             const float *rowweight, int64_t batch, float lr, float *loss_dev, ef_stream_t stream);
 
-/* The surrogate path (config: learned map from F's low modes to Q^sigma's low modes).  Built on a
- * uniform plan (whose ef_features define the band) and an MLP with nin = nout = 2 x (feature modes).
+/* The surrogate path (learned map from F's low modes to Q^sigma's low modes; no counterpart in the
+ * paper).  Built on a uniform plan (whose ef_features define the band) and an MLP with
+ * nout = 2 x (feature modes) and nin = nout, or nout + 2 to add the two moment features below.
  * Scratch for max_batch cells (features, activations, the fallback list and a full-size Q buffer
  * for fallback cells) is allocated here, so inference allocates nothing. */
 typedef struct ef_surrogate_s *ef_surrogate_t;
@@ -195,7 +196,11 @@ ef_status ef_surrogate_destroy(ef_surrogate_t sur);
  * EF_FEATURE_STRIDE floats each) and the cells' moments (ef_moments_entropy, EF_DIAG_STRIDE doubles
  * each).  With m = Fh_0 and u = momentum / mass, each mode is de-translated and mass-normalised,
  * x_k = Fh_k e^{i pi k.u/L} / m and y_k = Qh_k e^{i pi k.u/L} / m^2 (the operator is quadratic in F and
- * commutes with velocity shifts up to aliasing); then per-column mean and std of x, per-column mean
+ * commutes with velocity shifts up to aliasing).  If the MLP's input width is 2 x modes + 2, x also
+ * carries the kinetic temperature theta = (2E/rho - |u|^2)/d and the relative entropy to the local
+ * Maxwellian eta/rho - ln rho + (d/2)(ln(2 pi theta) + 1) (from the moments: mass rho, energy E,
+ * eta).  Then per-column mean and std of x (the std floored
+ * at 1e-4, so that columns that vary only at round-off level are not amplified), per-column mean
  * of y and one global scale of y.  Xt, Yt: caller scratch of n x EF_FEATURE_STRIDE floats.  If
  * rowweight (n floats) is not null it receives per-sample loss weights proportional to 1 / |y_b|^2
  * (mean 1), which make the training loss the per-cell relative error. */
@@ -209,14 +214,21 @@ ef_status ef_surrogate_normalize(ef_surrogate_t sur, const float *featF, const f
 /* Copy the statistics (4 x EF_FEATURE_STRIDE floats: mu, s, nu, t) to (set = 0) / from (set = 1) the host. */
 ef_status ef_surrogate_stats(ef_surrogate_t sur, float *host, int set);
 
+/* Audit policy (no counterpart in the paper): the whole batch falls back when more than
+ * max_miss_fraction (in [0, 1]; default 0, i.e. any miss) of the audited cells miss the tolerance;
+ * the input gate rejects cells with any normalised input beyond +-xmax (> 0; default 8).  Applies
+ * to later ef_surrogate_infer calls; not to be changed while one is in flight on a stream. */
+ef_status ef_surrogate_set_policy(ef_surrogate_t sur, float max_miss_fraction, float xmax);
+
 /* Band of Q^sigma for ncells cells (multiple of 64, <= max_batch): qfeat (EF_FEATURE_STRIDE per
  * cell, ef_features layout) receives the prediction, or the plain operator's band where the
  * prediction is not trusted.  flags (int per cell): 1 = a gate failed (non-finite, input outside
- * +-8 training standard deviations, or positive band entropy production sum Q ln F, which the
+ * +-xmax training standard deviations, or positive band entropy production sum Q ln F, which the
  * discrete H-theorem forbids), 2 = audited (a seeded fraction audit_fraction of cells, drawn from
  * seed), 4 = audited and the prediction missed the plain band by more than tol in relative L2,
- * 8 = plain result used, 16 = fell back because an audited cell of the batch missed tol (then the
- * whole batch uses the plain operator).  Everything stays on the device: no host synchronisation. */
+ * 8 = plain result used, 16 = fell back because the audit failed: more than the policy's fraction
+ * of the audited cells (by default none, ef_surrogate_set_policy) missed tol, and then the whole
+ * batch uses the plain operator.  Everything stays on the device: no host synchronisation. */
 ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat, int *flags, int64_t ncells,
                              float audit_fraction, uint64_t seed, float tol, ef_stream_t stream);
 

@@ -39,7 +39,7 @@ SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_
            "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_params",
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
-           "ef_surrogate_stats", "ef_surrogate_infer",
+           "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer",
            "ef_status_string", "ef_last_error")
 EF_FEATURE_K = 6
 EF_FEATURE_STRIDE = 928
@@ -94,6 +94,7 @@ def lib():
         L.ef_surrogate_fit_stats.argtypes = [vp, vp, vp, vp, vp, vp, vp, i64, vp]
         L.ef_surrogate_normalize.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         L.ef_surrogate_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+        L.ef_surrogate_set_policy.argtypes = [vp, ctypes.c_float, ctypes.c_float]
         L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
         L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
         L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
@@ -254,6 +255,9 @@ class Surrogate:
         import numpy as np
         host = np.ascontiguousarray(host, dtype=np.float32)
         _check(lib().ef_surrogate_stats(self.handle, host.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1))
+
+    def set_policy(self, max_miss_fraction=0.0, xmax=8.0):
+        _check(lib().ef_surrogate_set_policy(self.handle, float(max_miss_fraction), float(xmax)))
 
     def infer(self, F, qfeat, flags, ncells, audit_fraction=0.05, seed=0, tol=1e-3, stream=None):
         _check(lib().ef_surrogate_infer(self.handle, _ptr(F), _ptr(qfeat), _ptr(flags), int(ncells),

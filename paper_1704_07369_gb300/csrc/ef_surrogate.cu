@@ -10,8 +10,8 @@
 // training envelope); band entropy production P = 2 N^3 sum_{k != 0} Re(Qh_k conj(Lh_k)) <= 0 with
 // Lh the low modes of ln F (the discrete H-theorem, Theorem 1, restricted to the band).  A
 // seeded fraction of cells is also audited against the plain operator.  Gate failures and audited
-// cells get the plain operator's band; if any audited cell misses the tolerance, every remaining
-// cell falls back too.  No host synchronisation: counts and lists stay on the device.
+// cells get the plain operator's band; if more than a set fraction of the audited cells (by default
+// none) miss the tolerance, every remaining cell falls back too.  No host synchronisation: counts and lists stay on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,13 +46,23 @@ int sgrid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
 // (a velocity shift by u multiplies mode k by exp(-i pi k.u / L); the operator commutes with it up
 // to aliasing, so the network sees the family without its bulk velocity).  One thread per mode.
 __global__ void prep_kernel(const float *featF, const float *featQ, const double *mom, const int *kvec, int64_t n,
-                            int nmodes, int idx0, float pi_over_L, float *Xt, float *Yt)
+                            int nmodes, int idx0, float pi_over_L, int extra, int d, float *Xt, float *Yt)
 {
     const int64_t total = n * nmodes;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = q / nmodes;
         const int j = (int)(q % nmodes);
         const double *mi = mom + i * EF_DIAG_STRIDE;
+        if (extra && j == 0) {
+            // kinetic temperature and relative entropy to the local Maxwellian (zero at equilibrium):
+            // theta = (2E / rho - |u|^2) / d,  KL = eta / rho - ln rho + (d / 2)(ln(2 pi theta) + 1)
+            const double rho = mi[0];
+            const double u2 = (mi[1] * mi[1] + mi[2] * mi[2] + mi[3] * mi[3]) / (rho * rho);
+            const double theta = (2.0 * mi[4] / rho - u2) / d;
+            const double kl = mi[5] / rho - log(rho) + 0.5 * d * (log(2.0 * 3.14159265358979323846 * theta) + 1.0);
+            Xt[i * kStride + 2 * nmodes] = (float)theta;
+            Xt[i * kStride + 2 * nmodes + 1] = (float)kl;
+        }
         const float ux = (float)(mi[1] / mi[0]), uy = (float)(mi[2] / mi[0]), uz = (float)(mi[3] / mi[0]);
         const float ph = pi_over_L * (kvec[3 * j] * ux + kvec[3 * j + 1] * uy + kvec[3 * j + 2] * uz);
         float sn, cs;
@@ -69,15 +79,21 @@ __global__ void prep_kernel(const float *featF, const float *featQ, const double
     }
 }
 
+// Floor of an input column's standard deviation.  Inputs are relative to the mass mode (|x~_0| = 1);
+// after de-translation an isotropic cell has real band modes, so imaginary parts (and modes a family
+// never excites) vary only at round-off level, and standardising them by their own spread would feed
+// the network amplified rounding noise.
+constexpr double kSdFloor = 1e-4;
+
 // column mean / std of the prepared inputs and outputs; the output scale is one global RMS
-__global__ void stats_kernel(const float *Xt, const float *Yt, int64_t n, int nf, float *mu, float *sd, float *nu,
+__global__ void stats_kernel(const float *Xt, const float *Yt, int64_t n, int nin, int nf, float *mu, float *sd, float *nu,
                              float *colvar)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nf) return;
+    if (j >= nin) return;
     double sx = 0, sxx = 0, sy = 0, syy = 0;
     for (int64_t i = 0; i < n; ++i) {
-        const double x = Xt[i * kStride + j], y = Yt[i * kStride + j];
+        const double x = Xt[i * kStride + j], y = j < nf ? Yt[i * kStride + j] : 0.0;
         sx += x;
         sxx += x * x;
         sy += y;
@@ -87,7 +103,7 @@ __global__ void stats_kernel(const float *Xt, const float *Yt, int64_t n, int nf
     const double vx = fmax(sxx / n - mx * mx, 0.0), vy = fmax(syy / n - my * my, 0.0);
     mu[j] = (float)mx;
     nu[j] = (float)my;
-    sd[j] = (float)(vx > 1e-24 ? sqrt(vx) : 1.0);
+    sd[j] = (float)fmax(sqrt(vx), kSdFloor);
     colvar[j] = (float)vy;
 }
 
@@ -124,15 +140,15 @@ __global__ void rowweight_norm_kernel(int64_t n, float *rw)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) rw[i] *= scale;
 }
 
-__global__ void standardize_kernel(float *X, float *Y, int64_t n, int nf, const float *mu, const float *sd, const float *nu,
-                                   const float *td)
+__global__ void standardize_kernel(float *X, float *Y, int64_t n, int nin, int nf, const float *mu, const float *sd,
+                                   const float *nu, const float *td)
 {
-    const int64_t total = n * nf;
+    const int64_t total = n * nin;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / nf;
-        const int j = (int)(q % nf);
+        const int64_t i = q / nin;
+        const int j = (int)(q % nin);
         X[i * kStride + j] = (X[i * kStride + j] - mu[j]) / sd[j];
-        if (Y) Y[i * kStride + j] = (Y[i * kStride + j] - nu[j]) / td[j];
+        if (Y && j < nf) Y[i * kStride + j] = (Y[i * kStride + j] - nu[j]) / td[j];
     }
 }
 
@@ -147,10 +163,10 @@ __device__ __forceinline__ float hash_unit(uint64_t seed, int64_t i)
 
 // one warp per cell: decode, gates, audit draw, compaction of the cells that need the plain path
 __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *featF, const float *featL, const double *mom,
-                                   const int *kvec, float pi_over_L, int64_t n, int nf, int idx0, const float *nu,
+                                   const int *kvec, float pi_over_L, int64_t n, int nf, int nin, int idx0, const float *nu,
                                    const float *td, const float *Xn, float xmax, float N3, float audit_frac, uint64_t seed,
                                    float *qfeat, int *flags, unsigned long long *count, int64_t *list_off,
-                                   int64_t *list_id, int64_t cell)
+                                   int64_t *list_id, int64_t cell, unsigned *audit)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -174,6 +190,9 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
         qfeat[i * kStride + 2 * jm + 1] = qi;
         prod += qr * featL[i * kStride + 2 * jm] + qi * featL[i * kStride + 2 * jm + 1];   // Re(q conj(l))
     }
+    if (lane == 0)
+        for (int j = nf; j < nin; ++j)
+            if (fabsf(Xn[i * kStride + j]) > xmax) bad = true;
     for (int o = 16; o > 0; o >>= 1) {
         prod += __shfl_xor_sync(0xffffffffu, prod, o);
         bad |= __shfl_xor_sync(0xffffffffu, (int)bad, o) != 0;
@@ -182,7 +201,10 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
         prod *= 2.f * N3;
         int f = 0;
         if (bad || !(prod <= 0.f)) f |= 1;
-        if (hash_unit(seed, i) < audit_frac) f |= 2;
+        if (hash_unit(seed, i) < audit_frac) {
+            f |= 2;
+            atomicAdd(&audit[0], 1u);
+        }
         flags[i] = f;
         if (f) {
             const unsigned long long k = atomicAdd(count, 1ULL);
@@ -194,7 +216,7 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
 
 // merge the plain band of the listed cells into the output; audited cells compare first
 __global__ void merge_kernel(const unsigned long long *count, const int64_t *list_id, const float *qplain, float *qfeat, int nf,
-                             float tol, int *flags, int *untrusted)
+                             float tol, int *flags, unsigned *audit)
 {
     const int lane = threadIdx.x & 31;
     const long long k = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -217,18 +239,21 @@ __global__ void merge_kernel(const unsigned long long *count, const int64_t *lis
         int nf2 = f | 8;                                  // plain result used
         if ((f & 2) && num > tol * tol * den) {
             nf2 |= 4;
-            atomicOr(untrusted, 1);
+            atomicAdd(&audit[1], 1u);
         }
         flags[i] = nf2;
     }
 }
 
-// second round: when the audit failed, list every cell that still carries a prediction
-__global__ void relist_kernel(const int *untrusted, int64_t n, int *flags, unsigned long long *count, int64_t *list_off,
-                              int64_t *list_id, int64_t cell)
+// second round: when more than max_miss of the audited cells missed the tolerance (any miss when
+// max_miss = 0), list every cell that still carries a prediction
+__global__ void relist_kernel(const unsigned *audit, float max_miss, int64_t n, int *flags, unsigned long long *count,
+                              int64_t *list_off, int64_t *list_id, int64_t cell)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n || !*untrusted) return;
+    if (i >= n) return;
+    const unsigned audited = audit[0], missed = audit[1];
+    if (!(missed > 0 && (float)missed > max_miss * (float)audited)) return;
     if (flags[i] & 8) return;
     flags[i] |= 16;                                       // fell back because the batch was untrusted
     const unsigned long long k = atomicAdd(count, 1ULL);
@@ -242,17 +267,18 @@ struct ef_surrogate_s {
     ef_plan_t plan;
     ef_mlp_t mlp;
     int64_t max_batch;
-    int nf, idx0, noutp;
+    int nf, nin, idx0, noutp, d;        // nin = nf, or nf + 2 with the two moment features
     float *mu = nullptr, *sd = nullptr, *nu = nullptr, *td = nullptr, *colvar = nullptr;
     int *kvec = nullptr;
     double *mom = nullptr;
     float pi_over_L = 0.f;
     float *featF = nullptr, *featL = nullptr, *X = nullptr, *Y = nullptr, *qplain = nullptr;
     void *Qs = nullptr;
-    int *untrusted = nullptr;
+    unsigned *audit = nullptr;            // [0] audited cells, [1] audited misses (this call)
     unsigned long long *count = nullptr;
     int64_t *list_off = nullptr, *list_id = nullptr;
     float xmax = 8.f;
+    float max_miss = 0.f;
 };
 
 namespace {
@@ -273,7 +299,7 @@ void sur_free(ef_surrogate_s *s)
     cudaFree(s->Y);
     cudaFree(s->qplain);
     cudaFree(s->Qs);
-    cudaFree(s->untrusted);
+    cudaFree(s->audit);
     cudaFree(s->count);
     cudaFree(s->list_off);
     cudaFree(s->list_id);
@@ -317,7 +343,8 @@ ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, e
     ef_status st = ef_mlp_info(mlp, info);
     if (st != EF_OK) return st;
     const int nf = 2 * v.nfeat;
-    if (info[0] != nf || info[3] != nf) return sfail(EF_ERR_INVALID_ARG, "mlp widths must equal 2 x feature modes");
+    if ((info[0] != nf && info[0] != nf + 2) || info[3] != nf)
+        return sfail(EF_ERR_INVALID_ARG, "mlp widths: input 2 x feature modes (+ 2 moment features), output 2 x feature modes");
     if (max_batch < 64 || max_batch % 64 || max_batch > info[7])
         return sfail(EF_ERR_INVALID_ARG, "max_batch: multiple of 64, at most the mlp's max batch");
     ef_surrogate_s *s = new ef_surrogate_s();
@@ -325,6 +352,8 @@ ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, e
     s->mlp = mlp;
     s->max_batch = max_batch;
     s->nf = nf;
+    s->nin = (int)info[0];
+    s->d = v.d;
     s->noutp = (int)info[6];
     std::vector<int> kv;
     s->idx0 = mode_list(v.d, kv);
@@ -349,7 +378,7 @@ ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, e
     alloc((void **)&s->Y, (size_t)max_batch * s->noutp * 4);
     alloc((void **)&s->qplain, (size_t)max_batch * kStride * 4);
     alloc((void **)&s->Qs, (size_t)max_batch * cell * el);
-    alloc((void **)&s->untrusted, 4);
+    alloc((void **)&s->audit, 8);
     alloc((void **)&s->count, 8);
     alloc((void **)&s->list_off, (size_t)max_batch * 8);
     alloc((void **)&s->list_id, (size_t)max_batch * 8);
@@ -383,8 +412,9 @@ ef_status ef_surrogate_fit_stats(ef_surrogate_t s, const float *featF, const flo
     if (!s || !featF || !featQ || !mom || !Xt || !Yt || n <= 0) return sfail(EF_ERR_INVALID_ARG, "bad surrogate statistics arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const int nm = s->nf / 2;
-    prep_kernel<<<sgrid(n * nm), 256, 0, st>>>(featF, featQ, mom, s->kvec, n, nm, s->idx0, s->pi_over_L, Xt, Yt);
-    stats_kernel<<<(s->nf + 127) / 128, 128, 0, st>>>(Xt, Yt, n, s->nf, s->mu, s->sd, s->nu, s->colvar);
+    prep_kernel<<<sgrid(n * nm), 256, 0, st>>>(featF, featQ, mom, s->kvec, n, nm, s->idx0, s->pi_over_L, s->nin > s->nf,
+                                               s->d, Xt, Yt);
+    stats_kernel<<<(s->nin + 127) / 128, 128, 0, st>>>(Xt, Yt, n, s->nin, s->nf, s->mu, s->sd, s->nu, s->colvar);
     scale_kernel<<<1, 1, 0, st>>>(s->colvar, s->nf, s->td);
     if (rowweight) {
         rowweight_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(Yt, n, s->nf, rowweight);
@@ -403,8 +433,9 @@ ef_status ef_surrogate_normalize(ef_surrogate_t s, const float *featF, const flo
     const int nm = s->nf / 2;
     const bool withY = featQ && Y;
     prep_kernel<<<sgrid(n * nm), 256, 0, st>>>(featF, withY ? featQ : nullptr, mom, s->kvec, n, nm, s->idx0, s->pi_over_L,
-                                               X, withY ? Y : nullptr);
-    standardize_kernel<<<sgrid(n * s->nf), 256, 0, st>>>(X, withY ? Y : nullptr, n, s->nf, s->mu, s->sd, s->nu, s->td);
+                                               s->nin > s->nf, s->d, X, withY ? Y : nullptr);
+    standardize_kernel<<<sgrid(n * s->nin), 256, 0, st>>>(X, withY ? Y : nullptr, n, s->nin, s->nf, s->mu, s->sd, s->nu,
+                                                          s->td);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EF_OK : scuda(e, "normalise");
 }
@@ -418,6 +449,16 @@ ef_status ef_surrogate_stats(ef_surrogate_t s, float *host4, int set)
                             : cudaMemcpy(host4 + k * kStride, d[k], kStride * 4, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return scuda(e, "surrogate stats copy");
     }
+    return EF_OK;
+}
+
+ef_status ef_surrogate_set_policy(ef_surrogate_t s, float max_miss_fraction, float xmax)
+{
+    if (!s) return sfail(EF_ERR_INVALID_ARG, "null surrogate");
+    if (!(max_miss_fraction >= 0.f && max_miss_fraction <= 1.f)) return sfail(EF_ERR_INVALID_ARG, "max_miss_fraction in [0, 1]");
+    if (!(xmax > 0.f)) return sfail(EF_ERR_INVALID_ARG, "xmax > 0");
+    s->max_miss = max_miss_fraction;
+    s->xmax = xmax;
     return EF_OK;
 }
 
@@ -451,12 +492,12 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
     r = ef_mlp_forward(s->mlp, s->X, kStride, s->Y, s->noutp, ncells, stream);
     if (r != EF_OK) return r;
     e = cudaMemsetAsync(s->count, 0, 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->untrusted, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->audit, 0, 8, st);
     if (e != cudaSuccess) return scuda(e, "surrogate reset");
     decode_gate_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(
-        s->Y, s->noutp, s->featF, s->featL, s->mom, s->kvec, s->pi_over_L, ncells, s->nf, s->idx0, s->nu, s->td, s->X,
+        s->Y, s->noutp, s->featF, s->featL, s->mom, s->kvec, s->pi_over_L, ncells, s->nf, s->nin, s->idx0, s->nu, s->td, s->X,
         s->xmax, (float)cell,
-        audit_fraction, seed, qfeat, flags, s->count, s->list_off, s->list_id, cell);
+        audit_fraction, seed, qfeat, flags, s->count, s->list_off, s->list_id, cell, s->audit);
     for (int round = 0; round < 2; ++round) {
         // plain operator on the listed cells (count read on the device), then their band
         ef::CollideArgs a{};
@@ -492,12 +533,12 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
         e = ef::features_launch(v.prec, v.d, v.N, qa, st);
         if (e != cudaSuccess) return scuda(e, "fallback features");
         merge_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(s->count, s->list_id, s->qplain, qfeat, s->nf,
-                                                                            tol, flags, s->untrusted);
+                                                                            tol, flags, s->audit);
         if (round == 0) {
             e = cudaMemsetAsync(s->count, 0, 8, st);
             if (e != cudaSuccess) return scuda(e, "surrogate reset");
-            relist_kernel<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(s->untrusted, ncells, flags, s->count,
-                                                                            s->list_off, s->list_id, cell);
+            relist_kernel<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(s->audit, s->max_miss, ncells, flags,
+                                                                            s->count, s->list_off, s->list_id, cell);
         }
     }
     e = cudaGetLastError();

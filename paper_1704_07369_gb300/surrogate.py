@@ -65,17 +65,21 @@ def zero_slot(K=6):
 
 
 class Trainer:
-    """Fits the normalisation, then trains the MLP with Adam and a cosine learning-rate decay."""
+    """Fits the normalisation, then trains the MLP with Adam: a short linear warm-up, then a cosine
+    learning-rate decay from lr0 to lr1."""
 
-    def __init__(self, plan, nhidden=512, nlayers=4, batch=1024, max_infer_batch=16384, seed=0):
+    def __init__(self, plan, nhidden=512, nlayers=4, batch=1024, max_infer_batch=16384, seed=0, moment_features=True):
         self.plan = plan
         self.nf = 2 * 463
         self.batch = batch
-        self.mlp = MLP(self.nf, nhidden, nlayers, self.nf, max(batch, max_infer_batch), seed=seed)
+        # with moment_features the input also carries the cell's kinetic temperature and its
+        # relative entropy to the local Maxwellian (two scalars from the moments)
+        nin = self.nf + 2 if moment_features else self.nf
+        self.mlp = MLP(nin, nhidden, nlayers, self.nf, max(batch, max_infer_batch), seed=seed)
         self.sur = Surrogate(plan, self.mlp, max_infer_batch)
         self.wmask = loss_mask(self.nf, zero_slot())
 
-    def fit(self, featF, featQ, mom, epochs=20, lr0=1e-3, lr1=1e-5, seed=0, log=None):
+    def fit(self, featF, featQ, mom, epochs=20, lr0=1e-3, lr1=1e-5, seed=0, log=None, warmup=0.02):
         n = featF.shape[0] // self.batch * self.batch
         X = torch.zeros(featF.shape[0], EF_FEATURE_STRIDE, device=featF.device)
         Y = torch.zeros_like(X)
@@ -94,6 +98,7 @@ class Trainer:
             tot = torch.zeros(1, device=featF.device)
             for b0 in range(0, n, self.batch):
                 lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * step / max(1, steps)))
+                lr *= min(1.0, (step + 1) / max(1.0, warmup * steps))
                 self.mlp.train_step(Xs[b0:b0 + self.batch], Ys[b0:b0 + self.batch], self.batch, lr, loss,
                                     wmask=self.wmask, rowweight=Rs[b0:b0 + self.batch])
                 tot += loss

@@ -115,6 +115,44 @@ def test_mlp_training_reduces_loss():
     assert losses[-1] < 0.05 * losses[0]
 
 
+def test_surrogate_gain_over_plain():
+    """What the trained network buys over the method without it: on a batch of BKW-family cells
+    (3D, N = 32, L = 8, hard spheres) the surrogate path, gates included, is several times faster
+    than the plain operator, and after a short training its band of Q is already within a percent
+    of the plain band for the typical cell (a no-op prediction Qh = 0 is off by 100%)."""
+    plan = S.make_plan(ef.EF_KERNEL_HARD_SPHERE)
+    fF, fQ, fM = S.features_of_family(plan, 30720, seed=1000)
+    tr = S.Trainer(plan, batch=512, max_infer_batch=4096)
+    hist = tr.fit(fF, fQ, fM, epochs=40, lr0=1e-3, warmup=0.05)
+    assert hist[-1] < 0.01 * hist[0]
+    n = 4096
+    F = inputs.bkw_family_torch(32, 8.0, n, seed=9_000_000)
+    Q = torch.empty_like(F)
+    ref = torch.zeros(n, ef.EF_FEATURE_STRIDE, device="cuda")
+    plan.collide(F, Q, ncells=n)
+    ef.ef_features(plan.handle, Q, ref, n)
+    q = torch.zeros_like(ref)
+    flags = torch.zeros(n, dtype=torch.int32, device="cuda")
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_plain = timed(lambda: plan.collide(F, Q, ncells=n))
+    t_sur = timed(lambda: tr.sur.infer(F, q, flags, n, 0.0, 0, 1e-3))
+    e = S.band_rel_l2(q, ref)
+    assert t_plain / t_sur >= 3.0, (t_plain, t_sur)
+    assert float(e.median()) <= 1e-2, float(e.median())
+    assert int(((flags & 1) != 0).sum()) <= n // 20
+
+
 def test_surrogate_audit_and_fallback_paths():
     """audit 1.0: every cell gets the plain band bit for bit; a tolerance no prediction can meet
     makes the audited cells fail and the whole batch fall back."""
@@ -145,3 +183,23 @@ def test_surrogate_audit_and_fallback_paths():
     assert ((f & 2) != 0).sum() > 0 and ((f & 4) != 0).sum() > 0
     assert ((f & 8) != 0).all()
     assert torch.equal(q[:, :926], ref[:, :926])
+    # policy: tolerate every audited miss -> only the audited cells take the plain band
+    sur.set_policy(max_miss_fraction=1.0)
+    sur.infer(F, q, flags, n, audit_fraction=0.25, seed=9, tol=1e-12)
+    torch.cuda.synchronize()
+    f = flags.cpu().numpy()
+    audited = (f & 2) != 0
+    assert audited.sum() > 0 and ((f[audited] & 12) == 12).all()
+    assert ((f & 16) == 0).all()
+    keep = (f & 9) == 0                       # neither gated nor audited: the prediction stays
+    assert keep.sum() > 0
+    assert not torch.equal(q[torch.tensor(keep, device="cuda")][:, :926], ref[torch.tensor(keep, device="cuda")][:, :926])
+    # an input envelope no cell meets gates every cell onto the plain operator
+    sur.set_policy(max_miss_fraction=0.0, xmax=1e-6)
+    sur.infer(F, q, flags, n, audit_fraction=0.0, seed=1, tol=1e-3)
+    torch.cuda.synchronize()
+    f = flags.cpu().numpy()
+    assert ((f & 9) == 9).all()
+    assert torch.equal(q[:, :926], ref[:, :926])
+    with pytest.raises(ef.EfError):
+        sur.set_policy(max_miss_fraction=1.5)
