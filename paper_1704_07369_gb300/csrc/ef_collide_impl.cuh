@@ -3,12 +3,14 @@
 // Per cell (Sec. 4.1, eq. fastAlg; the DVM form eq. Qsr evaluated by collocation, Sec. 3.1):
 //   F1  each CTA of the cluster owns N/C planes of axis 0; it transforms its planes along the
 //       last axis (real -> half complex) and, in 3D, along axis 1, into its shared-memory slab.
-//   F2  every thread gathers one axis-0 pencil (a fixed spectral column p) from the slabs of all
-//       CTAs through distributed shared memory, finishes the forward transform along axis 0 and
-//       keeps the pencil Fhat[:, p] in registers for the rest of the cell.
-//   for each op (one spectral direction u, or the loss):
-//     A  Fhat[:, p] * M_u[:, p] (filter and radial kernel factor, L2-resident table), inverse
-//        transform along axis 0, scatter the result to the owning CTAs' slabs (DSMEM stores).
+//   F2  CTA r owns the axis-0 pencils (spectral columns p) [r npc, (r + 1) npc); a thread per
+//       pencil gathers it from the slabs of all CTAs through distributed shared memory, finishes
+//       the forward transform along axis 0 and stores Fhat[:, p] to the cluster's L2-resident
+//       workspace (registers stay free for the transforms).
+//   for each op (one spectral direction u, or the loss; paired ops two directions):
+//     A  a thread per (direction, pencil): Fhat[:, p] * M_u[:, p] (filter and radial kernel
+//        factor, L2-resident table), inverse transform along axis 0, scatter the result to the
+//        owning CTAs' slabs (DSMEM stores).
 //     B  each CTA finishes the inverse transform of its planes (axis 1, then half complex ->
 //        real along the last axis, two rows per thread) and folds the real-space values into the
 //        S / G accumulators, or, for the loss op, forms Q = G - F nu and writes the output
@@ -26,9 +28,10 @@ namespace ef {
 
 namespace cg = cooperative_groups;
 
-// Threads per CTA the kernel is compiled for.  A CTA with more than 8 warps puts 3 warps on some
-// SM sub-partition, which caps registers at 168 per thread; the large pencils (FP32 N >= 40, all
-// FP64) need more, so those instantiations are limited to 256 threads (255 registers).
+// Threads per CTA the kernel is compiled for.  Registers are shared per SM sub-partition: 8 warps
+// allow 255 per thread, 10 warps (3 on some sub-partition) 168.  The output pass (Q or F + dt Q
+// with the FP64 diagnostics) holds three rows of N values; FP32 N >= 40 and FP64 keep 8 warps so
+// that it does not spill (the plan-time autotuner picks smaller CTAs in any case).
 template <typename T, int N>
 __host__ __device__ constexpr int max_threads() { return (sizeof(T) == 8 || N >= 40) ? 256 : 320; }
 
@@ -71,6 +74,23 @@ struct Sync {
 __device__ __forceinline__ void record_status(int *status, int code)
 {
     if (status) atomicCAS(status, 0, code);
+}
+
+// Two Hermitian half rows R0, R1 (k = 0 .. N/2, in shared memory) -> the complex row
+// z = IFFT(R0) + i IFFT(R1) (unscaled, inverse sign): the two-for-one inverse of c2r_pair, built
+// straight from shared memory so that no half-spectrum copy lives in registers.
+template <int N, typename T>
+__device__ __forceinline__ void c2r_rows_from(const C2<T> *R0, const C2<T> *R1, C2<T> (&z)[N], const C2<T> *tw)
+{
+    z[0] = C2<T>{R0[0].x, R1[0].x};
+#pragma unroll
+    for (int k = 1; k < N / 2; ++k) {
+        const C2<T> x0 = R0[k], x1 = R1[k];
+        z[k] = C2<T>{x0.x - x1.y, x0.y + x1.x};
+        z[N - k] = C2<T>{x0.x + x1.y, x1.x - x0.y};
+    }
+    z[N / 2] = C2<T>{R0[N / 2].x, R1[N / 2].x};
+    fft<N, 1, N>(z, tw);
 }
 
 // shared-memory bytes of one CTA (must match the carve-up in the kernel).  Paired mode holds two
@@ -331,9 +351,9 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 
     const int64_t nclusters = gridDim.x / C;
     const int64_t cid = blockIdx.x / C;
-    const int pencil = rank * nt + tid;            // this thread's spectral column (stage A)
-    const bool has_pencil = pencil < NP;
-    const unsigned pmask = __ballot_sync(0xffffffffu, has_pencil);   // pencil pairs are complete: NP, nt even
+    const int lane = tid & 31;
+    const int NPC = a.npc;                          // pencils per CTA (even, so pairs never split)
+    C2<T> *Fh = reinterpret_cast<C2<T> *>(a.fh_ws) + cid * (int64_t)N * NP;   // this cluster's spectrum
     const T scale = T(1) / T(CELL);
     const T *Mbase = reinterpret_cast<const T *>(a.mult);
 
@@ -387,15 +407,23 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
         }
         bar.full();
 
-        // ---------------- F2: gather the axis-0 pencil and finish the forward transform
-        C2<T> fh[N];
-        if (has_pencil) {
-            gather_pencil<T, N, WIDE>(fh, Is0, P, NP, pencil, cl, pmask);
-            fft<N, -1, N>(fh, tw);
+        // ---------------- F2: gather the axis-0 pencils and finish the forward transform
+        // (warp-uniform trip count: lane pairs shuffle inside gather_pencil)
+        for (int q0 = tid - lane; q0 < NPC; q0 += nt) {
+            const int pencil = rank * NPC + q0 + lane;
+            const bool has = q0 + lane < NPC && pencil < NP;
+            const unsigned mask = __ballot_sync(0xffffffffu, has);
+            if (has) {
+                C2<T> v[N];
+                gather_pencil<T, N, WIDE>(v, Is0, P, NP, pencil, cl, mask);
+                fft<N, -1, N>(v, tw);
 #pragma unroll
-            for (int z = 0; z < N; ++z) fh[z] = cscale(fh[z], scale);
+                for (int z = 0; z < N; ++z) Fh[(size_t)z * NP + pencil] = cscale(v[z], scale);
+            }
         }
-        bar.war();
+        // publishes Fh to the CTA (stage A reads pencils other threads stored) and keeps every
+        // CTA's slab intact until all gathers are done
+        bar.full();
 
         Diag dg;
         dg.reset();
@@ -403,22 +431,29 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
         for (int o = 0; o < a.nops; ++o) {
             const Op op = a.ops[o];
             const bool pair = op.kind >= OP_PAIR;
-            // ---------------- A: multiply, inverse along axis 0, scatter to the owners' slabs
-            if (has_pencil) {
-#pragma unroll 1
-                for (int b = 0; b < (pair ? 2 : 1); ++b) {
-                    const T *M = Mbase + (size_t)(b ? op.dir2 : op.dir) * N * NP + pencil;
-                    C2<T> *slab = b ? Is1 : Is0;
+            // ---------------- A: multiply, inverse along axis 0, scatter to the owners' slabs;
+            // one (direction, pencil) item per thread, warp-uniform trip count
+            const int nitems = (pair ? 2 : 1) * NPC;
+            for (int q0 = tid - lane; q0 < nitems; q0 += nt) {
+                const int q = q0 + lane;
+                const int b = q >= NPC;
+                const int pencil = rank * NPC + (q - b * NPC);
+                const bool has = q < nitems && pencil < NP;
+                const unsigned mask = __ballot_sync(0xffffffffu, has);
+                if (has) {
+                    const int dir = b ? op.dir2 : op.dir;
+                    const T *M = Mbase + (size_t)dir * N * NP + pencil;
                     C2<T> v[N];
 #pragma unroll
-                    for (int z = 0; z < N; ++z) v[z] = cscale(fh[z], __ldg(M + (size_t)z * NP));
+                    for (int z = 0; z < N; ++z) v[z] = cscale(Fh[(size_t)z * NP + pencil], __ldg(M + (size_t)z * NP));
                     fft<N, 1, N>(v, tw);
-                    scatter_pencil<T, N, WIDE>(v, slab, P, NP, pencil, cl, pmask);
-                }
-                if (a.prefetch && o + 1 < a.nops) {   // pull the next direction's multipliers towards L1
-                    const T *Mn = Mbase + (size_t)a.ops[o + 1].dir * N * NP + pencil;
+                    scatter_pencil<T, N, WIDE>(v, b ? Is1 : Is0, P, NP, pencil, cl, mask);
+                    if (a.prefetch && o + 1 < a.nops) {   // pull the next op's multipliers towards L1
+                        const Op nx = a.ops[o + 1];
+                        const T *Mn = Mbase + (size_t)(b ? nx.dir2 : nx.dir) * N * NP + pencil;
 #pragma unroll
-                    for (int z = 0; z < N; ++z) asm volatile("prefetch.global.L1 [%0];" ::"l"(Mn + (size_t)z * NP));
+                        for (int z = 0; z < N; ++z) asm volatile("prefetch.global.L1 [%0];" ::"l"(Mn + (size_t)z * NP));
+                    }
                 }
             }
             bar.full();
@@ -446,22 +481,18 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                 const bool last = op.kind == OP_PAIR_LAST;
                 const bool big = *s_nubig != 0;
                 for (int r = tid; r < rows; r += nt) {
-                    C2<T> X0[H], X1[H];
-#pragma unroll
-                    for (int k = 0; k < H; ++k) {
-                        X0[k] = Is0[r * H + k];
-                        X1[k] = Is1[r * H + k];
-                    }
-                    T ya[N], yb[N];
-                    c2r_pair<N, T>(X0, X1, ya, yb, tw);
+                    // two Hermitian half rows -> one complex row z (a_e + i S_e), built straight
+                    // from shared memory (the two-for-one inverse of c2r_pair)
+                    C2<T> z[N];
+                    c2r_rows_from<N, T>(Is0 + r * H, Is1 + r * H, z, tw);
                     T *Gr = Gb + r;
                     if (!last) {
 #pragma unroll
-                        for (int n = 0; n < N; ++n) Gr[n * rows] += ya[n] * yb[n];
+                        for (int n = 0; n < N; ++n) Gr[n * rows] += z[n].x * z[n].y;
                     } else {
                         T qv[N];
 #pragma unroll
-                        for (int n = 0; n < N; ++n) qv[n] = Gr[n * rows] + ya[n] * yb[n];
+                        for (int n = 0; n < N; ++n) qv[n] = Gr[n * rows] + z[n].x * z[n].y;
                         const int64_t grow = (int64_t)rank * rows + r;
                         T fr[N];
                         load_row<T, N>(F + grow * N, fr);
@@ -471,14 +502,8 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             } else {
                 for (int q = tid; q < npairs; q += nt) {
                     const int r0 = q, r1 = q + npairs;
-                    C2<T> X0[H], X1[H];
-#pragma unroll
-                    for (int k = 0; k < H; ++k) {
-                        X0[k] = Is0[r0 * H + k];
-                        X1[k] = Is0[r1 * H + k];
-                    }
-                    T y0[N], y1[N];
-                    c2r_pair<N, T>(X0, X1, y0, y1, tw);
+                    C2<T> z[N];                      // z[n] = (row r0, row r1) at x = n
+                    c2r_rows_from<N, T>(Is0 + r0 * H, Is0 + r1 * H, z, tw);
                     // S and G are stored column-major ([x][row]): consecutive threads own
                     // consecutive rows, so every access below is conflict free without padding
                     T *S0 = Sb + r0, *S1 = Sb + r1;
@@ -487,35 +512,35 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
                     switch (op.kind) {
                     case OP_S_SET:
 #pragma unroll
-                        for (int n = 0; n < N; ++n) { S0[n * rows] = w * y0[n]; S1[n * rows] = w * y1[n]; }
+                        for (int n = 0; n < N; ++n) { S0[n * rows] = w * z[n].x; S1[n * rows] = w * z[n].y; }
                         break;
                     case OP_S_ADD:
 #pragma unroll
-                        for (int n = 0; n < N; ++n) { S0[n * rows] += w * y0[n]; S1[n * rows] += w * y1[n]; }
+                        for (int n = 0; n < N; ++n) { S0[n * rows] += w * z[n].x; S1[n * rows] += w * z[n].y; }
                         break;
                     case OP_G_SET:
 #pragma unroll
-                        for (int n = 0; n < N; ++n) { G0[n * rows] = y0[n] * S0[n * rows]; G1[n * rows] = y1[n] * S1[n * rows]; }
+                        for (int n = 0; n < N; ++n) { G0[n * rows] = z[n].x * S0[n * rows]; G1[n * rows] = z[n].y * S1[n * rows]; }
                         break;
                     case OP_G_ADD:
 #pragma unroll
-                        for (int n = 0; n < N; ++n) { G0[n * rows] += y0[n] * S0[n * rows]; G1[n * rows] += y1[n] * S1[n * rows]; }
+                        for (int n = 0; n < N; ++n) { G0[n * rows] += z[n].x * S0[n * rows]; G1[n * rows] += z[n].y * S1[n * rows]; }
                         break;
                     case OP_NU_INIT: {          // paired mode, first pass: G = -F nu
                         bool big = false;
 #pragma unroll
                         for (int half = 0; half < 2; ++half) {
                             const int r = half ? r1 : r0;
-                            const T *nu = half ? y1 : y0;
                             T fr[N];
                             load_row<T, N>(F + ((int64_t)rank * rows + r) * N, fr);
                             T *Gr = Gb + r;
-                            T mx = nu[0];
+                            T mx = half ? z[0].y : z[0].x;
 #pragma unroll
                             for (int n = 0; n < N; ++n) {
-                                Gr[n * rows] = -fr[n] * nu[n];
-                                mx = nu[n] > mx ? nu[n] : mx;
-                                if (T(a.dt) * nu[n] > T(1)) big = true;
+                                const T nu = half ? z[n].y : z[n].x;
+                                Gr[n * rows] = -fr[n] * nu;
+                                mx = nu > mx ? nu : mx;
+                                if (T(a.dt) * nu > T(1)) big = true;
                             }
                             dg.max_nu = fmax(dg.max_nu, (double)mx);
                         }
@@ -525,12 +550,13 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 #pragma unroll
                         for (int half = 0; half < 2; ++half) {
                             const int r = half ? r1 : r0;
-                            const T *nu = half ? y1 : y0;
                             const int64_t grow = (int64_t)rank * rows + r;
-                            T fr[N];
+                            T fr[N], nu[N];
                             load_row<T, N>(F + grow * N, fr);
                             T *Gr = Gb + r;
                             T qv[N];
+#pragma unroll
+                            for (int n = 0; n < N; ++n) nu[n] = half ? z[n].y : z[n].x;
                             T mx = nu[0];
 #pragma unroll
                             for (int n = 0; n < N; ++n) {

@@ -57,6 +57,8 @@ struct CollideArgs {
     int prefetch;             // 1: prefetch the next op's multipliers into L1
     int paired;               // 1: two spectral slabs per CTA and the paired op kinds
     const long long *dev_ncells;  // nullable: cell count read from device memory at kernel start
+    void *fh_ws;              // forward spectrum workspace: per cluster slot N * NP complex, [z][p]
+    int npc;                  // axis-0 pencils per CTA (even; CTA r owns [r npc, (r + 1) npc) of NP)
 };
 
 // Arguments of the low-mode feature kernel (one launch per size class).

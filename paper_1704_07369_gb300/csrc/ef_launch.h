@@ -39,6 +39,19 @@ struct PlanView {
     int device;
 };
 bool plan_view(const struct ef_plan_s *p, PlanView *out);
+
+// Axis-0 pencils per CTA of a C-CTA cluster (even, so that lane pairs never straddle CTAs) and the
+// bytes of one cluster's forward-spectrum workspace (N x NP complex).
+inline int collide_npc(int d, int N, int C)
+{
+    const int NP = (d == 3 ? N : 1) * (N / 2 + 1);
+    const int npc = (NP + C - 1) / C;
+    return (npc + 1) / 2 * 2;
+}
+inline size_t collide_fh_bytes(int prec, int d, int N)
+{
+    return (size_t)N * (d == 3 ? N : 1) * (N / 2 + 1) * (prec == 0 ? 8 : 16);
+}
 size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired);
 cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
                            cudaStream_t s);

@@ -85,17 +85,20 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
     ef_status st = scratch_address(dev, &base);
     if (st != EF_OK) return st;
 
-    // S and G of one CTA in global memory: 2 * rows * N values
+    // per cluster: S and G of each CTA in global memory (2 * rows * N values per CTA) and the
+    // forward-spectrum workspace; layout [counter][S/G of grid * C CTAs][spectra of grid clusters]
     const int64_t rows = (int64_t)v.planes * (v.d == 3 ? v.N : 1);
     const size_t el = v.prec == EF_PREC_F32 ? 4 : 8;
-    const size_t per_cta = (size_t)2 * rows * v.N * el;
+    const size_t per_cta = ((size_t)2 * rows * v.N * el + 255) / 256 * 256;
+    const size_t per_fh = (ef::collide_fh_bytes(v.prec, v.d, v.N) + 255) / 256 * 256;
+    const size_t per_cluster = per_cta * v.cluster + per_fh;
     const size_t avail = kScratchBytes - kCounterBytes;
-    const int64_t clusters_fit = (int64_t)(avail / per_cta) / v.cluster;
+    const int64_t clusters_fit = (int64_t)(avail / per_cluster);
     if (clusters_fit < 1) {
         char buf[200];
         std::snprintf(buf, sizeof(buf),
                       "ef_collide_noalloc: one cell cluster needs %zu bytes of scratch, more than the %zu available",
-                      per_cta * v.cluster, avail);
+                      per_cluster, avail);
         ef::set_last_error(buf);
         return EF_ERR_UNSUPPORTED;
     }
@@ -119,6 +122,8 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
     a.planes = v.planes;
     a.sg_global = 1;
     a.sg_ws = static_cast<unsigned char *>(base) + kCounterBytes;
+    a.fh_ws = static_cast<unsigned char *>(base) + kCounterBytes + (size_t)grid * v.cluster * per_cta;
+    a.npc = ef::collide_npc(v.d, v.N, v.cluster);
     a.out_mode = ef::OUT_COLLIDE;
     a.h = 2.0 * v.L / v.N;
     a.status = v.status;

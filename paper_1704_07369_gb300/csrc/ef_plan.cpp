@@ -255,6 +255,8 @@ struct ClassPlan {
     int64_t *d_cell_off = nullptr, *d_cell_id = nullptr;
     void *d_sg = nullptr;
     int64_t sg_slots = 0;
+    void *d_fh = nullptr;                // forward-spectrum workspace, fh_slots clusters
+    int64_t fh_slots = 0;
 };
 
 }  // namespace
@@ -327,9 +329,10 @@ struct Shape {
 };
 
 // Every launch shape that fits one N: cluster sizes C | N with an even number of real rows per
-// CTA, one stage-A pencil per thread (C * tpb >= pencils), at most the instantiation's thread
-// limit, shared memory within the device's opt-in limit (S/G in global memory only when nothing
-// fits otherwise) and at least one co-resident cluster.
+// CTA; threads per CTA enough for one work item each of the widest stage (the stage-A (direction,
+// pencil) items, the axis-1 columns or the row pairs), or half of that (two rounds), at most the
+// instantiation's thread limit; shared memory within the device's opt-in limit (S/G in global
+// memory only when nothing fits otherwise) and at least one co-resident cluster.
 std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
 {
     const int d = ds.d;
@@ -347,21 +350,26 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
                 const int planes = N / C;
                 const int rows = planes * N1;
                 if (rows % 2) continue;
-                const int need = std::max({(NP + C - 1) / C, rows / 2, d == 3 ? planes * H : 1});
-                const int tpb = std::max(64, (need + 31) / 32 * 32);
-                if (tpb > maxthreads_for(ds.prec, d, N)) continue;
-                if ((int64_t)C * tpb < NP) continue;
+                const int nb = paired ? 2 : 1;
+                const int need = std::max({nb * ef::collide_npc(d, N, C), paired ? rows : rows / 2,
+                                           d == 3 ? nb * planes * H : 1});
                 const size_t smem = smem_for(ds.prec, d, N, planes, sg, paired);
                 if ((long)smem > smem_max) continue;
-                int mc = 0;
-                cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, &mc);
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    why = cudaGetErrorString(e);
-                    continue;
+                int last = 0;
+                for (int rounds = 1; rounds <= 2; ++rounds) {
+                    const int tpb = std::max(64, ((need + rounds - 1) / rounds + 31) / 32 * 32);
+                    if (tpb > maxthreads_for(ds.prec, d, N) || tpb == last) continue;
+                    last = tpb;
+                    int mc = 0;
+                    cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, &mc);
+                    if (e != cudaSuccess) {
+                        cudaGetLastError();
+                        why = cudaGetErrorString(e);
+                        continue;
+                    }
+                    if (mc <= 0) continue;
+                    out.push_back(Shape{C, tpb, planes, sg, paired, smem, mc});
                 }
-                if (mc <= 0) continue;
-                out.push_back(Shape{C, tpb, planes, sg, paired, smem, mc});
             }
         }
     }
@@ -396,7 +404,8 @@ std::string device_key()
 std::string tune_key(const Desc &ds, int N)
 {
     char buf[256];
-    std::snprintf(buf, sizeof(buf), "%s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
+    // "v2": kernel layout generation (threads per CTA count stage-A items, not pencils)
+    std::snprintf(buf, sizeof(buf), "v2 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
                   ds.d, N, (int)ds.kernel, ds.R, ds.J, ds.nmu, ds.nphi, ds.nc, ds.sigma);
     return buf;
 }
@@ -457,12 +466,15 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     const int d = ds.d;
     const int64_t cell = d == 3 ? (int64_t)cp.N * cp.N * cp.N : (int64_t)cp.N * cp.N;
     const size_t el = ds.prec == EF_PREC_F32 ? 4 : 8;
-    void *F = nullptr, *Q = nullptr, *sgws = nullptr;
+    void *F = nullptr, *Q = nullptr, *sgws = nullptr, *fhws = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaMalloc(&F, ncells_tune * cell * el);
     if (e == cudaSuccess) e = cudaMalloc(&Q, ncells_tune * cell * el);
     if (e == cudaSuccess) e = cudaMemset(F, 0, ncells_tune * cell * el);
+    int64_t fh_need = 0;
+    for (const Shape &sh : shapes) fh_need = std::max<int64_t>(fh_need, std::min<int64_t>(ncells_tune, sh.max_clusters));
+    if (e == cudaSuccess) e = cudaMalloc(&fhws, (size_t)fh_need * ef::collide_fh_bytes(ds.prec, d, cp.N));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -492,6 +504,8 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
             a.planes = sh.planes;
             a.sg_global = sh.sg_global;
             a.sg_ws = sgws;
+            a.fh_ws = fhws;
+            a.npc = ef::collide_npc(d, cp.N, sh.cluster);
             a.out_mode = ef::OUT_COLLIDE;
             a.h = 1.0;
             a.prefetch = pfv;
@@ -515,6 +529,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     cudaFree(F);
     cudaFree(Q);
     cudaFree(sgws);
+    cudaFree(fhws);
     if (st) cudaStreamDestroy(st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -655,6 +670,12 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
 
 ef_status ensure_sg(ef_plan_s *p, ClassPlan &cp, int grid_clusters)
 {
+    if (grid_clusters > cp.fh_slots) {
+        if (cp.d_fh) cudaFree(cp.d_fh);
+        cudaError_t e = cudaMalloc(&cp.d_fh, (size_t)grid_clusters * ef::collide_fh_bytes(p->desc.prec, p->desc.d, cp.N));
+        if (e != cudaSuccess) { cp.d_fh = nullptr; cp.fh_slots = 0; return cuda_fail(e, "spectrum workspace"); }
+        cp.fh_slots = grid_clusters;
+    }
     if (!cp.sg_global) return EF_OK;
     const int N = cp.N, N1 = p->desc.d == 3 ? N : 1;
     const int64_t rows = (int64_t)cp.planes * N1;
@@ -679,6 +700,7 @@ void destroy_plan(ef_plan_s *p)
         cudaFree(cp.d_cell_off);
         cudaFree(cp.d_cell_id);
         cudaFree(cp.d_sg);
+        cudaFree(cp.d_fh);
     }
     cudaFree(p->d_all_off);
     cudaFree(p->d_all_N);
@@ -755,7 +777,14 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
               cudaStream_t s)
 {
     const Desc &ds = p->desc;
-    const bool multi = p->classes.size() > 1;
+    // size classes run back to back on the caller's stream unless EF_CONCURRENT_CLASSES=1 forks
+    // them onto their own streams (concurrent clusters of different sizes fragment the SMs'
+    // shared memory, which measured slower)
+    static const bool concurrent = [] {
+        const char *v = std::getenv("EF_CONCURRENT_CLASSES");
+        return v && v[0] == '1';
+    }();
+    const bool multi = concurrent && p->classes.size() > 1;
     cudaError_t e;
     if (multi) {
         e = cudaEventRecord(p->fork, s);
@@ -789,6 +818,8 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
         a.planes = cp.planes;
         a.sg_global = cp.sg_global;
         a.sg_ws = cp.d_sg;
+        a.fh_ws = cp.d_fh;
+        a.npc = ef::collide_npc(ds.d, cp.N, cp.cluster);
         a.out_mode = mode;
         a.dt = dt;
         a.h = 2.0 * ds.L / cp.N;

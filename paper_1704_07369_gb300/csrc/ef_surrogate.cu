@@ -274,6 +274,7 @@ struct ef_surrogate_s {
     float pi_over_L = 0.f;
     float *featF = nullptr, *featL = nullptr, *X = nullptr, *Y = nullptr, *qplain = nullptr;
     void *Qs = nullptr;
+    void *fh = nullptr;                   // forward-spectrum workspace of the fallback collide launches
     unsigned *audit = nullptr;            // [0] audited cells, [1] audited misses (this call)
     unsigned long long *count = nullptr;
     int64_t *list_off = nullptr, *list_id = nullptr;
@@ -299,6 +300,7 @@ void sur_free(ef_surrogate_s *s)
     cudaFree(s->Y);
     cudaFree(s->qplain);
     cudaFree(s->Qs);
+    cudaFree(s->fh);
     cudaFree(s->audit);
     cudaFree(s->count);
     cudaFree(s->list_off);
@@ -378,6 +380,7 @@ ef_status ef_surrogate_create(ef_plan_t plan, ef_mlp_t mlp, int64_t max_batch, e
     alloc((void **)&s->Y, (size_t)max_batch * s->noutp * 4);
     alloc((void **)&s->qplain, (size_t)max_batch * kStride * 4);
     alloc((void **)&s->Qs, (size_t)max_batch * cell * el);
+    alloc((void **)&s->fh, (size_t)v.max_clusters * ef::collide_fh_bytes(v.prec, v.d, v.N));
     alloc((void **)&s->audit, 8);
     alloc((void **)&s->count, 8);
     alloc((void **)&s->list_off, (size_t)max_batch * 8);
@@ -513,6 +516,8 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
         a.cluster = v.cluster;
         a.planes = v.planes;
         a.paired = v.paired;
+        a.fh_ws = s->fh;
+        a.npc = ef::collide_npc(v.d, v.N, v.cluster);
         a.out_mode = ef::OUT_COLLIDE;
         a.h = 2.0 * v.L / v.N;
         a.status = v.status;
