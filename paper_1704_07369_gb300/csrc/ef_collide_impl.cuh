@@ -35,6 +35,16 @@ namespace cg = cooperative_groups;
 template <typename T, int N>
 __host__ __device__ constexpr int max_threads() { return (sizeof(T) == 8 || N >= 40) ? 256 : 320; }
 
+// Second instantiation for two co-resident CTAs per SM (of different cells, whose barrier phases
+// then overlap): at most 6 warps per CTA, so 12 per SM and 168 registers per thread.  Built for
+// the FP32 3D sizes of the batched workload; the autotuner chooses between the two.
+constexpr int kOcc2Threads = 192;
+template <typename T, int D, int N>
+__host__ __device__ constexpr bool occ2_built()
+{
+    return sizeof(T) == 4 && D == 3 && (N == 24 || N == 32 || N == 40 || N == 48);
+}
+
 template <typename T>
 __device__ __forceinline__ void sincospi_t(T x, T *s, T *c);
 template <>
@@ -230,14 +240,54 @@ __device__ __forceinline__ void emit_row(const CollideArgs &a, const T (&fr)[N],
     }
 }
 
+// Distributed shared memory through explicit shared::cluster addresses: mapa turns this CTA's
+// shared-memory address into the same offset in CTA `rank` of the cluster, and the loads / stores
+// name the state space, so that they take the shared-memory path rather than the generic one.
+__device__ __forceinline__ uint32_t smem_u32addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, int rank)
+{
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, float4 v)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, C2<float> v)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, C2<double> v)
+{
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t a)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ void ld_cluster(uint32_t a, C2<float> &v)
+{
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void ld_cluster(uint32_t a, C2<double> &v)
+{
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+}
+
 // Stage-A scatter of one inverse-transformed axis-0 pencil into the owners' slabs.  For FP32,
 // lanes 2j and 2j+1 hold the adjacent pencils p, p+1 (p even); one shuffle per z pair lets each
 // lane write both pencils of one z as a single 16-byte store, halving the number of (mostly
 // remote, distributed shared memory) store transactions.
 template <typename T, int N, bool WIDE>
 __device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab, int P, int NP, int pencil,
-                                               cg::cluster_group &cl, unsigned mask)
+                                               unsigned mask)
 {
+    const uint32_t base = smem_u32addr(slab);
     if constexpr (WIDE) {
         const bool odd = pencil & 1;
         const int pbase = pencil & ~1;
@@ -251,24 +301,23 @@ __device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab,
             const C2<T> lo = odd ? recv : v[z0];
             const C2<T> hi = odd ? v[z0 + 1] : recv;
             const int owner = z / P, zl = z - owner * P;
-            float4 *dst = reinterpret_cast<float4 *>(cl.map_shared_rank(slab, owner) + (size_t)zl * NP + pbase);
-            *dst = make_float4(lo.x, lo.y, hi.x, hi.y);
+            const uint32_t dst = cluster_map(base + (uint32_t)((zl * NP + pbase) * sizeof(C2<T>)), owner);
+            st_cluster(dst, make_float4(lo.x, lo.y, hi.x, hi.y));
         }
     } else {
 #pragma unroll
         for (int z = 0; z < N; ++z) {
             const int owner = z / P, zl = z - owner * P;
-            C2<T> *dst = cl.map_shared_rank(slab, owner);
-            dst[(size_t)zl * NP + pencil] = v[z];
+            st_cluster(cluster_map(base + (uint32_t)((zl * NP + pencil) * sizeof(C2<T>)), owner), v[z]);
         }
     }
 }
 
 // The matching gather (forward pass F2): 16-byte loads of both pencils of one z, one shuffle.
 template <typename T, int N, bool WIDE>
-__device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P, int NP, int pencil,
-                                              cg::cluster_group &cl, unsigned mask)
+__device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P, int NP, int pencil, unsigned mask)
 {
+    const uint32_t base = smem_u32addr(slab);
     if constexpr (WIDE) {
         const bool odd = pencil & 1;
         const int pbase = pencil & ~1;
@@ -276,7 +325,7 @@ __device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P,
         for (int z0 = 0; z0 < N; z0 += 2) {
             const int z = odd ? z0 + 1 : z0;
             const int owner = z / P, zl = z - owner * P;
-            const float4 w = *reinterpret_cast<const float4 *>(cl.map_shared_rank(slab, owner) + (size_t)zl * NP + pbase);
+            const float4 w = ld_cluster_f4(cluster_map(base + (uint32_t)((zl * NP + pbase) * sizeof(C2<T>)), owner));
             const C2<T> lo = C2<T>{w.x, w.y}, hi = C2<T>{w.z, w.w};
             const C2<T> send = odd ? lo : hi;
             C2<T> recv;
@@ -289,14 +338,13 @@ __device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P,
 #pragma unroll
         for (int z = 0; z < N; ++z) {
             const int owner = z / P, zl = z - owner * P;
-            const C2<T> *src = cl.map_shared_rank(slab, owner);
-            v[z] = src[(size_t)zl * NP + pencil];
+            ld_cluster(cluster_map(base + (uint32_t)((zl * NP + pencil) * sizeof(C2<T>)), owner), v[z]);
         }
     }
 }
 
-template <typename T, int D, int N>
-__global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const CollideArgs a)
+template <typename T, int D, int N, int OCC = 1>
+__global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads, OCC) collide_kernel(const CollideArgs a)
 {
     constexpr int H = N / 2 + 1;
     constexpr int N1 = (D == 3) ? N : 1;
@@ -415,7 +463,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
             const unsigned mask = __ballot_sync(0xffffffffu, has);
             if (has) {
                 C2<T> v[N];
-                gather_pencil<T, N, WIDE>(v, Is0, P, NP, pencil, cl, mask);
+                gather_pencil<T, N, WIDE>(v, Is0, P, NP, pencil, mask);
                 fft<N, -1, N>(v, tw);
 #pragma unroll
                 for (int z = 0; z < N; ++z) Fh[(size_t)z * NP + pencil] = cscale(v[z], scale);
@@ -447,7 +495,7 @@ __global__ void __launch_bounds__(max_threads<T, N>(), 1) collide_kernel(const C
 #pragma unroll
                     for (int z = 0; z < N; ++z) v[z] = cscale(Fh[(size_t)z * NP + pencil], __ldg(M + (size_t)z * NP));
                     fft<N, 1, N>(v, tw);
-                    scatter_pencil<T, N, WIDE>(v, b ? Is1 : Is0, P, NP, pencil, cl, mask);
+                    scatter_pencil<T, N, WIDE>(v, b ? Is1 : Is0, P, NP, pencil, mask);
                     if (a.prefetch && o + 1 < a.nops) {   // pull the next op's multipliers towards L1
                         const Op nx = a.ops[o + 1];
                         const T *Mn = Mbase + (size_t)(b ? nx.dir2 : nx.dir) * N * NP + pencil;

@@ -12,11 +12,11 @@ namespace ef {
 
 #define EF_DECLARE_VARIANT(SUF)                                                                      \
     bool collide_supported_##SUF(int N);                                                             \
-    int collide_maxthreads_##SUF(int N);                                                             \
+    int collide_maxthreads_##SUF(int N, int occ);                                                    \
     size_t collide_smem_##SUF(int N, int planes, int sg_global, int paired);                         \
-    cudaError_t collide_setup_##SUF(int N, size_t smem, int cluster, int tpb, int *max_clusters);    \
+    cudaError_t collide_setup_##SUF(int N, size_t smem, int cluster, int tpb, int occ, int *max_clusters); \
     cudaError_t collide_launch_##SUF(int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, \
-                                     cudaStream_t s);
+                                     int occ, cudaStream_t s);
 
 EF_DECLARE_VARIANT(f32_2d)
 EF_DECLARE_VARIANT(f32_3d)
@@ -30,6 +30,7 @@ EF_DECLARE_VARIANT(f64_3d)
 struct PlanView {
     int prec, d, N;
     int cluster, tpb, planes, paired, nops, max_clusters, sg_global, nfeat;   // nfeat: band modes
+    int occ;                  // kernel instantiation: 1 or 2 CTAs per SM
     size_t smem;
     double L;
     const void *mult;
@@ -54,7 +55,7 @@ inline size_t collide_fh_bytes(int prec, int d, int N)
 }
 size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired);
 cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
-                           cudaStream_t s);
+                           int occ, cudaStream_t s);
 void set_last_error(const char *msg);
 
 // low-mode features (ef_features_f32.cu / ef_features_f64.cu): nf = 1 or 2 fields; the grid is

@@ -129,7 +129,7 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
     a.status = v.status;
     a.counter = static_cast<unsigned long long *>(base);
     a.paired = v.paired;
-    e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, smem, s);
+    e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, smem, v.occ, s);
     if (e != cudaSuccess) {
         ef::set_last_error(cudaGetErrorString(e));
         return EF_ERR_CUDA;

@@ -241,7 +241,7 @@ int mode_of(int N, int i) { return i < N / 2 ? i : i - N; }
 struct ClassPlan {
     int N = 0;
     int64_t ncells = 0;                 // batched: cells of this size; uniform plan: 0
-    int cluster = 1, tpb = 32, planes = 0, sg_global = 0, prefetch = 1, paired = 0;
+    int cluster = 1, tpb = 32, planes = 0, sg_global = 0, prefetch = 1, paired = 0, occ = 1;
     double tuned_ms = 0.0;              // autotuner's best time (0 when not tuned)
     size_t smem = 0;
     int max_clusters = 0;
@@ -295,10 +295,10 @@ bool size_built(int prec, int d, int N)
     return d == 3 ? ef::collide_supported_f64_3d(N) : ef::collide_supported_f64_2d(N);
 }
 
-int maxthreads_for(int prec, int d, int N)
+int maxthreads_for(int prec, int d, int N, int occ)
 {
-    if (prec == EF_PREC_F32) return d == 3 ? ef::collide_maxthreads_f32_3d(N) : ef::collide_maxthreads_f32_2d(N);
-    return d == 3 ? ef::collide_maxthreads_f64_3d(N) : ef::collide_maxthreads_f64_2d(N);
+    if (prec == EF_PREC_F32) return d == 3 ? ef::collide_maxthreads_f32_3d(N, occ) : ef::collide_maxthreads_f32_2d(N, occ);
+    return d == 3 ? ef::collide_maxthreads_f64_3d(N, occ) : ef::collide_maxthreads_f64_2d(N, occ);
 }
 
 size_t smem_for(int prec, int d, int N, int planes, int sg, int paired)
@@ -308,22 +308,25 @@ size_t smem_for(int prec, int d, int N, int planes, int sg, int paired)
     return d == 3 ? ef::collide_smem_f64_3d(N, planes, sg, paired) : ef::collide_smem_f64_2d(N, planes, sg, paired);
 }
 
-cudaError_t setup_for(int prec, int d, int N, size_t smem, int cl, int tpb, int *mc)
+cudaError_t setup_for(int prec, int d, int N, size_t smem, int cl, int tpb, int occ, int *mc)
 {
     if (prec == EF_PREC_F32)
-        return d == 3 ? ef::collide_setup_f32_3d(N, smem, cl, tpb, mc) : ef::collide_setup_f32_2d(N, smem, cl, tpb, mc);
-    return d == 3 ? ef::collide_setup_f64_3d(N, smem, cl, tpb, mc) : ef::collide_setup_f64_2d(N, smem, cl, tpb, mc);
+        return d == 3 ? ef::collide_setup_f32_3d(N, smem, cl, tpb, occ, mc) : ef::collide_setup_f32_2d(N, smem, cl, tpb, occ, mc);
+    return d == 3 ? ef::collide_setup_f64_3d(N, smem, cl, tpb, occ, mc) : ef::collide_setup_f64_2d(N, smem, cl, tpb, occ, mc);
 }
 
-cudaError_t launch_for(int prec, int d, int N, const ef::CollideArgs &a, int grid, int tpb, size_t smem, cudaStream_t s)
+cudaError_t launch_for(int prec, int d, int N, const ef::CollideArgs &a, int grid, int tpb, size_t smem, int occ,
+                       cudaStream_t s)
 {
     if (prec == EF_PREC_F32)
-        return d == 3 ? ef::collide_launch_f32_3d(N, a, grid, tpb, smem, s) : ef::collide_launch_f32_2d(N, a, grid, tpb, smem, s);
-    return d == 3 ? ef::collide_launch_f64_3d(N, a, grid, tpb, smem, s) : ef::collide_launch_f64_2d(N, a, grid, tpb, smem, s);
+        return d == 3 ? ef::collide_launch_f32_3d(N, a, grid, tpb, smem, occ, s)
+                      : ef::collide_launch_f32_2d(N, a, grid, tpb, smem, occ, s);
+    return d == 3 ? ef::collide_launch_f64_3d(N, a, grid, tpb, smem, occ, s)
+                  : ef::collide_launch_f64_2d(N, a, grid, tpb, smem, occ, s);
 }
 
 struct Shape {
-    int cluster, tpb, planes, sg_global, paired;
+    int cluster, tpb, planes, sg_global, paired, occ;
     size_t smem;
     int max_clusters;
 };
@@ -355,20 +358,23 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
                                            d == 3 ? nb * planes * H : 1});
                 const size_t smem = smem_for(ds.prec, d, N, planes, sg, paired);
                 if ((long)smem > smem_max) continue;
-                int last = 0;
-                for (int rounds = 1; rounds <= 2; ++rounds) {
-                    const int tpb = std::max(64, ((need + rounds - 1) / rounds + 31) / 32 * 32);
-                    if (tpb > maxthreads_for(ds.prec, d, N) || tpb == last) continue;
-                    last = tpb;
-                    int mc = 0;
-                    cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, &mc);
-                    if (e != cudaSuccess) {
-                        cudaGetLastError();
-                        why = cudaGetErrorString(e);
-                        continue;
+                for (int occ = 1; occ <= 2; ++occ) {
+                    const int tmax = maxthreads_for(ds.prec, d, N, occ);
+                    int last = 0;
+                    for (int rounds = 1; rounds <= 2; ++rounds) {
+                        const int tpb = std::max(64, ((need + rounds - 1) / rounds + 31) / 32 * 32);
+                        if (tpb > tmax || tpb == last) continue;
+                        last = tpb;
+                        int mc = 0;
+                        cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, occ, &mc);
+                        if (e != cudaSuccess) {
+                            cudaGetLastError();
+                            why = cudaGetErrorString(e);
+                            continue;
+                        }
+                        if (mc <= 0) continue;
+                        out.push_back(Shape{C, tpb, planes, sg, paired, occ, smem, mc});
                     }
-                    if (mc <= 0) continue;
-                    out.push_back(Shape{C, tpb, planes, sg, paired, smem, mc});
                 }
             }
         }
@@ -383,6 +389,7 @@ void apply_shape(ClassPlan &cp, const Shape &sh)
     cp.planes = sh.planes;
     cp.sg_global = sh.sg_global;
     cp.paired = sh.paired;
+    cp.occ = sh.occ;
     cp.smem = sh.smem;
     cp.max_clusters = sh.max_clusters;
     cp.d_ops = sh.paired ? cp.d_ops_paired : cp.d_ops_single;
@@ -404,13 +411,13 @@ std::string device_key()
 std::string tune_key(const Desc &ds, int N)
 {
     char buf[256];
-    // "v2": kernel layout generation (threads per CTA count stage-A items, not pencils)
-    std::snprintf(buf, sizeof(buf), "v2 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
+    // "v3": kernel layout generation (threads per CTA count stage-A items; occupancy variants)
+    std::snprintf(buf, sizeof(buf), "v3 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
                   ds.d, N, (int)ds.kernel, ds.R, ds.J, ds.nmu, ds.nphi, ds.nc, ds.sigma);
     return buf;
 }
 
-bool cache_lookup(const std::string &key, int &C, int &tpb, int &sg, int &pf, int &pr)
+bool cache_lookup(const std::string &key, int &C, int &tpb, int &sg, int &pf, int &pr, int &occ)
 {
     const char *path = std::getenv("EF_AUTOTUNE_CACHE");
     if (!path) return false;
@@ -422,19 +429,19 @@ bool cache_lookup(const std::string &key, int &C, int &tpb, int &sg, int &pf, in
         std::string ln(line);
         const size_t bar = ln.find('|');
         if (bar == std::string::npos || ln.substr(0, bar) != key) continue;
-        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d %d %d", &C, &tpb, &sg, &pf, &pr) == 5) found = true;
+        if (std::sscanf(ln.c_str() + bar + 1, "%d %d %d %d %d %d", &C, &tpb, &sg, &pf, &pr, &occ) == 6) found = true;
     }
     std::fclose(f);
     return found;
 }
 
-void cache_store(const std::string &key, int C, int tpb, int sg, int pf, int pr, double ms)
+void cache_store(const std::string &key, int C, int tpb, int sg, int pf, int pr, int occ, double ms)
 {
     const char *path = std::getenv("EF_AUTOTUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s|%d %d %d %d %d %.4f\n", key.c_str(), C, tpb, sg, pf, pr, ms);
+    std::fprintf(f, "%s|%d %d %d %d %d %d %.4f\n", key.c_str(), C, tpb, sg, pf, pr, occ, ms);
     std::fclose(f);
 }
 
@@ -454,10 +461,10 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     const bool tune = ncells_tune > 0 && !(env && env[0] == '0') && shapes.size() > 1;
     if (!tune) return EF_OK;
     const std::string key = tune_key(ds, cp.N);
-    int C = 0, tpb = 0, sg = 0, pf = 1, pr = 0;
-    if (cache_lookup(key, C, tpb, sg, pf, pr)) {
+    int C = 0, tpb = 0, sg = 0, pf = 1, pr = 0, occ = 1;
+    if (cache_lookup(key, C, tpb, sg, pf, pr, occ)) {
         for (const Shape &sh : shapes)
-            if (sh.cluster == C && sh.tpb == tpb && sh.sg_global == sg && sh.paired == pr) {
+            if (sh.cluster == C && sh.tpb == tpb && sh.sg_global == sg && sh.paired == pr && sh.occ == occ) {
                 apply_shape(cp, sh);
                 cp.prefetch = pf;
                 return EF_OK;
@@ -512,7 +519,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
             double tmin = 1e30;
             for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
                 e = cudaEventRecord(e0, st);
-                if (e == cudaSuccess) e = launch_for(ds.prec, d, cp.N, a, grid, sh.tpb, sh.smem, st);
+                if (e == cudaSuccess) e = launch_for(ds.prec, d, cp.N, a, grid, sh.tpb, sh.smem, sh.occ, st);
                 if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -537,7 +544,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     apply_shape(cp, best_sh);
     cp.prefetch = best_pf;
     cp.tuned_ms = best;
-    cache_store(key, best_sh.cluster, best_sh.tpb, best_sh.sg_global, best_pf, best_sh.paired, best);
+    cache_store(key, best_sh.cluster, best_sh.tpb, best_sh.sg_global, best_pf, best_sh.paired, best_sh.occ, best);
     return EF_OK;
 }
 
@@ -828,7 +835,7 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
         a.counter = multi ? p->d_counters + ci : nullptr;
         a.prefetch = cp.prefetch;
         a.paired = cp.paired;
-        e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, cs);
+        e = launch_for(ds.prec, ds.d, cp.N, a, grid, cp.tpb, cp.smem, cp.occ, cs);
         if (e != cudaSuccess) return cuda_fail(e, "collide launch");
         if (multi) {
             e = cudaEventRecord(p->cevents[ci], cs);
@@ -1057,6 +1064,7 @@ bool plan_view(const ef_plan_s *p, PlanView *out)
     out->max_clusters = cp.max_clusters;
     out->sg_global = cp.sg_global;
     out->nfeat = cp.nfeat;
+    out->occ = cp.occ;
     out->smem = cp.smem;
     out->modes = cp.d_modes;
     out->L = p->desc.L;
@@ -1094,9 +1102,9 @@ size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paire
 }
 
 cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
-                           cudaStream_t s)
+                           int occ, cudaStream_t s)
 {
-    return launch_for(prec, d, N, a, grid_clusters, tpb, smem, s);
+    return launch_for(prec, d, N, a, grid_clusters, tpb, smem, occ, s);
 }
 
 void set_last_error(const char *msg) { g_last_error = msg; }

@@ -522,7 +522,7 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
         a.h = 2.0 * v.L / v.N;
         a.status = v.status;
         const int grid = (int)std::min<int64_t>(ncells, v.max_clusters);
-        e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, v.smem, st);
+        e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, v.smem, v.occ, st);
         if (e != cudaSuccess) return scuda(e, "fallback collide");
         ef::FeatArgs qa{};
         qa.F = s->Qs;
