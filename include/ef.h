@@ -115,6 +115,17 @@ ef_status ef_collide(ef_plan_t plan, const void *F_dev, void *Q_dev, int64_t nce
 ef_status ef_euler_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, double *diag_dev,
                         int64_t ncells, ef_stream_t stream);
 
+/* nsteps third-order strong-stability-preserving Runge-Kutta steps (Gottlieb, Shu and Tadmor; the
+ * time integrator of Sec. 4.1), in place:
+ *   F1 = F + dt Q[F],  F2 = 3/4 F + 1/4 (F1 + dt Q[F1]),  F <- 1/3 F + 2/3 (F2 + dt Q[F2]).
+ * Each stage is a convex combination of forward Euler steps, so positivity carries over from the
+ * Euler step under the same dt max nu <= 1.  diag_dev (nullable) receives, per step, the diagnostics
+ * of the first stage ([step][cell][k] as for ef_euler_step: moments of F before the step).  The
+ * plan keeps two batch-sized stage buffers, allocated on the first call (and grown, after a device
+ * synchronisation, when a later call needs more).  F must be 16-byte aligned. */
+ef_status ef_rk3_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, double *diag_dev, int64_t ncells,
+                      ef_stream_t stream);
+
 /* ef_collide for callers that cannot allocate device memory when they evaluate the operator (a
  * host framework whose allocator owns all device memory, a real-time loop or callback where an
  * allocation may block or fail, code that must keep the device footprint fixed after start-up).
@@ -232,8 +243,9 @@ ef_status ef_surrogate_set_policy(ef_surrogate_t sur, float max_miss_fraction, f
 ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat, int *flags, int64_t ncells,
                              float audit_fraction, uint64_t seed, float tol, ef_stream_t stream);
 
-/* Moments and entropy of each cell (layout EF_DIAG_STRIDE, entries [0..7] and [9]; [8] = 0).
- * Q_dev may be null; then [6] = 0 and [9] = 0. */
+/* Moments and entropy of each cell (layout EF_DIAG_STRIDE, entries [0..7] and [9]).  Here [8] is
+ * the positivity error of Sec. 4.2, Example 1: (sum |F| - sum F) / sum |F| (0 for F >= 0), in place
+ * of max nu.  Q_dev may be null; then [6] = 0 and [9] = 0. */
 ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_dev, double *out_dev,
                              int64_t ncells, ef_stream_t stream);
 

@@ -34,7 +34,7 @@ EF_DIAG_STRIDE = 10
 
 # every symbol include/ef.h declares
 SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
-           "ef_collide", "ef_euler_step", "ef_moments_entropy", "ef_plan_status",
+           "ef_collide", "ef_euler_step", "ef_rk3_step", "ef_moments_entropy", "ef_plan_status",
            "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_collide_noalloc",
            "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_params",
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
@@ -97,6 +97,7 @@ def lib():
         L.ef_surrogate_set_policy.argtypes = [vp, ctypes.c_float, ctypes.c_float]
         L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
         L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
+        L.ef_rk3_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
         L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
         L.ef_plan_status.argtypes = [vp, i32, i32]
         L.ef_plan_set_graph.argtypes = [vp, i32]
@@ -279,6 +280,10 @@ def ef_euler_step(plan, F, dt, nsteps, diag, ncells, stream=None):
     _check(lib().ef_euler_step(plan, _ptr(F), float(dt), int(nsteps), _ptr(diag), int(ncells), _stream(stream)))
 
 
+def ef_rk3_step(plan, F, dt, nsteps, diag, ncells, stream=None):
+    _check(lib().ef_rk3_step(plan, _ptr(F), float(dt), int(nsteps), _ptr(diag), int(ncells), _stream(stream)))
+
+
 def ef_moments_entropy(plan, F, Q, out, ncells, stream=None):
     _check(lib().ef_moments_entropy(plan, _ptr(F), _ptr(Q), _ptr(out), int(ncells), _stream(stream)))
 
@@ -326,6 +331,9 @@ class Plan:
 
     def euler(self, F, dt, nsteps=1, diag=None, ncells=None, stream=None):
         ef_euler_step(self.handle, F, dt, nsteps, diag, self._n(F, ncells), stream)
+
+    def rk3(self, F, dt, nsteps=1, diag=None, ncells=None, stream=None):
+        ef_rk3_step(self.handle, F, dt, nsteps, diag, self._n(F, ncells), stream)
 
     def moments(self, F, Q, out, ncells=None, stream=None):
         ef_moments_entropy(self.handle, F, Q, out, self._n(F, ncells), stream)

@@ -671,7 +671,8 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
 
 // ------------------------------------------------------------------ moments kernel ---------
 
-// One CTA per cell: moments / entropy of F (and entropy production with Q), FP64 across the cell.
+// One CTA per cell: moments / entropy of F (and entropy production with Q), FP64 across the cell;
+// slot 8 holds the positivity error of Sec. 4.2 (the negative part of F, accumulated directly).
 // A warp walks rows (lanes along the contiguous axis, coalesced); each lane sums its values in T
 // over a run of at most 16 rows (at most 32 terms) and folds the run into FP64 accumulators, the
 // same split as the fused diagnostics of the collide kernel (no per-point FP64 work: the FP64 pipe
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, co
         double s[kDiag];
         for (int k = 0; k < kDiag; ++k) s[k] = 0.0;
         T mn = big, mq = big;
-        T p0 = 0, pz = 0, py = 0, px = 0, pe = 0, peta = 0, pprod = 0;
+        T p0 = 0, pz = 0, py = 0, px = 0, pe = 0, peta = 0, pprod = 0, pneg = 0;
         int run = 0;
         for (int r = warp; r < nrows; r += nw) {
             const T jz = (D == 3) ? T(r / N - N / 2) : T(0);
@@ -716,6 +717,7 @@ __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, co
                     if (Qr) pprod += Qr[x] * lf;
                 }
                 mn = f < mn ? f : mn;
+                pneg += f < T(0) ? -f : T(0);
                 if (Qr) mq = Qr[x] < mq ? Qr[x] : mq;
             }
             if (++run == kRun || r + nw >= nrows) {
@@ -731,7 +733,8 @@ __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, co
                 s[4] += (double)pe;
                 s[5] += (double)peta;
                 s[6] += (double)pprod;
-                p0 = pz = py = px = pe = peta = pprod = T(0);
+                s[8] += (double)pneg;
+                p0 = pz = py = px = pe = peta = pprod = pneg = T(0);
                 run = 0;
             }
         }
@@ -754,7 +757,11 @@ __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, co
             if (k == 0 || k == 5) v *= hd;
             else if (k >= 1 && k <= 3) v *= hd * h;
             else if (k == 4) v *= 0.5 * hd * h * h;
-            if (k == 8) v = 0.0;
+            if (k == 8) {       // positivity error (sum|F| - sum F) / sum|F| = 2 neg / (sum F + 2 neg)
+                double m = red[0][0];
+                for (int w = 1; w < nw; ++w) m += red[w][0];
+                v = (m + 2.0 * v) > 0.0 ? 2.0 * v / (m + 2.0 * v) : 0.0;
+            }
             if (D == 2 && k == 3) v = 0.0;
             out[c * kDiag + k] = v;
         }

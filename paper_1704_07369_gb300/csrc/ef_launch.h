@@ -69,6 +69,10 @@ EF_DECLARE_FEAT(f32)
 EF_DECLARE_FEAT(f64)
 #undef EF_DECLARE_FEAT
 
+// out = a x + b y over n values (ef_step.cu); prec 0 = FP32, 1 = FP64
+cudaError_t axpby_launch(int prec, void *out, const void *x, const void *y, double a, double b, int64_t n,
+                         cudaStream_t s);
+
 // moments / entropy (ef_moments.cu)
 cudaError_t moments_launch(int prec, int d, const void *F, const void *Q, const int64_t *cell_off,
                            const int64_t *cell_N, int64_t ncells, int N_uniform, double twoL, double *out,

@@ -285,6 +285,9 @@ struct ef_plan_s {
     double g_dt = 0.0;
     double *g_diag = nullptr;
     cudaStream_t g_stream = nullptr;
+    // SSP-RK3 stage buffers: two batch-sized arrays, grown on demand
+    void *d_rk = nullptr;
+    size_t rk_bytes = 0;
 };
 
 namespace {
@@ -711,6 +714,7 @@ void destroy_plan(ef_plan_s *p)
     }
     cudaFree(p->d_all_off);
     cudaFree(p->d_all_N);
+    cudaFree(p->d_rk);
     cudaFree(p->d_status);
     cudaFree(p->d_counters);
     for (cudaStream_t st : p->cstreams) cudaStreamDestroy(st);
@@ -1142,6 +1146,58 @@ ef_status ef_euler_step(ef_plan_t p, void *F, double dt, int nsteps, double *dia
         st = step(p, F, F, ncells, ef::OUT_EULER, dt, diag ? diag + (int64_t)k * ncells * ef::kDiag : nullptr,
                   (cudaStream_t)stream);
         if (st != EF_OK) return st;
+    }
+    return EF_OK;
+}
+
+ef_status ef_rk3_step(ef_plan_t p, void *F, double dt, int nsteps, double *diag, int64_t ncells, ef_stream_t stream)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (nsteps < 0 || ncells < 0) return fail(EF_ERR_INVALID_ARG, "negative nsteps or ncells");
+    if (!std::isfinite(dt)) return fail(EF_ERR_INVALID_ARG, "dt must be finite");
+    if (p->batched && ncells != p->ncells) return fail(EF_ERR_INVALID_ARG, "ncells differs from the batched plan");
+    if (nsteps == 0 || ncells == 0) return EF_OK;
+    if (!F) return fail(EF_ERR_INVALID_ARG, "null F");
+    if ((uintptr_t)F % 16) return fail(EF_ERR_INVALID_ARG, "F must be 16-byte aligned");
+    ef_status st = check_device(p);
+    if (st != EF_OK) return st;
+    const Desc &ds = p->desc;
+    int64_t total = 0;                                   // values in the batch
+    if (p->batched) {
+        for (const ClassPlan &cp : p->classes)
+            total += cp.ncells * (int64_t)cp.N * cp.N * (ds.d == 3 ? cp.N : 1);
+    } else {
+        total = ncells * (int64_t)ds.N * ds.N * (ds.d == 3 ? ds.N : 1);
+    }
+    const size_t el = ds.prec == EF_PREC_F32 ? 4 : 8;
+    const size_t half = ((size_t)total * el + 255) / 256 * 256;
+    if (2 * half > p->rk_bytes) {
+        cudaError_t e = cudaDeviceSynchronize();          // the old buffers may still be in use
+        if (e == cudaSuccess && p->d_rk) e = cudaFree(p->d_rk);
+        p->d_rk = nullptr;
+        p->rk_bytes = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_rk, 2 * half);
+        if (e != cudaSuccess) return cuda_fail(e, "RK3 stage buffers");
+        p->rk_bytes = 2 * half;
+    }
+    void *A = p->d_rk, *B = static_cast<unsigned char *>(p->d_rk) + half;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int prec = ds.prec == EF_PREC_F32 ? 0 : 1;
+    for (int k = 0; k < nsteps; ++k) {
+        double *dk = diag ? diag + (int64_t)k * ncells * ef::kDiag : nullptr;
+        // F1 = F + dt Q[F]
+        st = run(p, F, A, ncells, ef::OUT_EULER, dt, dk, s);
+        if (st != EF_OK) return st;
+        // F2 = 3/4 F + 1/4 (F1 + dt Q[F1])
+        st = run(p, A, B, ncells, ef::OUT_EULER, dt, nullptr, s);
+        if (st != EF_OK) return st;
+        cudaError_t e = ef::axpby_launch(prec, B, F, B, 0.75, 0.25, total, s);
+        if (e != cudaSuccess) return cuda_fail(e, "RK3 combine");
+        // F <- 1/3 F + 2/3 (F2 + dt Q[F2])
+        st = run(p, B, A, ncells, ef::OUT_EULER, dt, nullptr, s);
+        if (st != EF_OK) return st;
+        e = ef::axpby_launch(prec, F, F, A, 1.0 / 3.0, 2.0 / 3.0, total, s);
+        if (e != cudaSuccess) return cuda_fail(e, "RK3 combine");
     }
     return EF_OK;
 }

@@ -370,3 +370,12 @@ def test_moments_kernel_against_oracle():
             tol = 1e-12 if prec == ef.EF_PREC_F64 else 1e-5
             for kg, kr in zip(k_gpu, range(len(ref))):
                 assert abs(o[i, kg] - ref[kr]) <= tol * max(1.0, abs(ref[kr])), (d, kg)
+            assert abs(o[i, 8] - oracle.positivity_error(Fi)) <= 1e-15
+        # positivity error of Sec. 4.2 on cells with negative values
+        Fn = F - 0.02 * F.amax()
+        plan.moments(Fn, None, out, ncells=2)
+        torch.cuda.synchronize()
+        for i in range(2):
+            eps = oracle.positivity_error(Fn[i].double().cpu().numpy())
+            assert eps > 1e-3
+            assert abs(out[i, 8].item() - eps) <= (1e-12 if prec == ef.EF_PREC_F64 else 1e-5) * eps, (d, N)
