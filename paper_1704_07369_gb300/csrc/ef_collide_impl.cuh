@@ -673,8 +673,8 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
 
 // One CTA per cell: moments / entropy of F (and entropy production with Q), FP64 across the cell;
 // slot 8 holds the positivity error of Sec. 4.2 (the negative part of F, accumulated directly).
-// A warp walks rows (lanes along the contiguous axis, coalesced); each lane sums its values in T
-// over a run of at most 16 rows (at most 32 terms) and folds the run into FP64 accumulators, the
+// A warp walks rows (lanes along the contiguous axis, coalesced), four rows in flight; each lane
+// sums its values in T over runs of at most 32 terms and folds each run into FP64 accumulators, the
 // same split as the fused diagnostics of the collide kernel (no per-point FP64 work: the FP64 pipe
 // is a small fraction of the FP32 one).
 template <typename T, int D>
@@ -683,7 +683,6 @@ __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, co
                                                       double h_uniform_times_N, double *out)
 {
     __shared__ double red[8][kDiag];
-    constexpr int kRun = 16;
     T big;
     if constexpr (sizeof(T) == 4) big = T(3.0e38f);
     else big = T(1.0e300);
@@ -697,30 +696,52 @@ __global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, co
         for (int k = 0; k < kDiag; ++k) s[k] = 0.0;
         T mn = big, mq = big;
         T p0 = 0, pz = 0, py = 0, px = 0, pe = 0, peta = 0, pprod = 0, pneg = 0;
+        // four rows per warp in flight: their loads are issued before any of them is used
+        constexpr int U = 4;
+        const int per_row = (N + 31) / 32;                 // values per lane and row (N <= 64)
+        const int run_len = 32 / (U * per_row);            // iterations per FP64 fold: <= 32 terms
         int run = 0;
-        for (int r = warp; r < nrows; r += nw) {
-            const T jz = (D == 3) ? T(r / N - N / 2) : T(0);
-            const T jy = (D == 3) ? T(r % N - N / 2) : T(r - N / 2);
-            const T *Fr = F + coff + (int64_t)r * N;
-            const T *Qr = Q ? Q + coff + (int64_t)r * N : nullptr;
-            for (int x = lane; x < N; x += 32) {
-                const T f = Fr[x];
-                const T jx = T(x - N / 2);
-                p0 += f;
-                pz += f * jz;
-                py += f * jy;
-                px += f * jx;
-                pe += f * (jx * jx + jy * jy + jz * jz);
-                if (f > T(0)) {
-                    const T lf = log_t<T>(f);
-                    peta += f * lf;
-                    if (Qr) pprod += Qr[x] * lf;
+        for (int r0 = warp; r0 < nrows; r0 += U * nw) {
+            T fv[U][2], qv[U][2];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + u * nw;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int x = lane + 32 * e;
+                    const bool ok = r < nrows && x < N;
+                    fv[u][e] = ok ? F[coff + (int64_t)r * N + x] : T(0);
+                    qv[u][e] = (ok && Q) ? Q[coff + (int64_t)r * N + x] : T(0);
                 }
-                mn = f < mn ? f : mn;
-                pneg += f < T(0) ? -f : T(0);
-                if (Qr) mq = Qr[x] < mq ? Qr[x] : mq;
             }
-            if (++run == kRun || r + nw >= nrows) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int r = r0 + u * nw;
+                if (r >= nrows) break;                      // uniform across the warp
+                const T jz = (D == 3) ? T(r / N - N / 2) : T(0);
+                const T jy = (D == 3) ? T(r % N - N / 2) : T(r - N / 2);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int x = lane + 32 * e;
+                    if (x >= N) continue;
+                    const T f = fv[u][e];
+                    const T jx = T(x - N / 2);
+                    p0 += f;
+                    pz += f * jz;
+                    py += f * jy;
+                    px += f * jx;
+                    pe += f * (jx * jx + jy * jy + jz * jz);
+                    if (f > T(0)) {
+                        const T lf = log_t<T>(f);
+                        peta += f * lf;
+                        if (Q) pprod += qv[u][e] * lf;
+                    }
+                    mn = f < mn ? f : mn;
+                    pneg += f < T(0) ? -f : T(0);
+                    if (Q) mq = qv[u][e] < mq ? qv[u][e] : mq;
+                }
+            }
+            if (++run >= run_len || r0 + U * nw >= nrows) {
                 s[0] += (double)p0;
                 if (D == 3) {
                     s[1] += (double)pz;

@@ -40,7 +40,7 @@ constexpr int feat_pz()
 
 template <typename T, int D, int N>
 struct FeatLayout {
-    static constexpr int PZ = (D == 3) ? feat_pz<N, sizeof(T) == 4 ? 16 : 4>() : 1;
+    static constexpr int PZ = (D == 3) ? feat_pz<N, sizeof(T) == 4 ? 8 : 4>() : 1;
     static constexpr int NZ = (D == 3) ? N : 1;
     static constexpr int X1_PLANE = N * kFeatKx + 1;         // odd complex stride per plane
     static constexpr int X1_FIELD = PZ * X1_PLANE;
@@ -83,9 +83,11 @@ __device__ __forceinline__ void feat_load_row(const T *src, T (&x)[N])
     }
 }
 
-// row sums of one row (T), folded into the FP64 accumulators
+// row sums of one row (T), folded into the FP64 accumulators; the entropy term only with eta
+// (otherwise the ln F pass adds it, from the logarithms it computes anyway)
 template <typename T, int D, int N>
-__device__ __forceinline__ void feat_row_moments(const T (&x)[N], int jz, int jy, double (&s)[EF_DIAG_STRIDE], T &mn)
+__device__ __forceinline__ void feat_row_moments(const T (&x)[N], int jz, int jy, double (&s)[EF_DIAG_STRIDE], T &mn,
+                                                 bool eta)
 {
     T p0 = 0, px = 0, pe = 0, peta = 0;
 #pragma unroll
@@ -95,7 +97,7 @@ __device__ __forceinline__ void feat_row_moments(const T (&x)[N], int jz, int jy
         p0 += f;
         px += f * jx;
         pe += f * jx * jx;
-        if (f > T(0)) peta += f * feat_log<T>(f);
+        if (eta && f > T(0)) peta += f * feat_log<T>(f);
         mn = f < mn ? f : mn;
     }
     const double m = (double)p0;
@@ -133,8 +135,14 @@ __device__ __forceinline__ void r2c_low(const T (&x)[N], C2<T> (&X)[KX], const C
     }
 }
 
+// CTAs of 4 warps, several per SM (cells in flight overlap their barrier phases): 168 registers
+// for N <= 32 (3 CTAs per SM), 255 above (2 per SM)
+constexpr int kFeatThreads = 128;
+template <int N>
+constexpr int feat_min_blocks() { return N <= 32 ? 3 : 2; }
+
 template <typename T, int D, int N>
-__global__ void __launch_bounds__(256) features_kernel(const FeatArgs a)
+__global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_kernel(const FeatArgs a)
 {
     using Lay = FeatLayout<T, D, N>;
     constexpr int PZ = Lay::PZ, NZ = Lay::NZ;
@@ -176,10 +184,16 @@ __global__ void __launch_bounds__(256) features_kernel(const FeatArgs a)
                     T x[N];
                     feat_load_row<T, N>(src, x);
                     if (f == 0 && a.mom)
-                        feat_row_moments<T, D, N>(x, (D == 3) ? z0 + zl - N / 2 : 0, y - N / 2, s, mn);
+                        feat_row_moments<T, D, N>(x, (D == 3) ? z0 + zl - N / 2 : 0, y - N / 2, s, mn, nf == 1);
                     if (f == 1 || a.log_input) {
+                        T peta = 0;
 #pragma unroll
-                        for (int n = 0; n < N; ++n) x[n] = feat_log<T>(x[n]);
+                        for (int n = 0; n < N; ++n) {
+                            const T lf = feat_log<T>(x[n]);
+                            if (f == 1 && x[n] > T(0)) peta += x[n] * lf;
+                            x[n] = lf;
+                        }
+                        if (f == 1 && a.mom) s[5] += (double)peta;
                     }
                     C2<T> X[kFeatKx];
                     r2c_low<N, kFeatKx, T>(x, X, tw);

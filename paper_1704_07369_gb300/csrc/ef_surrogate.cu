@@ -140,15 +140,39 @@ __global__ void rowweight_norm_kernel(int64_t n, float *rw)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) rw[i] *= scale;
 }
 
-__global__ void standardize_kernel(float *X, float *Y, int64_t n, int nin, int nf, const float *mu, const float *sd,
-                                   const float *nu, const float *td)
+// prep_kernel followed by the standardisation (x - mu) / s, (y - nu) / t in one pass: one warp per
+// cell, lanes over modes
+__global__ void normalize_kernel(const float *featF, const float *featQ, const double *mom, const int *kvec, int64_t n,
+                                 int nmodes, int idx0, float pi_over_L, int extra, int d, const float *mu,
+                                 const float *sd, const float *nu, const float *td, float *X, float *Y)
 {
-    const int64_t total = n * nin;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / nin;
-        const int j = (int)(q % nin);
-        X[i * kStride + j] = (X[i * kStride + j] - mu[j]) / sd[j];
-        if (Y && j < nf) Y[i * kStride + j] = (Y[i * kStride + j] - nu[j]) / td[j];
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const double *mi = mom + i * EF_DIAG_STRIDE;
+    const float ux = (float)(mi[1] / mi[0]), uy = (float)(mi[2] / mi[0]), uz = (float)(mi[3] / mi[0]);
+    const float m = featF[i * kStride + 2 * idx0];
+    for (int j = lane; j < nmodes; j += 32) {
+        const float ph = pi_over_L * (kvec[3 * j] * ux + kvec[3 * j + 1] * uy + kvec[3 * j + 2] * uz);
+        float sn, cs;
+        sincosf(ph, &sn, &cs);
+        const float fr = featF[i * kStride + 2 * j], fi = featF[i * kStride + 2 * j + 1];
+        X[i * kStride + 2 * j] = ((fr * cs - fi * sn) / m - mu[2 * j]) / sd[2 * j];
+        X[i * kStride + 2 * j + 1] = ((fr * sn + fi * cs) / m - mu[2 * j + 1]) / sd[2 * j + 1];
+        if (featQ && Y) {
+            const float qr = featQ[i * kStride + 2 * j], qi = featQ[i * kStride + 2 * j + 1];
+            Y[i * kStride + 2 * j] = ((qr * cs - qi * sn) / (m * m) - nu[2 * j]) / td[2 * j];
+            Y[i * kStride + 2 * j + 1] = ((qr * sn + qi * cs) / (m * m) - nu[2 * j + 1]) / td[2 * j + 1];
+        }
+    }
+    if (extra && lane == 0) {
+        const double rho = mi[0];
+        const double u2 = (mi[1] * mi[1] + mi[2] * mi[2] + mi[3] * mi[3]) / (rho * rho);
+        const double theta = (2.0 * mi[4] / rho - u2) / d;
+        const double kl = mi[5] / rho - log(rho) + 0.5 * d * (log(2.0 * 3.14159265358979323846 * theta) + 1.0);
+        const int j = 2 * nmodes;
+        X[i * kStride + j] = ((float)theta - mu[j]) / sd[j];
+        X[i * kStride + j + 1] = ((float)kl - mu[j + 1]) / sd[j + 1];
     }
 }
 
@@ -435,10 +459,9 @@ ef_status ef_surrogate_normalize(ef_surrogate_t s, const float *featF, const flo
     cudaStream_t st = (cudaStream_t)stream;
     const int nm = s->nf / 2;
     const bool withY = featQ && Y;
-    prep_kernel<<<sgrid(n * nm), 256, 0, st>>>(featF, withY ? featQ : nullptr, mom, s->kvec, n, nm, s->idx0, s->pi_over_L,
-                                               s->nin > s->nf, s->d, X, withY ? Y : nullptr);
-    standardize_kernel<<<sgrid(n * s->nin), 256, 0, st>>>(X, withY ? Y : nullptr, n, s->nin, s->nf, s->mu, s->sd, s->nu,
-                                                          s->td);
+    normalize_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(featF, withY ? featQ : nullptr, mom, s->kvec, n, nm, s->idx0,
+                                                              s->pi_over_L, s->nin > s->nf, s->d, s->mu, s->sd, s->nu,
+                                                              s->td, X, withY ? Y : nullptr);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? EF_OK : scuda(e, "normalise");
 }
