@@ -249,6 +249,28 @@ ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat
 ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_dev, double *out_dev,
                              int64_t ncells, ef_stream_t stream);
 
+/* Streaming a batch that lives in host memory (no counterpart in the paper; the paper's method
+ * is per cell).  The cells (sizes N_host[c], back to back as for ef_plan_create_batched) are cut
+ * into nchunks contiguous chunks of about equal work, each with its own batched plan and CUDA
+ * stream, and a device copy of the whole batch is allocated here.  ef_stream_euler_step uploads
+ * each chunk, runs nsteps Euler steps on it (ef_euler_step) and downloads it, in place in F_host;
+ * chunks run concurrently, so copies in both directions overlap the collision steps of other
+ * chunks when F_host is page-locked (pageable memory works but serialises the copies).  diag_host
+ * (nullable) receives nsteps * ncells * EF_DIAG_STRIDE doubles, [step][cell][k] as ef_euler_step
+ * (a device buffer for them is allocated on the first call that needs it).  All work is ordered
+ * after earlier work on `stream`, and later work on `stream` waits for it; the host buffers must
+ * stay untouched until then. */
+typedef struct ef_stream_plan_s *ef_stream_plan_t;
+ef_status ef_stream_plan_create(int d, int64_t ncells, const int *N_host, double L, ef_kernel kernel, int R,
+                                ef_precision prec, int nchunks, ef_stream_plan_t *out);
+ef_status ef_stream_plan_destroy(ef_stream_plan_t sp);
+/* info: [0] cells, [1] chunks, [2] values in the batch, [3] bytes per value. */
+ef_status ef_stream_plan_info(ef_stream_plan_t sp, int64_t info[4]);
+ef_status ef_stream_euler_step(ef_stream_plan_t sp, void *F_host, double dt, int nsteps, double *diag_host,
+                               ef_stream_t stream);
+/* First non-OK device status word of the chunk plans (as ef_plan_status). */
+ef_status ef_stream_plan_status(ef_stream_plan_t sp, int sync, int reset);
+
 /* Read the plan's device status word (the first error seen by a kernel, EF_OK if none).  With
  * sync = 1 the call first synchronises the plan's device; with sync = 0 it returns the value
  * copied back by the last synchronising call.  reset = 1 clears the word after reading. */

@@ -40,7 +40,8 @@ SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
            "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer",
-           "ef_status_string", "ef_last_error")
+           "ef_stream_plan_create", "ef_stream_plan_destroy", "ef_stream_plan_info", "ef_stream_euler_step",
+           "ef_stream_plan_status", "ef_status_string", "ef_last_error")
 EF_FEATURE_K = 6
 EF_FEATURE_STRIDE = 928
 
@@ -98,6 +99,11 @@ def lib():
         L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
         L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
         L.ef_rk3_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
+        L.ef_stream_plan_create.argtypes = [i32, i64, vp, dbl, i32, i32, i32, i32, ctypes.POINTER(vp)]
+        L.ef_stream_plan_destroy.argtypes = [vp]
+        L.ef_stream_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+        L.ef_stream_euler_step.argtypes = [vp, vp, dbl, i32, vp, vp]
+        L.ef_stream_plan_status.argtypes = [vp, i32, i32]
         L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
         L.ef_plan_status.argtypes = [vp, i32, i32]
         L.ef_plan_set_graph.argtypes = [vp, i32]
@@ -282,6 +288,42 @@ def ef_euler_step(plan, F, dt, nsteps, diag, ncells, stream=None):
 
 def ef_rk3_step(plan, F, dt, nsteps, diag, ncells, stream=None):
     _check(lib().ef_rk3_step(plan, _ptr(F), float(dt), int(nsteps), _ptr(diag), int(ncells), _stream(stream)))
+
+
+class StreamPlan:
+    """Owning wrapper of an ``ef_stream_plan_t``: a host-resident batch streamed through the GPU in
+    ``nchunks`` concurrent chunks (uploads, collision steps and downloads overlap)."""
+
+    def __init__(self, d, N_list, L, kernel, R, prec, nchunks=8):
+        arr = (ctypes.c_int * len(N_list))(*[int(n) for n in N_list])
+        self.handle = ctypes.c_void_p()
+        _check(lib().ef_stream_plan_create(d, len(N_list), arr, float(L), kernel, R, prec, int(nchunks),
+                                           ctypes.byref(self.handle)))
+        self.ncells = len(N_list)
+
+    def info(self):
+        out = (ctypes.c_int64 * 4)()
+        _check(lib().ef_stream_plan_info(self.handle, out))
+        return {"cells": out[0], "chunks": out[1], "values": out[2], "bytes_per_value": out[3]}
+
+    def euler(self, F_host, dt, nsteps=1, diag_host=None, stream=None):
+        """F_host: a (preferably pinned) CPU tensor of the whole batch, updated in place."""
+        _check(lib().ef_stream_euler_step(self.handle, _ptr(F_host), float(dt), int(nsteps), _ptr(diag_host),
+                                          _stream(stream)))
+
+    def status(self, sync=1, reset=0):
+        return lib().ef_stream_plan_status(self.handle, int(sync), int(reset))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ef_stream_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ef_moments_entropy(plan, F, Q, out, ncells, stream=None):

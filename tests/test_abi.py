@@ -38,6 +38,15 @@ def test_host_side_argument_checks():
     assert lib.ef_collide(None, None, None, 1, None) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_plan_destroy(None) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_status_string(ef.EF_ERR_POSITIVITY) == b"EF_ERR_POSITIVITY"
+    Ns = (ctypes.c_int * 3)(24, 32, 24)
+    sp = ctypes.c_void_p()
+    assert lib.ef_stream_plan_create(3, 3, Ns, 8.0, 1, 32, 0, 0, ctypes.byref(sp)) == ef.EF_ERR_INVALID_ARG
+    assert b"nchunks" in lib.ef_last_error()
+    assert lib.ef_stream_plan_create(3, 0, Ns, 8.0, 1, 32, 0, 2, ctypes.byref(sp)) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_stream_plan_create(3, 3, Ns, 8.0, 1, 32, 0, 2, None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_stream_plan_destroy(None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_stream_euler_step(None, None, 0.01, 1, None, None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_rk3_step(None, None, 0.01, 1, None, 1, None) == ef.EF_ERR_INVALID_ARG
 
 
 def test_oracle_is_not_on_the_product_path():
