@@ -123,3 +123,27 @@ def test_rk3_fp32_tracks_fp64():
         torch.cuda.synchronize()
         out[prec] = F[0].double().cpu().numpy()
     assert np.abs(out[ef.EF_PREC_F32] - out[ef.EF_PREC_F64]).max() <= 1e-5 * np.abs(out[ef.EF_PREC_F64]).max()
+
+
+def test_positivity_error_efm_zero_fcm_positive():
+    """The contrast of Fig. 2 (Example 1): on the 2D BKW problem EFM keeps the positivity error of
+    Sec. 4.2 at exactly zero, while the same collocation method without the filter (FCM, sigma = 1)
+    produces negative values; the unfiltered GPU path matches the oracle's."""
+    N, M, dt, steps = 32, 32, 0.05, 10
+    F0 = inputs.bkw(2, N, T_PAPER, 0.0)
+    eps = {}
+    for filt in (1, 0):
+        plan = ef.Plan(2, N, T_PAPER, ef.EF_KERNEL_MAXWELL, 2 * M, ef.EF_PREC_F64, R_tr=6.0, sigma_enabled=filt)
+        F = torch.tensor(F0[None], dtype=torch.float64, device="cuda")
+        plan.rk3(F, dt, nsteps=steps, ncells=1)
+        mom = torch.zeros(1, ef.EF_DIAG_STRIDE, dtype=torch.float64, device="cuda")
+        plan.moments(F, None, mom, ncells=1)
+        torch.cuda.synchronize()
+        eps[filt] = mom[0, 8].item()
+        if not filt:
+            p = oracle.Params(d=2, N=N, T=T_PAPER, kernel=oracle.KERNEL_MAXWELL, R=2 * M, Rtr=6.0, filter=False)
+            ref = oracle.ssp_rk3(p, F0, dt, steps=steps)
+            assert _rel_l2(F[0].cpu().numpy(), ref) <= 1e-12
+            assert abs(eps[0] - oracle.positivity_error(ref)) <= 1e-12
+    assert eps[1] == 0.0
+    assert eps[0] > 1e-6
