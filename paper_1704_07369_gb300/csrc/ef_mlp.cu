@@ -3,8 +3,8 @@
 //
 // Layer l: pre_l = A_{l-1} W_l^T + b_l, A_l = relu(pre_l) (no activation on the last layer).
 // Every product is one "TN" GEMM C[M,N] = A[M,K] B[N,K]^T with both operands K-contiguous bf16
-// and an FP32 accumulator, on the tensor cores (mma.sync m16n8k16 bf16), 64 x 64 block tiles,
-// cp.async double buffering and ldmatrix fragment loads.  Backward products use the transposed
+// and an FP32 accumulator on the tensor cores: tcgen05.mma with the accumulator in tensor memory
+// for the shapes it tiles (M a multiple of 128), else mma.sync m16n8k16 with 64 x 64 tiles.  Backward products use the transposed
 // copies the forward pass and the optimizer write alongside (activations^T, W^T).
 // Split precision: every layer input a (the features and each hidden activation) is stored as two
 // bf16 halves, hi = bf16(a) and lo = bf16(a - hi), side by side, and multiplied against the weights
@@ -34,6 +34,10 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16_u32(uint32_t smem_addr, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
@@ -176,8 +180,206 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const GemmArgs g)
             }
 }
 
+// ------------------------------------------------------------ tcgen05 GEMM ---------------
+// The same product and epilogue on the 5th-generation tensor cores: one CTA of 4 warps per
+// 128 x TN tile of C, K in blocks of 64, a TS-stage ring of shared-memory operand tiles filled by
+// cp.async in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix:
+// element (row, k) at ((row/8)*8 + k/8)*128 + (row%8)*16 + (k%8)*2 bytes of a tile), the
+// accumulator in tensor memory.  Thread 0 issues tcgen05.mma (M = 128, N = TN, K = 16) and commits
+// each K block to that stage's mbarrier; a stage is refilled once the MMAs that read it are
+// complete, after the next block's MMAs have been queued.  The epilogue reads the accumulator with
+// tcgen05.ld (warp w owns tensor-memory lanes, i.e. rows, 32w .. 32w+31).  Every mbarrier wait is
+// bounded; a wait that gives up makes the tile's outputs NaN instead of hanging.
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 3;
+
+__device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr)
+{
+    // start address, leading byte offset 128 (the next core matrix along K), stride byte offset
+    // 1024 (the next 8-row group), descriptor version 1, no swizzle
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both K-major
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int TN>
+__global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GemmArgs g)
+{
+    constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = TN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
+    constexpr int TCOLS = TN <= 64 ? 64 : (TN <= 128 ? 128 : 256);     // tensor-memory columns
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TN;
+    const int nk = g.K / TC_BK;
+    const uint32_t sbase = smem_u32(tc_smem);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < TC_STAGES; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[i])));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const uint32_t tmem = tmem_base;
+
+    auto load = [&](int kb, int buf) {
+        const uint32_t a0 = sbase + buf * STAGE, b0 = a0 + A_BYTES;
+        for (int c = tid; c < TC_BM * TC_BK / 8; c += 128) {
+            const int row = c >> 3, kc = c & 7;
+            cp_async16_u32(a0 + ((row >> 3) * 8 + kc) * 128 + (row & 7) * 16,
+                           g.A + (size_t)(m0 + row) * g.lda + kb * TC_BK + kc * 8);
+        }
+        for (int c = tid; c < TN * TC_BK / 8; c += 128) {
+            const int row = c >> 3, kc = c & 7;
+            cp_async16_u32(b0 + ((row >> 3) * 8 + kc) * 128 + (row & 7) * 16,
+                           g.B + (size_t)(n0 + row) * g.ldb + kb * TC_BK + kc * 8);
+        }
+    };
+
+    bool ok = true;
+    uint32_t phase[TC_STAGES];
+    for (int i = 0; i < TC_STAGES; ++i) {
+        phase[i] = 0;
+        if (i < nk) load(i, i);
+        cp_async_commit();
+    }
+    for (int kb = 0; kb < nk; ++kb) {
+        const int buf = kb % TC_STAGES;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 1));
+        asm volatile("fence.proxy.async.shared::cta;\n" ::);
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+            const uint32_t a0 = sbase + buf * STAGE, b0 = a0 + A_BYTES;
+#pragma unroll
+            for (int k16 = 0; k16 < TC_BK / 16; ++k16) {
+                const uint64_t ad = tc_sdesc(a0 + k16 * 256), bd = tc_sdesc(b0 + k16 * 256);
+                const uint32_t acc = (kb > 0 || k16 > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(tmem), "l"(ad), "l"(bd), "r"(tc_idesc(TC_BM, TN)), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                         ::"r"(smem_u32(&mbar[buf])));
+        }
+        const int nxt = kb - 1 + TC_STAGES;          // refill the stage of kb - 1
+        if (kb >= 1 && nxt < nk) {
+            const int pb = (kb - 1) % TC_STAGES;
+            ok = ok && tc_wait(smem_u32(&mbar[pb]), phase[pb]);
+            phase[pb] ^= 1;
+            load(nxt, pb);
+        }
+        cp_async_commit();
+    }
+    {
+        const int last = (nk - 1) % TC_STAGES;
+        ok = ok && tc_wait(smem_u32(&mbar[last]), phase[last]);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+
+    const int row = m0 + warp * 32 + lane;
+    const float bad = __int_as_float(0x7fc00000);
+#pragma unroll 1
+    for (int c0 = 0; c0 < TN; c0 += 8) {
+        uint32_t r[8];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+        const int col = n0 + c0;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = ok ? __uint_as_float(r[j]) : bad;
+            if (g.bias) v[j] += g.bias[col + j];
+        }
+        if (g.Cf) {
+            float4 *d = reinterpret_cast<float4 *>(g.Cf + (size_t)row * g.ldcf + col);
+            d[0] = make_float4(v[0], v[1], v[2], v[3]);
+            d[1] = make_float4(v[4], v[5], v[6], v[7]);
+        }
+        if (g.relu) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = fmaxf(v[j], 0.f);
+        }
+        bf16 hi[8], lo[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            hi[j] = __float2bfloat16(v[j]);
+            lo[j] = __float2bfloat16(v[j] - __bfloat162float(hi[j]));
+        }
+        if (g.Cb) {
+            *reinterpret_cast<uint4 *>(g.Cb + (size_t)row * g.ldcb + col) = *reinterpret_cast<const uint4 *>(hi);
+            if (g.lo_off)
+                *reinterpret_cast<uint4 *>(g.Cb + (size_t)row * g.ldcb + g.lo_off + col) = *reinterpret_cast<const uint4 *>(lo);
+        }
+        if (g.CbT) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                g.CbT[(size_t)(col + j) * g.ldcbt + row] = hi[j];
+                if (g.lo_off) g.CbT[(size_t)(g.lo_off + col + j) * g.ldcbt + row] = lo[j];
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
+}
+
+template <int TN>
+cudaError_t gemm_tc(const GemmArgs &g, cudaStream_t s)
+{
+    constexpr size_t smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + TN * TC_BK * 2);
+    static unsigned long long set_on = 0;    // devices on which the attribute has been raised
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(__atomic_load_n(&set_on, __ATOMIC_ACQUIRE) & bit)) {
+        e = cudaFuncSetAttribute(gemm_tc_kernel<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        __atomic_fetch_or(&set_on, bit, __ATOMIC_ACQ_REL);
+    }
+    dim3 grid(g.N / TN, g.M / TC_BM);
+    gemm_tc_kernel<TN><<<grid, 128, smem, s>>>(g);
+    return cudaGetLastError();
+}
+
+// tcgen05 for the shapes it tiles (M multiple of 128, K of 64, N of 64, 16-byte aligned rows), the
+// mma.sync kernel for the rest
 cudaError_t gemm(const GemmArgs &g, cudaStream_t s)
 {
+    const bool aligned = g.lda % 8 == 0 && g.ldb % 8 == 0 && (!g.Cf || g.ldcf % 4 == 0) && (!g.Cb || g.ldcb % 8 == 0) &&
+                         g.lo_off % 8 == 0;
+    if (g.M % TC_BM == 0 && g.K % TC_BK == 0 && aligned) {
+        if (g.N % 256 == 0) return gemm_tc<256>(g, s);
+        if (g.N % 192 == 0) return gemm_tc<192>(g, s);
+        if (g.N % 128 == 0) return gemm_tc<128>(g, s);
+        if (g.N % 64 == 0) return gemm_tc<64>(g, s);
+    }
     if (g.M % BM || g.N % BN || g.K % BK) return cudaErrorInvalidValue;
     dim3 grid(g.N / BN, g.M / BM);
     gemm_tn_kernel<<<grid, 128, 0, s>>>(g);
