@@ -3,15 +3,20 @@
 //
 // Layer l: pre_l = A_{l-1} W_l^T + b_l, A_l = relu(pre_l) (no activation on the last layer).
 // Every product is one "TN" GEMM C[M,N] = A[M,K] B[N,K]^T with both operands K-contiguous bf16
-// and an FP32 accumulator on the tensor cores: tcgen05.mma with the accumulator in tensor memory
-// for the shapes it tiles (M a multiple of 128), else mma.sync m16n8k16 with 64 x 64 tiles.  Backward products use the transposed
+// and an FP32 accumulator on the tensor cores: tcgen05.mma fed by TMA, with the accumulator in
+// tensor memory, for the shapes it tiles (M a multiple of 128), else mma.sync m16n8k16 with 64 x 64
+// tiles.  Backward products use the transposed
 // copies the forward pass and the optimizer write alongside (activations^T, W^T).
 // Split precision: every layer input a (the features and each hidden activation) is stored as two
 // bf16 halves, hi = bf16(a) and lo = bf16(a - hi), side by side, and multiplied against the weights
 // duplicated [bf16(W) | bf16(W)], so that a forward product sees a to about 16 mantissa bits while
 // both tensor-core operands stay bf16.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include <cmath>
 #include <cstdint>
@@ -34,10 +39,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async16_u32(uint32_t smem_addr, const void *gmem)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::); }
@@ -182,22 +183,22 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const GemmArgs g)
 
 // ------------------------------------------------------------ tcgen05 GEMM ---------------
 // The same product and epilogue on the 5th-generation tensor cores: one CTA of 4 warps per
-// 128 x TN tile of C, K in blocks of 64, a TS-stage ring of shared-memory operand tiles filled by
-// cp.async in the no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix:
-// element (row, k) at ((row/8)*8 + k/8)*128 + (row%8)*16 + (k%8)*2 bytes of a tile), the
-// accumulator in tensor memory.  Thread 0 issues tcgen05.mma (M = 128, N = TN, K = 16) and commits
-// each K block to that stage's mbarrier; a stage is refilled once the MMAs that read it are
-// complete, after the next block's MMAs have been queued.  The epilogue reads the accumulator with
-// tcgen05.ld (warp w owns tensor-memory lanes, i.e. rows, 32w .. 32w+31).  Every mbarrier wait is
-// bounded; a wait that gives up makes the tile's outputs NaN instead of hanging.
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 3;
+// 128 x TN tile of C, K in blocks of 64.  Thread 0 runs the pipeline: TMA loads (128-byte
+// swizzle) of the A and B tiles of a K block into one of TC_STAGES shared-memory stages, each
+// stage with a "full" mbarrier (TMA bytes arrived) and an "empty" one (its MMAs done, committed by
+// tcgen05.commit); tcgen05.mma kind::f16 (M = 128, N = TN, K = 16) accumulates in tensor memory;
+// a stage is refilled once the MMAs that read it are complete, after the next block's MMAs have
+// been queued.  The epilogue reads the accumulator with tcgen05.ld (warp w owns tensor-memory
+// lanes, i.e. rows, 32w .. 32w+31).  Every mbarrier wait is bounded; a wait that gives up makes
+// the tile's outputs NaN instead of hanging.
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
 
 __device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr)
 {
-    // start address, leading byte offset 128 (the next core matrix along K), stride byte offset
-    // 1024 (the next 8-row group), descriptor version 1, no swizzle
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46);
+    // K-major operand with 128-byte swizzle: start address, leading offset unused (1), stride 1024
+    // bytes between 8-row groups, descriptor version 1, layout type 2 (128-byte swizzle)
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
+           ((uint64_t)2 << 61);
 }
 
 // instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B, both K-major
@@ -218,12 +219,14 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity)
 }
 
 template <int TN>
-__global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GemmArgs g)
+__global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__ CUtensorMap tA,
+                                                         const __grid_constant__ CUtensorMap tB, const GemmArgs g)
 {
     constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = TN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
     constexpr int TCOLS = TN <= 64 ? 64 : (TN <= 128 ? 128 : 256);     // tensor-memory columns
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t mbar[TC_STAGES];
+    extern __shared__ __align__(1024) unsigned char tc_raw[];
+    unsigned char *tc_smem = (unsigned char *)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);   // swizzle atoms
+    __shared__ __align__(8) uint64_t full[TC_STAGES], empty[TC_STAGES];
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * TC_BM, n0 = blockIdx.x * TN;
@@ -236,68 +239,71 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GemmArgs g)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
     }
     if (tid == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[i])));
+        for (int i = 0; i < TC_STAGES; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&full[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&empty[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tA));
+        asm volatile("prefetch.tensormap [%0];\n" ::"l"(&tB));
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     const uint32_t tmem = tmem_base;
 
-    auto load = [&](int kb, int buf) {
-        const uint32_t a0 = sbase + buf * STAGE, b0 = a0 + A_BYTES;
-        for (int c = tid; c < TC_BM * TC_BK / 8; c += 128) {
-            const int row = c >> 3, kc = c & 7;
-            cp_async16_u32(a0 + ((row >> 3) * 8 + kc) * 128 + (row & 7) * 16,
-                           g.A + (size_t)(m0 + row) * g.lda + kb * TC_BK + kc * 8);
+    __shared__ int s_ok;
+    if (tid == 0) {
+        bool ok = true;
+        auto issue = [&](int kb, int st) {
+            const uint32_t a0 = sbase + st * STAGE, b0 = a0 + A_BYTES, bar = smem_u32(&full[st]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(STAGE));
+            asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+                         ::"r"(a0), "l"(&tA), "r"(kb * TC_BK), "r"(m0), "r"(bar) : "memory");
+            asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+                         ::"r"(b0), "l"(&tB), "r"(kb * TC_BK), "r"(n0), "r"(bar) : "memory");
+        };
+        uint32_t fph[TC_STAGES], eph[TC_STAGES];
+        for (int i = 0; i < TC_STAGES; ++i) {
+            fph[i] = eph[i] = 0;
+            if (i < nk) issue(i, i);
         }
-        for (int c = tid; c < TN * TC_BK / 8; c += 128) {
-            const int row = c >> 3, kc = c & 7;
-            cp_async16_u32(b0 + ((row >> 3) * 8 + kc) * 128 + (row & 7) * 16,
-                           g.B + (size_t)(n0 + row) * g.ldb + kb * TC_BK + kc * 8);
-        }
-    };
-
-    bool ok = true;
-    uint32_t phase[TC_STAGES];
-    for (int i = 0; i < TC_STAGES; ++i) {
-        phase[i] = 0;
-        if (i < nk) load(i, i);
-        cp_async_commit();
-    }
-    for (int kb = 0; kb < nk; ++kb) {
-        const int buf = kb % TC_STAGES;
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(TC_STAGES - 1));
-        asm volatile("fence.proxy.async.shared::cta;\n" ::);
-        __syncthreads();
-        if (tid == 0) {
+        for (int kb = 0; kb < nk && ok; ++kb) {
+            const int st = kb % TC_STAGES;
+            ok = tc_wait(smem_u32(&full[st]), fph[st]);
+            fph[st] ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-            const uint32_t a0 = sbase + buf * STAGE, b0 = a0 + A_BYTES;
+            const uint32_t a0 = sbase + st * STAGE, b0 = a0 + A_BYTES;
 #pragma unroll
             for (int k16 = 0; k16 < TC_BK / 16; ++k16) {
-                const uint64_t ad = tc_sdesc(a0 + k16 * 256), bd = tc_sdesc(b0 + k16 * 256);
+                const uint64_t ad = tc_sdesc(a0 + k16 * 32), bd = tc_sdesc(b0 + k16 * 32);
                 const uint32_t acc = (kb > 0 || k16 > 0) ? 1u : 0u;
                 asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
                              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                              ::"r"(tmem), "l"(ad), "l"(bd), "r"(tc_idesc(TC_BM, TN)), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                         ::"r"(smem_u32(&mbar[buf])));
+                         ::"r"(smem_u32(&empty[st])));
+            const int nxt = kb - 1 + TC_STAGES;          // refill the stage of kb - 1
+            if (kb >= 1 && nxt < nk) {
+                const int pb = (kb - 1) % TC_STAGES;
+                ok = ok && tc_wait(smem_u32(&empty[pb]), eph[pb]);
+                eph[pb] ^= 1;
+                issue(nxt, pb);
+            }
         }
-        const int nxt = kb - 1 + TC_STAGES;          // refill the stage of kb - 1
-        if (kb >= 1 && nxt < nk) {
-            const int pb = (kb - 1) % TC_STAGES;
-            ok = ok && tc_wait(smem_u32(&mbar[pb]), phase[pb]);
-            phase[pb] ^= 1;
-            load(nxt, pb);
+        if (ok) {            // the last commit covers every MMA; its parity counts the earlier waits
+            const int last = (nk - 1) % TC_STAGES;
+            int waited = 0;
+            for (int kb = last; kb + TC_STAGES < nk; kb += TC_STAGES) ++waited;
+            ok = tc_wait(smem_u32(&empty[last]), (uint32_t)(waited & 1));
         }
-        cp_async_commit();
+        s_ok = ok ? 1 : 0;
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
     }
-    {
-        const int last = (nk - 1) % TC_STAGES;
-        ok = ok && tc_wait(smem_u32(&mbar[last]), phase[last]);
-    }
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    const bool ok = s_ok != 0;
 
     const int row = m0 + warp * 32 + lane;
     const float bad = __int_as_float(0x7fc00000);
@@ -349,10 +355,42 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GemmArgs g)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
 }
 
-template <int TN>
-cudaError_t gemm_tc(const GemmArgs &g, cudaStream_t s)
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against the driver)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
-    constexpr size_t smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + TN * TC_BK * 2);
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// rows x K bf16 operand with row stride ld elements, boxes of 64 K-elements x box_rows rows
+bool tile_map(CUtensorMap *m, const bf16 *base, int rows, int K, int ld, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (uintptr_t)base % 16) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TN>
+cudaError_t gemm_tc(const GemmArgs &g, bool *used, cudaStream_t s)
+{
+    constexpr size_t smem = (size_t)TC_STAGES * (TC_BM * TC_BK * 2 + TN * TC_BK * 2) + 1024;
+    *used = false;
+    CUtensorMap tA, tB;
+    if (!tile_map(&tA, g.A, g.M, g.K, g.lda, TC_BM) || !tile_map(&tB, g.B, g.N, g.K, g.ldb, TN)) return cudaSuccess;
     static unsigned long long set_on = 0;    // devices on which the attribute has been raised
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -364,21 +402,25 @@ cudaError_t gemm_tc(const GemmArgs &g, cudaStream_t s)
         __atomic_fetch_or(&set_on, bit, __ATOMIC_ACQ_REL);
     }
     dim3 grid(g.N / TN, g.M / TC_BM);
-    gemm_tc_kernel<TN><<<grid, 128, smem, s>>>(g);
+    gemm_tc_kernel<TN><<<grid, 128, smem, s>>>(tA, tB, g);
+    *used = true;
     return cudaGetLastError();
 }
 
 // tcgen05 for the shapes it tiles (M multiple of 128, K of 64, N of 64, 16-byte aligned rows), the
-// mma.sync kernel for the rest
+// mma.sync kernel for the rest (and wherever a tensor map cannot be made)
 cudaError_t gemm(const GemmArgs &g, cudaStream_t s)
 {
     const bool aligned = g.lda % 8 == 0 && g.ldb % 8 == 0 && (!g.Cf || g.ldcf % 4 == 0) && (!g.Cb || g.ldcb % 8 == 0) &&
                          g.lo_off % 8 == 0;
     if (g.M % TC_BM == 0 && g.K % TC_BK == 0 && aligned) {
-        if (g.N % 256 == 0) return gemm_tc<256>(g, s);
-        if (g.N % 192 == 0) return gemm_tc<192>(g, s);
-        if (g.N % 128 == 0) return gemm_tc<128>(g, s);
-        if (g.N % 64 == 0) return gemm_tc<64>(g, s);
+        bool used = false;
+        cudaError_t e = cudaSuccess;
+        if (g.N % 256 == 0) e = gemm_tc<256>(g, &used, s);
+        else if (g.N % 192 == 0) e = gemm_tc<192>(g, &used, s);
+        else if (g.N % 128 == 0) e = gemm_tc<128>(g, &used, s);
+        else if (g.N % 64 == 0) e = gemm_tc<64>(g, &used, s);
+        if (e != cudaSuccess || used) return e;
     }
     if (g.M % BM || g.N % BN || g.K % BK) return cudaErrorInvalidValue;
     dim3 grid(g.N / BN, g.M / BM);
