@@ -407,19 +407,30 @@ cudaError_t gemm_tc(const GemmArgs &g, bool *used, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// tcgen05 for the shapes it tiles (M multiple of 128, K of 64, N of 64, 16-byte aligned rows), the
-// mma.sync kernel for the rest (and wherever a tensor map cannot be made)
+// tcgen05 for the shapes it tiles (M multiple of 128, K of 64, N of 64, 16-byte aligned rows) with at
+// least one tile per SM, the mma.sync kernel for the rest (and wherever a tensor map cannot be made)
 cudaError_t gemm(const GemmArgs &g, cudaStream_t s)
 {
     const bool aligned = g.lda % 8 == 0 && g.ldb % 8 == 0 && (!g.Cf || g.ldcf % 4 == 0) && (!g.Cb || g.ldcb % 8 == 0) &&
                          g.lo_off % 8 == 0;
     if (g.M % TC_BM == 0 && g.K % TC_BK == 0 && aligned) {
+        // the widest N tile that still gives every SM a tile; small products (the training batch)
+        // keep the 64 x 64 kernel, whose many CTAs fill the device
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (sms <= 0) sms = 1;
+        }
+        const int64_t mt = g.M / TC_BM;
+        auto fills = [&](int tn) { return g.N % tn == 0 && mt * (g.N / tn) >= sms; };
         bool used = false;
         cudaError_t e = cudaSuccess;
-        if (g.N % 256 == 0) e = gemm_tc<256>(g, &used, s);
-        else if (g.N % 192 == 0) e = gemm_tc<192>(g, &used, s);
-        else if (g.N % 128 == 0) e = gemm_tc<128>(g, &used, s);
-        else if (g.N % 64 == 0) e = gemm_tc<64>(g, &used, s);
+        if (fills(256)) e = gemm_tc<256>(g, &used, s);
+        else if (fills(192)) e = gemm_tc<192>(g, &used, s);
+        else if (fills(128)) e = gemm_tc<128>(g, &used, s);
+        else if (fills(64)) e = gemm_tc<64>(g, &used, s);
         if (e != cudaSuccess || used) return e;
     }
     if (g.M % BM || g.N % BN || g.K % BK) return cudaErrorInvalidValue;

@@ -99,6 +99,36 @@ def test_mlp_forward_and_gradients_match_oracle():
         assert np.sqrt(((gb - db) ** 2).sum() / (db ** 2).sum()) <= 2e-3
 
 
+def test_mlp_tcgen05_shapes_match_oracle():
+    """A batch of 152 x 128 rows: the forward products and the input-gradient products then run on
+    the tcgen05 kernel (N tiles of 256 and 192); outputs, loss and gradients against the FP64
+    oracle MLP with the same bf16 roundings."""
+    rng = np.random.default_rng(8)
+    nin, nh, nl, nout, B = 900, 512, 3, 926, 152 * 128
+    net = ef.MLP(nin, nh, nl, nout, B, seed=4)
+    layers = omlp.unpack(net.params(), net.layout())
+    X = rng.normal(size=(B, nin)).astype(np.float32)
+    T = rng.normal(size=(B, nout)).astype(np.float32)
+    Xd, Td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
+    Y = torch.zeros(B, net.noutp, device="cuda")
+    net.forward(Xd, Y, B)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(net.nparams, device="cuda")
+    net.grad(Xd, Td, B, loss, grad)
+    torch.cuda.synchronize()
+    Xp = np.zeros((B, net.ninp))
+    Xp[:, :nin] = X
+    y_ref, _ = omlp.forward(layers, Xp, bf=True)
+    y = Y.cpu().numpy()
+    assert np.sqrt(((y - y_ref) ** 2).sum() / (y_ref ** 2).sum()) <= 1e-4
+    l_ref, g_ref = omlp.loss_and_grads(layers, Xp, T.astype(np.float64), nout, bf=True)
+    assert abs(loss.item() - l_ref) <= 1e-4 * l_ref
+    gh = grad.cpu().numpy()
+    for (woff, o, i, boff), (dW, db) in zip(net.layout(), g_ref):
+        gW = gh[woff:woff + o * i].reshape(o, i)
+        assert np.sqrt(((gW - dW) ** 2).sum() / (dW ** 2).sum()) <= 2e-3
+
+
 def test_mlp_training_reduces_loss():
     rng = np.random.default_rng(6)
     nin, nh, nout, B = 64, 128, 32, 256
