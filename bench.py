@@ -385,6 +385,7 @@ SUR_TOL = 1e-3
 SUR_AUDIT = 0.02
 SUR_BATCH = 512
 SUR_LR = 7e-4
+SUR_LR1 = 1e-6
 
 
 def _quantiles(e):
@@ -411,7 +412,7 @@ def surrogate_leg(args, device):
     out = {"workload": "3D BKW family (t0~U[0.5,10], rho~U[0.5,2], theta~U[0.5,2], |u|<=1), N=32, L=8, R=32, "
                        "FP32 plain operator vs bf16 MLP surrogate with gates, audit and fallback",
            "cells": SUR_CELLS, "train_cells": SUR_TRAIN, "epochs": args.sur_epochs, "batch": SUR_BATCH,
-           "lr": SUR_LR, "tol": SUR_TOL, "inputs": "926 band floats + theta + relative entropy",
+           "lr": SUR_LR, "lr_final": SUR_LR1, "tol": SUR_TOL, "inputs": "926 band floats + theta + relative entropy",
            "audit_fraction": SUR_AUDIT, "metric": "band rel-L2 per cell, modes |k|<=6", "kernels": {}}
     F = torch.empty(SUR_CELLS, SUR_N, SUR_N, SUR_N, device=device)
     Q = torch.empty_like(F)
@@ -423,7 +424,7 @@ def surrogate_leg(args, device):
         data_s = time.perf_counter() - t0
         tr = S.Trainer(plan, batch=SUR_BATCH, max_infer_batch=SUR_CELLS, seed=0)
         t0 = time.perf_counter()
-        hist = tr.fit(fF, fQ, fM, epochs=args.sur_epochs, lr0=SUR_LR, warmup=0.05)
+        hist = tr.fit(fF, fQ, fM, epochs=args.sur_epochs, lr0=SUR_LR, lr1=SUR_LR1, warmup=0.05)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
         del fF, fQ, fM

@@ -1,5 +1,5 @@
 // ef_moments.cu -- launcher of the FP64 moments / entropy reduction (ef_moments_entropy).
-#include "ef_collide_impl.cuh"
+#include "ef_moments_impl.cuh"
 #include "ef_launch.h"
 
 namespace ef {
