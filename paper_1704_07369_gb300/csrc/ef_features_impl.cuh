@@ -8,10 +8,13 @@
 //   stage 1  every row along the contiguous axis is transformed (a real row through a half-length
 //            complex FFT) and only kx = 0 .. K is kept in shared memory;
 //   stage 2  every (plane, kx) column is transformed along axis 1 and ky = -K .. K kept;
-// then, with all planes done,
-//   stage 3  every band mode sums its N axis-0 values against exp(-2 pi i kz z / N) directly.
-// 2D cells are one plane (stage 3 is the identity).  The moments fold each row's sums (in T) into
-// FP64, like the fused diagnostics of the collide kernel.
+//   stage 3  every band mode adds the chunk's axis-0 values times exp(-2 pi i kz z / N) to its
+//            accumulator (a direct sum over z, one register pair per mode a thread owns);
+// after the last chunk the accumulators, scaled, are the output rows.  Only one chunk of planes is
+// ever held in shared memory, so FP32 cells up to N = 40 also stage the next chunk's raw planes
+// with asynchronous copies while the current one is transformed.
+// 2D cells are one plane (stage 3 is the identity).  The moments: each thread sums its rows in T
+// and the CTA folds those partial sums into FP64 once per cell.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -38,6 +41,25 @@ constexpr int feat_pz()
     return p;
 }
 
+// band modes |k| <= K in the canonical half space (3D), the most a cell has
+constexpr int feat_band_modes()
+{
+    int n = 0;
+    for (int a = -kFeatK; a <= kFeatK; ++a)
+        for (int b = -kFeatK; b <= kFeatK; ++b)
+            for (int c = 0; c <= kFeatK; ++c)
+                if (a * a + b * b + c * c <= kFeatK * kFeatK && (c > 0 || b > 0 || (b == 0 && a >= 0))) ++n;
+    return n;
+}
+
+// CTAs of 4 warps, several per SM (cells in flight overlap their barrier phases): 168 registers
+// for N <= 32 (3 CTAs per SM), 255 above (2 per SM)
+constexpr int kFeatThreads = 128;
+template <int N>
+constexpr int feat_min_blocks() { return N <= 32 ? 3 : 2; }
+// accumulators per thread: both fields' band modes over the CTA
+constexpr int kFeatQ = (2 * feat_band_modes() + kFeatThreads - 1) / kFeatThreads;
+
 template <typename T, int D, int N>
 struct FeatLayout {
     static constexpr int PZ = (D == 3) ? feat_pz<N, sizeof(T) == 4 ? 8 : 4>() : 1;
@@ -45,18 +67,48 @@ struct FeatLayout {
     static constexpr int X1_PLANE = N * kFeatKx + 1;         // odd complex stride per plane
     static constexpr int X1_FIELD = PZ * X1_PLANE;
     static constexpr int X2_PLANE = kFeatKy * kFeatKx;
-    static constexpr int X2_FIELD = NZ * X2_PLANE;
+    static constexpr int X2_FIELD = PZ * X2_PLANE;             // the current chunk's planes only
+    static constexpr size_t BASE = (size_t)N * sizeof(C2<T>) + 2 * (size_t)(X1_FIELD + X2_FIELD) * sizeof(C2<T>) +
+                                   8 * EF_DIAG_STRIDE * sizeof(double);
+    // FP32 3D cells whose two-field layout plus one chunk of raw planes still leaves the CTAs per
+    // SM of the launch bounds: each chunk of PZ planes is staged in shared memory by asynchronous
+    // copies (cp.async, 16 bytes a thread) issued while the previous chunk is being transformed
+    static constexpr size_t RB_FULL = (size_t)PZ * N * N * sizeof(T);
+    static constexpr bool PF = sizeof(T) == 4 && D == 3 && N % 4 == 0 &&
+                               (BASE + RB_FULL + 16 + 1024) * feat_min_blocks<N>() <= 228 * 1024;
+    static constexpr size_t RB_BYTES = PF ? RB_FULL : 0;
     static constexpr size_t bytes(int nf)
     {
         return (size_t)N * sizeof(C2<T>) + (size_t)nf * (X1_FIELD + X2_FIELD) * sizeof(C2<T>) +
-               8 * EF_DIAG_STRIDE * sizeof(double);
+               8 * EF_DIAG_STRIDE * sizeof(double) + (PF ? RB_BYTES + 16 : 0);
     }
 };
+
+// position of 16-byte piece i of staged row r: XOR with the row's low bits when a row has a power
+// of two of pieces, else a rotation by the row (consecutive rows start on different banks)
+template <int NC>
+__device__ __forceinline__ int feat_swz(int i, int r)
+{
+    if constexpr ((NC & (NC - 1)) == 0) return i ^ (r & (NC < 8 ? NC - 1 : 7));
+    else return (i + r) % NC;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void feat_load_row_swz(const float4 *RB, int r, T (&x)[N])
+{
+    constexpr int NC = N / 4;
+    const float4 *row = RB + r * NC;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+        const float4 v = row[feat_swz<NC>(i, r)];
+        x[4 * i] = v.x; x[4 * i + 1] = v.y; x[4 * i + 2] = v.z; x[4 * i + 3] = v.w;
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ T feat_log(T x);
 template <>
-__device__ __forceinline__ float feat_log<float>(float x) { return logf(x > 1e-30f ? x : 1e-30f); }
+__device__ __forceinline__ float feat_log<float>(float x) { return __logf(x > 1e-30f ? x : 1e-30f); }
 template <>
 __device__ __forceinline__ double feat_log<double>(double x) { return log(x > 1e-30 ? x : 1e-30); }
 
@@ -83,11 +135,11 @@ __device__ __forceinline__ void feat_load_row(const T *src, T (&x)[N])
     }
 }
 
-// row sums of one row (T), folded into the FP64 accumulators; the entropy term only with eta
+// row sums of one row, added to the thread's partial sums (T; folded into FP64 once per cell):
+// mass, the two or three momentum sums, energy, entropy.  The entropy term only with eta
 // (otherwise the ln F pass adds it, from the logarithms it computes anyway)
 template <typename T, int D, int N>
-__device__ __forceinline__ void feat_row_moments(const T (&x)[N], int jz, int jy, double (&s)[EF_DIAG_STRIDE], T &mn,
-                                                 bool eta)
+__device__ __forceinline__ void feat_row_moments(const T (&x)[N], int jz, int jy, T (&ms)[6], T &mn, bool eta)
 {
     T p0 = 0, px = 0, pe = 0, peta = 0;
 #pragma unroll
@@ -100,18 +152,17 @@ __device__ __forceinline__ void feat_row_moments(const T (&x)[N], int jz, int jy
         if (eta && f > T(0)) peta += f * feat_log<T>(f);
         mn = f < mn ? f : mn;
     }
-    const double m = (double)p0;
-    s[0] += m;
+    ms[0] += p0;
     if (D == 3) {
-        s[1] += m * jz;
-        s[2] += m * jy;
-        s[3] += (double)px;
+        ms[1] += p0 * T(jz);
+        ms[2] += p0 * T(jy);
+        ms[3] += px;
     } else {
-        s[1] += m * jy;
-        s[2] += (double)px;
+        ms[1] += p0 * T(jy);
+        ms[2] += px;
     }
-    s[4] += (double)pe + m * ((double)jy * jy + (double)jz * jz);
-    s[5] += (double)peta;
+    ms[4] += pe + p0 * T(jy * jy + jz * jz);
+    ms[5] += peta;
 }
 
 // One real row -> its spectrum at k = 0 .. KX-1 (forward sign, unscaled) through a half-length
@@ -135,12 +186,6 @@ __device__ __forceinline__ void r2c_low(const T (&x)[N], C2<T> (&X)[KX], const C
     }
 }
 
-// CTAs of 4 warps, several per SM (cells in flight overlap their barrier phases): 168 registers
-// for N <= 32 (3 CTAs per SM), 255 above (2 per SM)
-constexpr int kFeatThreads = 128;
-template <int N>
-constexpr int feat_min_blocks() { return N <= 32 ? 3 : 2; }
-
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_kernel(const FeatArgs a)
 {
@@ -154,6 +199,9 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
     C2<T> *X1 = tw + N;
     C2<T> *X2 = X1 + (size_t)nf * Lay::X1_FIELD;
     double *red = reinterpret_cast<double *>(X2 + (size_t)nf * Lay::X2_FIELD);   // [8 warps][EF_DIAG_STRIDE]
+    // chunk staging buffer: PZ * N rows of N / 4 float4 pieces, each row's pieces permuted so that
+    // one thread per row reads without bank conflicts
+    float4 *RB = reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(red + 8 * EF_DIAG_STRIDE) + 15) & ~(uintptr_t)15);
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int j = tid; j < N; j += nt) {
         T sn, cs;
@@ -161,30 +209,52 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
         else sincospi(T(2 * j) / T(N), &sn, &cs);
         tw[j] = C2<T>{cs, -sn};
     }
-    __syncthreads();
     const T scale = T(1) / T(D == 3 ? N * N * N : N * N);
     const int64_t ncells = a.dev_ncells ? (int64_t)*a.dev_ncells : a.ncells;
+    constexpr int64_t CELLSZ = (D == 3) ? (int64_t)N * N * N : (int64_t)N * N;
+    // all threads: asynchronous 16-byte copies of planes [zz, zz + PZ) of cell cc into the buffer
+    auto rb_issue = [&](int64_t cc, int zz) {
+        if constexpr (Lay::PF) {
+            constexpr int NC = N / 4;
+            const int64_t off = a.cell_off ? a.cell_off[cc] : cc * CELLSZ;
+            const float4 *src = reinterpret_cast<const float4 *>(reinterpret_cast<const T *>(a.F) + off + (int64_t)zz * N * N);
+            const uint32_t base = (uint32_t)__cvta_generic_to_shared(RB);
+            for (int p = tid; p < PZ * N * NC; p += kFeatThreads) {
+                const int r = p / NC, i = p % NC;
+                const uint32_t dst = base + (uint32_t)(r * NC + feat_swz<NC>(i, r)) * 16u;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src + p) : "memory");
+            }
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
+    };
+    if (Lay::PF && (int64_t)blockIdx.x < ncells) {
+        rb_issue(blockIdx.x, 0);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
+    __syncthreads();
     for (int64_t c = blockIdx.x; c < ncells; c += gridDim.x) {
         const int64_t coff = a.cell_off ? a.cell_off[c] : c * (int64_t)(D == 3 ? N * N * N : N * N);
         const int64_t row = a.cell_id ? a.cell_id[c] : c;
         const T *F = reinterpret_cast<const T *>(a.F) + coff;
-        double s[EF_DIAG_STRIDE];
-#pragma unroll
-        for (int k = 0; k < EF_DIAG_STRIDE; ++k) s[k] = 0.0;
+        T ms[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         T mn;
         if constexpr (sizeof(T) == 4) mn = T(3.0e38f);
         else mn = T(1.0e300);
+        C2<T> acc[kFeatQ];
+#pragma unroll
+        for (int j = 0; j < kFeatQ; ++j) acc[j] = C2<T>{T(0), T(0)};
 
         for (int z0 = 0; z0 < NZ; z0 += PZ) {
-            // ---- stage 1: rows -> kx = 0 .. K (field 1 reloads its row: it is in L1 / L2)
+            // ---- stage 1: rows -> kx = 0 .. K (field 1 reloads its row: from the staged chunk, or L1 / L2)
             for (int r = tid; r < ROWS; r += nt) {
                 const int zl = r / N, y = r % N;
                 const T *src = F + ((int64_t)(z0 + zl) * N + y) * N;
                 for (int f = 0; f < nf; ++f) {
                     T x[N];
-                    feat_load_row<T, N>(src, x);
+                    if constexpr (Lay::PF) feat_load_row_swz<T, N>(RB, r, x);
+                    else feat_load_row<T, N>(src, x);
                     if (f == 0 && a.mom)
-                        feat_row_moments<T, D, N>(x, (D == 3) ? z0 + zl - N / 2 : 0, y - N / 2, s, mn, nf == 1);
+                        feat_row_moments<T, D, N>(x, (D == 3) ? z0 + zl - N / 2 : 0, y - N / 2, ms, mn, nf == 1);
                     if (f == 1 || a.log_input) {
                         T peta = 0;
 #pragma unroll
@@ -193,7 +263,7 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
                             if (f == 1 && x[n] > T(0)) peta += x[n] * lf;
                             x[n] = lf;
                         }
-                        if (f == 1 && a.mom) s[5] += (double)peta;
+                        if (f == 1 && a.mom) ms[5] += peta;
                     }
                     C2<T> X[kFeatKx];
                     r2c_low<N, kFeatKx, T>(x, X, tw);
@@ -203,6 +273,10 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
                 }
             }
             __syncthreads();
+            if constexpr (Lay::PF) {                  // stage the next chunk (or the next cell's first)
+                if (z0 + PZ < NZ) rb_issue(c, z0 + PZ);
+                else if (c + (int64_t)gridDim.x < ncells) rb_issue(c + gridDim.x, 0);
+            }
             // ---- stage 2: (plane, kx) columns along axis 1 -> ky = -K .. K
             for (int q = tid; q < nf * PZ * kFeatKx; q += nt) {
                 const int f = q / (PZ * kFeatKx);
@@ -213,42 +287,59 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
 #pragma unroll
                 for (int y = 0; y < N; ++y) v[y] = col[y * kFeatKx];
                 fft<N, -1, N>(v, tw);
-                C2<T> *dst = X2 + (size_t)f * Lay::X2_FIELD + (size_t)(z0 + zl) * Lay::X2_PLANE + kx;
+                C2<T> *dst = X2 + (size_t)f * Lay::X2_FIELD + (size_t)zl * Lay::X2_PLANE + kx;
 #pragma unroll
                 for (int ky = -kFeatK; ky <= kFeatK; ++ky) dst[(ky + kFeatK) * kFeatKx] = v[(ky + N) % N];
             }
+            if constexpr (Lay::PF) asm volatile("cp.async.wait_all;\n" ::: "memory");   // the next chunk has landed
             __syncthreads();
+            // ---- stage 3: each band mode adds the chunk's planes times exp(-2 pi i kz z / N)
+            // (the next chunk's stage 2 rewrites X2 only after its stage-1 barrier)
+#pragma unroll
+            for (int j = 0; j < kFeatQ; ++j) {
+                const int q = tid + j * kFeatThreads;
+                if (q < nf * a.nmodes) {
+                    const int f = q >= a.nmodes ? 1 : 0, m = q - f * a.nmodes;
+                    const int kz = __ldg(a.modes + 3 * m), ky = __ldg(a.modes + 3 * m + 1), kx = __ldg(a.modes + 3 * m + 2);
+                    const C2<T> *src = X2 + (size_t)f * Lay::X2_FIELD + (ky + kFeatK) * kFeatKx + kx;
+                    if constexpr (D == 3) {
+                        const int step = ((kz % N) + N) % N;
+                        int e = (step * z0) % N;
+#pragma unroll
+                        for (int zl = 0; zl < PZ; ++zl) {
+                            acc[j] = acc[j] + cmul(src[(size_t)zl * Lay::X2_PLANE], tw[e]);
+                            e += step;
+                            e -= (e >= N) ? N : 0;
+                        }
+                    } else {
+                        acc[j] = src[0];
+                    }
+                }
+            }
         }
 
-        // ---- stage 3: axis-0 sums of the band modes, scaled, to the output rows
-        for (int q = tid; q < nf * a.nmodes; q += nt) {
-            const int f = q / a.nmodes, m = q % a.nmodes;
-            const int kz = a.modes[3 * m], ky = a.modes[3 * m + 1], kx = a.modes[3 * m + 2];
-            const C2<T> *src = X2 + (size_t)f * Lay::X2_FIELD + (ky + kFeatK) * kFeatKx + kx;
-            C2<T> acc{T(0), T(0)};
-            if constexpr (D == 3) {
-                const int step = ((kz % N) + N) % N;
-                int e = 0;
-#pragma unroll 8
-                for (int z = 0; z < N; ++z) {
-                    acc = acc + cmul(src[(size_t)z * Lay::X2_PLANE], tw[e]);
-                    e += step;
-                    e -= (e >= N) ? N : 0;
-                }
-            } else {
-                acc = src[0];
+        // ---- the accumulated band modes, scaled, to the output rows
+#pragma unroll
+        for (int j = 0; j < kFeatQ; ++j) {
+            const int q = tid + j * kFeatThreads;
+            if (q < nf * a.nmodes) {
+                const int f = q >= a.nmodes ? 1 : 0, m = q - f * a.nmodes;
+                float *out = (f == 0 ? a.feat : a.featL) + row * a.fstride;
+                out[2 * m] = (float)(acc[j].x * scale);
+                out[2 * m + 1] = (float)(acc[j].y * scale);
             }
-            float *out = (f == 0 ? a.feat : a.featL) + row * a.fstride;
-            out[2 * m] = (float)(acc.x * scale);
-            out[2 * m + 1] = (float)(acc.y * scale);
         }
 
         // ---- moments: CTA reduction
         if (a.mom) {
+            double s[EF_DIAG_STRIDE];
+#pragma unroll
+            for (int k = 0; k < EF_DIAG_STRIDE; ++k) s[k] = k < 6 ? (double)ms[k] : 0.0;
             s[7] = (double)mn;
             const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
             for (int k = 0; k < EF_DIAG_STRIDE; ++k) {
+                if (k == 6 || k >= 8) continue;       // zero slots
                 double v = s[k];
                 for (int sh = 16; sh > 0; sh >>= 1) {
                     const double u = __shfl_xor_sync(0xffffffffu, v, sh);

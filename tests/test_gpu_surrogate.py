@@ -36,7 +36,7 @@ def _modes(K=6):
     return out
 
 
-@pytest.mark.parametrize("d,N,prec", [(3, 16, ef.EF_PREC_F64), (3, 16, ef.EF_PREC_F32), (3, 24, ef.EF_PREC_F32),
+@pytest.mark.parametrize("d,N,prec", [(3, 16, ef.EF_PREC_F64), (3, 16, ef.EF_PREC_F32), (3, 24, ef.EF_PREC_F32), (3, 32, ef.EF_PREC_F32),
                                        (3, 40, ef.EF_PREC_F64), (3, 48, ef.EF_PREC_F32), (3, 64, ef.EF_PREC_F32),
                                        (2, 32, ef.EF_PREC_F64), (2, 64, ef.EF_PREC_F32)])
 def test_features_match_oracle_dft(d, N, prec):
@@ -61,6 +61,32 @@ def test_features_match_oracle_dft(d, N, prec):
         c = F[i].double().cpu().numpy()          # the values the kernel read
         for field, got in ((c, feat[i]), (np.log(np.maximum(c, 1e-30)), featL[i])):
             Fh = oracle.dft(field) if N <= 24 or d == 2 else oracle.dft_fft(field)
+            ref = np.array([Fh[tuple(k % N for k in m)] * (-1) ** sum(m) for m in modes])
+            g = got.cpu().numpy()[:2 * len(modes)].reshape(-1, 2)
+            g = g[:, 0] + 1j * g[:, 1]
+            assert np.abs(g - ref).max() <= 2e-6 * np.abs(ref).max(), (i, np.abs(g - ref).max() / np.abs(ref).max())
+
+
+@pytest.mark.parametrize("N", [16, 24, 32])
+def test_features_many_cells_per_cta(N):
+    """FP32 3D batches several times larger than the resident CTAs, so each CTA walks many cells
+    and stages the next cell's first planes while finishing the current one: sampled cells
+    (first, middle, last) against the oracle's DFT, of F and of ln F."""
+    L, n = 8.0, 1500
+    plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F32)
+    F = torch.empty(n, N, N, N, device="cuda")
+    inputs.bkw_family_torch(N, L, n, 4242, device="cuda", out=F)
+    feat = torch.zeros(n, ef.EF_FEATURE_STRIDE, device="cuda")
+    featL = torch.zeros_like(feat)
+    ef.ef_features(plan.handle, F, feat, n)
+    ef.ef_features(plan.handle, F, featL, n, log_input=1)
+    torch.cuda.synchronize()
+    assert plan.status(sync=1, reset=1) == ef.EF_OK
+    modes = _modes()
+    for i in (0, 1, 457, n // 2, n - 2, n - 1):
+        c = F[i].double().cpu().numpy()
+        for field, got in ((c, feat[i]), (np.log(np.maximum(c, 1e-30)), featL[i])):
+            Fh = oracle.dft_fft(field)
             ref = np.array([Fh[tuple(k % N for k in m)] * (-1) ** sum(m) for m in modes])
             g = got.cpu().numpy()[:2 * len(modes)].reshape(-1, 2)
             g = g[:, 0] + 1j * g[:, 1]
