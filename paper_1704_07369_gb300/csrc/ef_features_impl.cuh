@@ -5,8 +5,8 @@
 // index-origin convention
 //   Fh_k = N^-d sum_i F[i] exp(-2 pi i k.i / N)      (i the array index, 0 .. N-1 per axis).
 // One CTA per cell (persistent over cells).  For a chunk of PZ axis-0 planes at a time:
-//   stage 1  every row along the contiguous axis is transformed (a real row through a half-length
-//            complex FFT) and only kx = 0 .. K is kept in shared memory;
+//   stage 1  every row along the contiguous axis gets its kx = 0 .. K spectrum by a folded direct
+//            sum with compile-time weights, kept in shared memory;
 //   stage 2  every (plane, kx) column is transformed along axis 1 and ky = -K .. K kept;
 //   stage 3  every band mode adds the chunk's axis-0 values times exp(-2 pi i kz z / N) to its
 //            accumulator (a direct sum over z, one register pair per mode a thread owns);
@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "ef.h"
 #include "ef_fft.cuh"
@@ -165,25 +166,92 @@ __device__ __forceinline__ void feat_row_moments(const T (&x)[N], int jz, int jy
     ms[5] += peta;
 }
 
-// One real row -> its spectrum at k = 0 .. KX-1 (forward sign, unscaled) through a half-length
-// complex transform of z_m = x_2m + i x_2m+1: X_k = E_k + exp(-2 pi i k / N) O_k with
-// E_k = (Z_k + conj Z_{M-k}) / 2 and O_k = (Z_k - conj Z_{M-k}) / 2i, M = N / 2.
-template <int N, int KX, typename T>
-__device__ __forceinline__ void r2c_low(const T (&x)[N], C2<T> (&X)[KX], const C2<T> *tw)
+// Compile-time cos(2 pi p / q) and sin(2 pi p / q) for integers p, q: the angle is folded by its
+// symmetries into |x| <= pi/4 and summed as a Taylor series (terms to x^25: far below FP64 rounding).
+constexpr double kCtPi = 3.14159265358979323846;
+constexpr double ct_sin_series(double x)
 {
-    constexpr int M = N / 2;
-    static_assert(KX <= M, "band wider than the half-length transform");
-    C2<T> z[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) z[m] = C2<T>{x[2 * m], x[2 * m + 1]};
-    fft<M, -1, N>(z, tw);
-#pragma unroll
-    for (int k = 0; k < KX; ++k) {
-        const C2<T> a = z[k], b = cconj(z[(M - k) % M]);
-        const C2<T> e = C2<T>{T(0.5) * (a.x + b.x), T(0.5) * (a.y + b.y)};
-        const C2<T> o = C2<T>{T(0.5) * (a.y - b.y), T(-0.5) * (a.x - b.x)};
-        X[k] = e + cmul(tw[k], o);
+    double t = x, s = x;
+    for (int i = 1; i <= 12; ++i) {
+        t *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        s += t;
     }
+    return s;
+}
+constexpr double ct_cos_series(double x)
+{
+    double t = 1.0, s = 1.0;
+    for (int i = 1; i <= 12; ++i) {
+        t *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        s += t;
+    }
+    return s;
+}
+constexpr double ct_cos2pi(long p, long q)
+{
+    long r = ((p % q) + q) % q;                 // angle a = 2 pi r / q in [0, 2 pi)
+    if (2 * r > q) r = q - r;                   // cos is even: a in [0, pi]
+    if (8 * r <= q) return ct_cos_series(2.0 * kCtPi * r / q);                           // a <= pi / 4
+    if (8 * r <= 3 * q) return ct_sin_series(2.0 * kCtPi * (q - 4 * r) / (4.0 * q));     // cos a = sin(pi/2 - a)
+    return -ct_cos_series(2.0 * kCtPi * (q - 2 * r) / (2.0 * q));                        // cos a = -cos(pi - a)
+}
+constexpr double ct_sin2pi(long p, long q) { return ct_cos2pi(4 * p - q, 4 * q); }    // sin x = cos(x - pi/2)
+
+template <long P, long Q>
+struct Trig2Pi {
+    static constexpr double c = ct_cos2pi(P, Q);
+    static constexpr double s = ct_sin2pi(P, Q);
+};
+
+// One real row -> its spectrum X_k = sum_n x_n exp(-2 pi i k n / N) at k = 0 .. K (unscaled) by the
+// direct sum, folded twice by the symmetries of the kernel: with a_n = x_n + x_{N-n} and
+// b_n = x_n - x_{N-n}, Re X_k = x_0 + (-1)^k x_{N/2} + sum_{n<N/2} a_n cos(2 pi k n / N) and
+// Im X_k = -sum_{n<N/2} b_n sin(2 pi k n / N); pairing n with N/2 - n then leaves N/4 - 1 terms per
+// part, weighted by the compile-time constants (even k: a_n + a_{N/2-n}, b_n - b_{N/2-n}; odd k:
+// a_n - a_{N/2-n}, b_n + b_{N/2-n}).  About 2N + 2(K+1)N/4 operations for the whole band.
+template <typename T, int N, int k, int... n>
+__device__ __forceinline__ C2<T> rdft_mode(const T (&ce)[N / 4], const T (&co)[N / 4], const T (&se)[N / 4],
+                                           const T (&so)[N / 4], T e0, T o0, T aq, T bq, std::integer_sequence<int, n...>)
+{
+    constexpr bool ev = (k % 2) == 0;
+    const T(&cc)[N / 4] = ev ? ce : co;
+    const T(&ss)[N / 4] = ev ? se : so;
+    T re = ev ? e0 : o0;
+    if constexpr (k % 4 == 0) re += aq;
+    else if constexpr (k % 4 == 2) re -= aq;
+    T im = T(0);
+    if constexpr (k % 4 == 1) im = bq;
+    else if constexpr (k % 4 == 3) im = -bq;
+    ((re = fma(cc[n + 1], T(Trig2Pi<(long)k * (n + 1), N>::c), re)), ...);
+    if constexpr (k != 0) ((im = fma(ss[n + 1], T(Trig2Pi<(long)k * (n + 1), N>::s), im)), ...);
+    return C2<T>{re, -im};
+}
+
+template <typename T, int N, int... k>
+__device__ __forceinline__ void rdft_band_all(const T (&x)[N], C2<T> (&X)[sizeof...(k)], std::integer_sequence<int, k...>)
+{
+    static_assert(N % 4 == 0, "the folded direct sum wants N a multiple of 4");
+    constexpr int H = N / 2, Q = N / 4;
+    T ce[Q], co[Q], se[Q], so[Q];               // [1 .. Q-1] used
+#pragma unroll
+    for (int n = 1; n < Q; ++n) {
+        const T an = x[n] + x[N - n], bn = x[n] - x[N - n];
+        const T am = x[H - n] + x[H + n], bm = x[H - n] - x[H + n];
+        ce[n] = an + am;
+        co[n] = an - am;
+        se[n] = bn - bm;
+        so[n] = bn + bm;
+    }
+    ce[0] = co[0] = se[0] = so[0] = T(0);
+    const T aq = x[Q] + x[N - Q], bq = x[Q] - x[N - Q];
+    const T e0 = x[0] + x[H], o0 = x[0] - x[H];
+    ((X[k] = rdft_mode<T, N, k>(ce, co, se, so, e0, o0, aq, bq, std::make_integer_sequence<int, Q - 1>{})), ...);
+}
+
+template <typename T, int N, int KX>
+__device__ __forceinline__ void rdft_band(const T (&x)[N], C2<T> (&X)[KX])
+{
+    rdft_band_all<T, N>(x, X, std::make_integer_sequence<int, KX>{});
 }
 
 template <typename T, int D, int N>
@@ -266,7 +334,7 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
                         if (f == 1 && a.mom) ms[5] += peta;
                     }
                     C2<T> X[kFeatKx];
-                    r2c_low<N, kFeatKx, T>(x, X, tw);
+                    rdft_band<T, N, kFeatKx>(x, X);
                     C2<T> *d = X1 + (size_t)f * Lay::X1_FIELD + (size_t)zl * Lay::X1_PLANE + y * kFeatKx;
 #pragma unroll
                     for (int k = 0; k < kFeatKx; ++k) d[k] = X[k];

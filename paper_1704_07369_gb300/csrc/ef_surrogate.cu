@@ -41,6 +41,27 @@ ef_status scuda(cudaError_t e, const char *what)
 
 int sgrid(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
+// Per-cell scalars of the moments, in FP32 arithmetic (the network's inputs are FP32, and FP64 is a
+// narrow pipe): the mean velocity u = momentum / mass, and the kinetic temperature and relative
+// entropy to the local Maxwellian (zero at equilibrium):
+//   theta = (2E / rho - |u|^2) / d,  KL = eta / rho - ln rho + (d / 2)(ln(2 pi theta) + 1)
+__device__ __forceinline__ void cell_velocity(const double *mi, float &ux, float &uy, float &uz)
+{
+    const float r = 1.0f / (float)mi[0];
+    ux = (float)mi[1] * r;
+    uy = (float)mi[2] * r;
+    uz = (float)mi[3] * r;
+}
+
+__device__ __forceinline__ void cell_theta_kl(const double *mi, int d, float &theta, float &kl)
+{
+    const float rho = (float)mi[0], r = 1.0f / rho;
+    float ux, uy, uz;
+    cell_velocity(mi, ux, uy, uz);
+    theta = (2.0f * (float)mi[4] * r - (ux * ux + uy * uy + uz * uz)) / (float)d;
+    kl = (float)mi[5] * r - logf(rho) + 0.5f * (float)d * (logf(6.283185307179586f * theta) + 1.0f);
+}
+
 // De-translated, mass-normalised features: with m = Fh_0 and u = momentum / mass the mean velocity,
 //   x~_k = Fh_k exp(+i pi k.u / L) / m,     y~_k = Qh_k exp(+i pi k.u / L) / m^2
 // (a velocity shift by u multiplies mode k by exp(-i pi k.u / L); the operator commutes with it up
@@ -54,16 +75,13 @@ __global__ void prep_kernel(const float *featF, const float *featQ, const double
         const int j = (int)(q % nmodes);
         const double *mi = mom + i * EF_DIAG_STRIDE;
         if (extra && j == 0) {
-            // kinetic temperature and relative entropy to the local Maxwellian (zero at equilibrium):
-            // theta = (2E / rho - |u|^2) / d,  KL = eta / rho - ln rho + (d / 2)(ln(2 pi theta) + 1)
-            const double rho = mi[0];
-            const double u2 = (mi[1] * mi[1] + mi[2] * mi[2] + mi[3] * mi[3]) / (rho * rho);
-            const double theta = (2.0 * mi[4] / rho - u2) / d;
-            const double kl = mi[5] / rho - log(rho) + 0.5 * d * (log(2.0 * 3.14159265358979323846 * theta) + 1.0);
-            Xt[i * kStride + 2 * nmodes] = (float)theta;
-            Xt[i * kStride + 2 * nmodes + 1] = (float)kl;
+            float theta, kl;
+            cell_theta_kl(mi, d, theta, kl);
+            Xt[i * kStride + 2 * nmodes] = theta;
+            Xt[i * kStride + 2 * nmodes + 1] = kl;
         }
-        const float ux = (float)(mi[1] / mi[0]), uy = (float)(mi[2] / mi[0]), uz = (float)(mi[3] / mi[0]);
+        float ux, uy, uz;
+        cell_velocity(mi, ux, uy, uz);
         const float ph = pi_over_L * (kvec[3 * j] * ux + kvec[3 * j + 1] * uy + kvec[3 * j + 2] * uz);
         float sn, cs;
         sincosf(ph, &sn, &cs);
@@ -150,7 +168,8 @@ __global__ void normalize_kernel(const float *featF, const float *featQ, const d
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const double *mi = mom + i * EF_DIAG_STRIDE;
-    const float ux = (float)(mi[1] / mi[0]), uy = (float)(mi[2] / mi[0]), uz = (float)(mi[3] / mi[0]);
+    float ux, uy, uz;
+    cell_velocity(mi, ux, uy, uz);
     const float m = featF[i * kStride + 2 * idx0];
     for (int j = lane; j < nmodes; j += 32) {
         const float ph = pi_over_L * (kvec[3 * j] * ux + kvec[3 * j + 1] * uy + kvec[3 * j + 2] * uz);
@@ -166,13 +185,11 @@ __global__ void normalize_kernel(const float *featF, const float *featQ, const d
         }
     }
     if (extra && lane == 0) {
-        const double rho = mi[0];
-        const double u2 = (mi[1] * mi[1] + mi[2] * mi[2] + mi[3] * mi[3]) / (rho * rho);
-        const double theta = (2.0 * mi[4] / rho - u2) / d;
-        const double kl = mi[5] / rho - log(rho) + 0.5 * d * (log(2.0 * 3.14159265358979323846 * theta) + 1.0);
+        float theta, kl;
+        cell_theta_kl(mi, d, theta, kl);
         const int j = 2 * nmodes;
-        X[i * kStride + j] = ((float)theta - mu[j]) / sd[j];
-        X[i * kStride + j + 1] = ((float)kl - mu[j + 1]) / sd[j + 1];
+        X[i * kStride + j] = (theta - mu[j]) / sd[j];
+        X[i * kStride + j + 1] = (kl - mu[j + 1]) / sd[j + 1];
     }
 }
 
@@ -197,7 +214,8 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
     if (i >= n) return;
     const float m = featF[i * kStride + 2 * idx0];
     const double *mi = mom + i * EF_DIAG_STRIDE;
-    const float ux = (float)(mi[1] / mi[0]), uy = (float)(mi[2] / mi[0]), uz = (float)(mi[3] / mi[0]);
+    float ux, uy, uz;
+    cell_velocity(mi, ux, uy, uz);
     float prod = 0.f;
     bool bad = false;
     for (int jm = lane; jm < nf / 2; jm += 32) {
