@@ -7,7 +7,7 @@
 // One CTA per cell (persistent over cells).  For a chunk of PZ axis-0 planes at a time:
 //   stage 1  every row along the contiguous axis gets its kx = 0 .. K spectrum by a folded direct
 //            sum with compile-time weights, kept in shared memory;
-//   stage 2  every (plane, kx) column is transformed along axis 1 and ky = -K .. K kept;
+//   stage 2  every (plane, kx) column gets its ky = -K .. K spectrum along axis 1 the same way;
 //   stage 3  every band mode adds the chunk's axis-0 values times exp(-2 pi i kz z / N) to its
 //            accumulator (a direct sum over z, one register pair per mode a thread owns);
 // after the last chunk the accumulators, scaled, are the output rows.  Only one chunk of planes is
@@ -254,6 +254,65 @@ __device__ __forceinline__ void rdft_band(const T (&x)[N], C2<T> (&X)[KX])
     rdft_band_all<T, N>(x, X, std::make_integer_sequence<int, KX>{});
 }
 
+// One complex column -> X_k = sum_n v_n exp(-2 pi i k n / N) at k = -K .. K by the same folded
+// direct sum: with p_n = v_n + v_{N-n} and m_n = v_n - v_{N-n},
+//   X_{+-k} = C_k -+ i S_k,  C_k = v_0 + (-1)^k v_{N/2} + sum_{n<N/2} p_n cos(2 pi k n / N),
+//   S_k = sum_{n<N/2} m_n sin(2 pi k n / N),
+// and pairing n with N/2 - n halves both sums again (even k: p_n + p_{N/2-n}, m_n - m_{N/2-n};
+// odd k: p_n - p_{N/2-n}, m_n + m_{N/2-n}).  Y[K + k] receives X_k.
+template <typename T, int N, int K, int k, int... n>
+__device__ __forceinline__ void cdft_mode(const C2<T> (&pe)[N / 4], const C2<T> (&po)[N / 4], const C2<T> (&me)[N / 4],
+                                          const C2<T> (&mo)[N / 4], C2<T> e0, C2<T> o0, C2<T> pq, C2<T> mq,
+                                          C2<T> (&Y)[2 * K + 1], std::integer_sequence<int, n...>)
+{
+    constexpr bool ev = (k % 2) == 0;
+    const C2<T>(&pp)[N / 4] = ev ? pe : po;
+    const C2<T>(&mm)[N / 4] = ev ? me : mo;
+    C2<T> c = ev ? e0 : o0;
+    if constexpr (k % 4 == 0) c = c + pq;
+    else if constexpr (k % 4 == 2) c = c - pq;
+    ((c.x = fma(pp[n + 1].x, T(Trig2Pi<(long)k * (n + 1), N>::c), c.x)), ...);
+    ((c.y = fma(pp[n + 1].y, T(Trig2Pi<(long)k * (n + 1), N>::c), c.y)), ...);
+    if constexpr (k == 0) {
+        Y[K] = c;
+    } else {
+        C2<T> sv{T(0), T(0)};
+        if constexpr (k % 4 == 1) sv = mq;
+        else if constexpr (k % 4 == 3) sv = C2<T>{-mq.x, -mq.y};
+        ((sv.x = fma(mm[n + 1].x, T(Trig2Pi<(long)k * (n + 1), N>::s), sv.x)), ...);
+        ((sv.y = fma(mm[n + 1].y, T(Trig2Pi<(long)k * (n + 1), N>::s), sv.y)), ...);
+        Y[K + k] = C2<T>{c.x + sv.y, c.y - sv.x};          // C - i S
+        Y[K - k] = C2<T>{c.x - sv.y, c.y + sv.x};          // C + i S
+    }
+}
+
+template <typename T, int N, int K, int... k>
+__device__ __forceinline__ void cdft_band_all(const C2<T> (&v)[N], C2<T> (&Y)[2 * K + 1], std::integer_sequence<int, k...>)
+{
+    static_assert(N % 4 == 0, "the folded direct sum wants N a multiple of 4");
+    constexpr int H = N / 2, Q = N / 4;
+    C2<T> pe[Q], po[Q], me[Q], mo[Q];           // [1 .. Q-1] used
+#pragma unroll
+    for (int n = 1; n < Q; ++n) {
+        const C2<T> pn = v[n] + v[N - n], mn = v[n] - v[N - n];
+        const C2<T> pm = v[H - n] + v[H + n], mm = v[H - n] - v[H + n];
+        pe[n] = pn + pm;
+        po[n] = pn - pm;
+        me[n] = mn - mm;
+        mo[n] = mn + mm;
+    }
+    pe[0] = po[0] = me[0] = mo[0] = C2<T>{T(0), T(0)};
+    const C2<T> pq = v[Q] + v[N - Q], mq = v[Q] - v[N - Q];
+    const C2<T> e0 = v[0] + v[H], o0 = v[0] - v[H];
+    (cdft_mode<T, N, K, k>(pe, po, me, mo, e0, o0, pq, mq, Y, std::make_integer_sequence<int, Q - 1>{}), ...);
+}
+
+template <typename T, int N, int K>
+__device__ __forceinline__ void cdft_band(const C2<T> (&v)[N], C2<T> (&Y)[2 * K + 1])
+{
+    cdft_band_all<T, N, K>(v, Y, std::make_integer_sequence<int, K + 1>{});
+}
+
 template <typename T, int D, int N>
 __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_kernel(const FeatArgs a)
 {
@@ -354,10 +413,11 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
                 C2<T> v[N];
 #pragma unroll
                 for (int y = 0; y < N; ++y) v[y] = col[y * kFeatKx];
-                fft<N, -1, N>(v, tw);
+                C2<T> Yk[kFeatKy];
+                cdft_band<T, N, kFeatK>(v, Yk);
                 C2<T> *dst = X2 + (size_t)f * Lay::X2_FIELD + (size_t)zl * Lay::X2_PLANE + kx;
 #pragma unroll
-                for (int ky = -kFeatK; ky <= kFeatK; ++ky) dst[(ky + kFeatK) * kFeatKx] = v[(ky + N) % N];
+                for (int j = 0; j < kFeatKy; ++j) dst[j * kFeatKx] = Yk[j];
             }
             if constexpr (Lay::PF) asm volatile("cp.async.wait_all;\n" ::: "memory");   // the next chunk has landed
             __syncthreads();
