@@ -463,6 +463,11 @@ def surrogate_leg(args, device):
                                        ("audit_tolerant", SUR_AUDIT, 0.05)):
             tr.sur.set_policy(max_miss_fraction=max_miss)
             ms = timed(lambda i: tr.sur.infer(F, q, flags, SUR_CELLS, audit, i, SUR_TOL), reps)
+            # the timed calls again, untimed, to count the draws that sent the batch to the plain operator
+            fallbacks = 0
+            for i in range(reps):
+                tr.sur.infer(F, q, flags, SUR_CELLS, audit, 100 + i, SUR_TOL)
+                fallbacks += int(((flags & 16) != 0).any().item())
             f = flags.cpu().numpy()
             e = S.band_rel_l2(q, ref)
             e64 = S.band_rel_l2(q[:n64], ref64)
@@ -471,7 +476,7 @@ def surrogate_leg(args, device):
                 "cells_per_s": SUR_CELLS / ms * 1e3, "speedup_vs_plain": plain_ms / ms,
                 "gated": int(((f & 1) != 0).sum()), "audited": int(((f & 2) != 0).sum()),
                 "audit_misses": int(((f & 4) != 0).sum()), "plain_used": int(((f & 8) != 0).sum()),
-                "batch_fallback": bool(((f & 16) != 0).any()),
+                "batch_fallback": bool(((f & 16) != 0).any()), "timed_calls": reps, "batch_fallback_calls": fallbacks,
                 "band_rel_l2_vs_fp32_plain": _quantiles(e), "band_rel_l2_vs_fp64_first1024": _quantiles(e64)}
         tr.sur.set_policy(0.0)
         out["kernels"][name] = res

@@ -13,8 +13,8 @@
 // after the last chunk the accumulators, scaled, are the output rows.  Only one chunk of planes is
 // ever held in shared memory, so FP32 cells up to N = 40 also stage the next chunk's raw planes
 // with asynchronous copies while the current one is transformed.
-// 2D cells are one plane (stage 3 is the identity).  The moments: each thread sums its rows in T
-// and the CTA folds those partial sums into FP64 once per cell.
+// 2D cells are one plane (stage 3 is the identity).  The moments: each thread sums its rows in T,
+// each warp its threads' sums in T, and the CTA the warps' sums in FP64, once per cell.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -459,21 +459,21 @@ __global__ void __launch_bounds__(kFeatThreads, feat_min_blocks<N>()) features_k
         }
 
         // ---- moments: CTA reduction
-        if (a.mom) {
-            double s[EF_DIAG_STRIDE];
+        if (a.mom) {                              // warp sums in T, the CTA's in FP64
+            T s[EF_DIAG_STRIDE];
 #pragma unroll
-            for (int k = 0; k < EF_DIAG_STRIDE; ++k) s[k] = k < 6 ? (double)ms[k] : 0.0;
-            s[7] = (double)mn;
+            for (int k = 0; k < EF_DIAG_STRIDE; ++k) s[k] = k < 6 ? ms[k] : T(0);
+            s[7] = mn;
             const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
             for (int k = 0; k < EF_DIAG_STRIDE; ++k) {
                 if (k == 6 || k >= 8) continue;       // zero slots
-                double v = s[k];
+                T v = s[k];
                 for (int sh = 16; sh > 0; sh >>= 1) {
-                    const double u = __shfl_xor_sync(0xffffffffu, v, sh);
-                    v = (k == 7) ? fmin(v, u) : v + u;
+                    const T u = __shfl_xor_sync(0xffffffffu, v, sh);
+                    v = (k == 7) ? (u < v ? u : v) : v + u;
                 }
-                if (lane == 0) red[warp * EF_DIAG_STRIDE + k] = v;
+                if (lane == 0) red[warp * EF_DIAG_STRIDE + k] = (double)v;
             }
         }
         __syncthreads();
