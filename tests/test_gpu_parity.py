@@ -365,8 +365,9 @@ def test_moments_kernel_against_oracle():
             Fi = F[i].double().cpu().numpy()
             ref = oracle.moments(Fi, L, Q[i].double().cpu().numpy())
             k_gpu = [0, 1, 2] + ([3] if d == 3 else []) + [4, 5, 6, 7]
-            # FP32 input: each lane sums at most 32 FP32 products before the FP64 fold, so the
-            # error is at most about 33 * 2^-24 of the sum of |terms| (a few times max(1, |ref|))
+            # FP32 input: each lane sums runs of at most 32 float4 partials, keeps the runs' total in
+            # a compensated FP32 pair, and a warp adds its lanes in FP32: the error is at most about
+            # (3 + 32 + 8) * 2^-24 of the sum of |terms| (a few times max(1, |ref|))
             tol = 1e-12 if prec == ef.EF_PREC_F64 else 1e-5
             for kg, kr in zip(k_gpu, range(len(ref))):
                 assert abs(o[i, kg] - ref[kr]) <= tol * max(1.0, abs(ref[kr])), (d, kg)
