@@ -37,7 +37,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 // four terms, a run of 32 float4 partials, the pair, the warp); the logarithm is the fast one
 // (a few ulp), in the same budget.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) moments_kernel(const T *F, const T *Q, const int64_t *cell_off,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) moments_kernel(const T *F, const T *Q, const int64_t *cell_off,
                                                       const int64_t *cell_N, int64_t ncells, int N_uniform,
                                                       double h_uniform_times_N, double *out)
 {
