@@ -245,7 +245,9 @@ ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat
 
 /* Moments and entropy of each cell (layout EF_DIAG_STRIDE, entries [0..7] and [9]).  Here [8] is
  * the positivity error of Sec. 4.2, Example 1: (sum |F| - sum F) / sum |F| (0 for F >= 0), in place
- * of max nu.  Q_dev may be null; then [6] = 0 and [9] = 0. */
+ * of max nu.  Q_dev may be null; then [6] = 0 and [9] = 0.  Accuracy: FP64 plans sum in FP64;
+ * FP32 plans sum runs in FP32 into compensated FP32 pairs and warps in FP32, an error of at most
+ * about 43 * 2^-24 of the sum of the entries' |terms|, results stored as doubles. */
 ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_dev, double *out_dev,
                              int64_t ncells, ef_stream_t stream);
 
