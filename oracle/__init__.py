@@ -11,7 +11,10 @@ The arithmetic lives in ``ef_oracle.c`` (plain C, double precision, OpenMP), bui
 * the relative l_p errors of Sec. 4.2, the positivity error epsilon and the discrete entropy
   eta = (2T/N)^d sum F ln F;
 * third-order SSP Runge-Kutta and forward Euler steppers over the oracle operator (Sec. 4.1);
-* moments and entropy production of a grid function.
+* moments and entropy production of a grid function;
+* the spatially inhomogeneous coupling (left to future work in Sec. 5): first-order upwind free
+  transport between cells that are the points of a periodic 1D spatial grid, and Lie splitting of
+  transport and collision.
 
 Kernel numbering follows the library's C header: 0 = Maxwell molecules (2D, B = 1/(2 pi)),
 1 = hard spheres (3D, B = |g|/(4 pi)), 2 = Maxwell molecules (3D, B = 1/(4 pi)).
@@ -361,4 +364,34 @@ def euler(p: Params, F: np.ndarray, dt: float, steps: int = 1):
     """Forward Euler F <- F + dt Q^sigma[F]."""
     for _ in range(steps):
         F = F + dt * collide(p, F)
+    return F
+
+
+# ------------------------------------------------- spatially inhomogeneous coupling ----------
+# The paper leaves the spatially inhomogeneous equation to future work (Sec. 5).  Reading used here:
+# the cells of a batch are the points x_i = i dx of a periodic 1D spatial grid, F moves along x with
+# the velocity component of the first array axis, and free transport is discretised by first-order
+# upwinding; transport and collision are combined by Lie splitting.
+
+def transport_upwind(F: np.ndarray, T: float, dx: float, dt: float) -> np.ndarray:
+    """One upwind step of dF/dt + v dF/dx = 0 on cells F[i] (shape [M, N, ...]), periodic in i, with
+    v = h (j - N/2) the velocity of the first velocity axis and nu = v dt / dx:
+    F_i - nu (F_i - F_{i-1}) where nu > 0, F_i - nu (F_{i+1} - F_i) where nu < 0."""
+    F = np.asarray(F, dtype=np.float64)
+    N = F.shape[1]
+    h = 2.0 * T / N
+    nu = (np.arange(N) - N // 2) * h * dt / dx
+    nu = nu.reshape([1, N] + [1] * (F.ndim - 2))
+    left = np.roll(F, 1, axis=0)        # F_{i-1}
+    right = np.roll(F, -1, axis=0)      # F_{i+1}
+    return np.where(nu > 0, F - nu * (F - left), F - nu * (right - F))
+
+
+def inhomogeneous_lie(p: Params, F: np.ndarray, dx: float, dt: float, steps: int = 1, rk3: bool = False):
+    """Lie splitting: each step one upwind transport step, then one collision step (forward Euler or
+    SSP-RK3 of the oracle operator) in every cell."""
+    F = np.asarray(F, dtype=np.float64)
+    for _ in range(steps):
+        F = transport_upwind(F, p.T, dx, dt)
+        F = np.stack([(ssp_rk3 if rk3 else euler)(p, c, dt) for c in F])
     return F

@@ -385,3 +385,71 @@ def test_classical_form_conserves_mass_and_dissipates_entropy():
     Q = oracle.collide_classical(p, F)
     assert abs(Q.sum()) <= 1e-13 * np.abs(Q).sum()
     assert (Q[F > 0] * np.log(F[F > 0])).sum() < 0
+
+
+# ---------------------------------------------- spatially inhomogeneous coupling (Sec. 5) -------
+
+def _cells(M, N, d, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.1, 1.0, size=(M,) + (N,) * d)
+
+
+def test_transport_keeps_a_spatially_uniform_state():
+    F = np.stack([_cells(1, 8, 2, 3)[0]] * 5)
+    out = oracle.transport_upwind(F, 4.0, 0.5, 0.1)
+    assert np.array_equal(out, F)
+
+
+def test_transport_at_courant_one_is_the_exact_shift():
+    """N = 8, T = 4: h = 1, the first-axis indices 7 and 1 carry v = +3 and -3.  With dt / dx = 1/3
+    their Courant numbers are +1 and -1: those slices move one cell up and one cell down; index 4
+    (v = 0) stays."""
+    F = _cells(6, 8, 2, 5)
+    out = oracle.transport_upwind(F, 4.0, 3.0, 1.0)
+    assert np.allclose(out[:, 7], np.roll(F, 1, axis=0)[:, 7], rtol=0, atol=1e-15)
+    assert np.allclose(out[:, 1], np.roll(F, -1, axis=0)[:, 1], rtol=0, atol=1e-15)
+    assert np.array_equal(out[:, 4], F[:, 4])
+
+
+def test_transport_conserves_mass_per_velocity_and_keeps_positivity_below_courant_one():
+    F = _cells(9, 8, 3, 7)
+    T, dx = 4.0, 1.0
+    vmax = 4.0                                   # |v| <= (N/2) h
+    out = oracle.transport_upwind(F, T, dx, 0.9 * dx / vmax)
+    assert np.allclose(out.sum(axis=0), F.sum(axis=0), rtol=1e-14, atol=0)
+    assert out.min() >= 0.0
+    # beyond Courant number one the upwind step is no longer a convex combination
+    G = np.zeros_like(F)
+    G[4] = 1.0
+    bad = oracle.transport_upwind(G, T, dx, 2.0 * dx / vmax)
+    assert bad.min() < 0.0
+
+
+def test_transport_converges_at_first_order_to_the_exact_shift():
+    """A smooth periodic profile in x, carried by each velocity: the upwind error at a fixed time,
+    with dt / dx fixed, halves when dx halves."""
+    N, T, Lx, t_end = 8, 4.0, 1.0, 0.125
+    h = 2.0 * T / N
+    v = (np.arange(N) - N // 2) * h
+
+    def err(M):
+        dx = Lx / M
+        dt = 0.5 * dx / np.abs(v).max()
+        steps = int(round(t_end / dt))
+        x = np.arange(M) * dx
+        F = np.stack([1.0 + 0.5 * np.sin(2 * np.pi * xi / Lx) * np.ones((N, N)) for xi in x])
+        for _ in range(steps):
+            F = oracle.transport_upwind(F, T, dx, dt)
+        exact = 1.0 + 0.5 * np.sin(2 * np.pi * (x[:, None] - v[None, :] * steps * dt) / Lx)
+        return np.abs(F[:, :, 0] - exact).max()
+
+    e1, e2, e3 = err(64), err(128), err(256)
+    assert 1.8 < e1 / e2 < 2.2 and 1.8 < e2 / e3 < 2.2, (e1, e2, e3)
+
+
+def test_lie_splitting_conserves_total_mass():
+    p = oracle.Params(d=2, N=8, T=4.0, kernel=oracle.KERNEL_MAXWELL, R=16)
+    F = _cells(4, 8, 2, 11)
+    out = oracle.inhomogeneous_lie(p, F, 0.5, 0.02, steps=2)
+    assert abs(out.sum() - F.sum()) <= 1e-13 * F.sum()
+    assert out.min() >= 0.0
