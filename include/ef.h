@@ -251,6 +251,21 @@ ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat
 ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_dev, double *out_dev,
                              int64_t ncells, ef_stream_t stream);
 
+/* Free transport between spatial cells (the spatially inhomogeneous setting that Sec. 5 leaves to
+ * future work; the collision step between transport steps is ef_euler_step or ef_rk3_step on the
+ * same batch, by operator splitting).  The ncells cells of a uniform plan are the points x_i of a
+ * periodic 1D spatial grid of spacing dx (cell i's neighbours are i - 1 and i + 1 modulo ncells),
+ * and the velocity component along the first array axis, v = h (j - N/2) with h = 2L/N, carries F
+ * along x.  One first-order upwind step with the Courant number nu = v dt / dx:
+ *   F_out_i = F_in_i - nu (F_in_i - F_in_{i-1})  (nu > 0),  F_in_i - nu (F_in_{i+1} - F_in_i)  (nu < 0),
+ * a convex combination of F_in_i and its upwind neighbour when max |nu| = (N/2) h |dt| / dx <= 1,
+ * so F >= 0 is kept then (not checked: larger steps are computed as asked).  Mass per velocity point
+ * summed over the cells is conserved.  F_in and F_out: device arrays of ncells cells (layout as
+ * ef_collide), 16-byte aligned, not overlapping.  Errors: EF_ERR_INVALID_ARG for a batched plan,
+ * null / misaligned / overlapping arrays, ncells < 0, dx <= 0 or non-finite dt. */
+ef_status ef_transport_step(ef_plan_t plan, const void *F_in_dev, void *F_out_dev, int64_t ncells, double dx,
+                            double dt, ef_stream_t stream);
+
 /* Streaming a batch that lives in host memory (no counterpart in the paper; the paper's method
  * is per cell).  The cells (sizes N_host[c], back to back as for ef_plan_create_batched) are cut
  * into nchunks contiguous chunks of about equal work, each with its own batched plan and CUDA

@@ -41,7 +41,7 @@ SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
            "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer",
            "ef_stream_plan_create", "ef_stream_plan_destroy", "ef_stream_plan_info", "ef_stream_euler_step",
-           "ef_stream_plan_status", "ef_status_string", "ef_last_error")
+           "ef_stream_plan_status", "ef_transport_step", "ef_status_string", "ef_last_error")
 EF_FEATURE_K = 6
 EF_FEATURE_STRIDE = 928
 
@@ -105,6 +105,7 @@ def lib():
         L.ef_stream_euler_step.argtypes = [vp, vp, dbl, i32, vp, vp]
         L.ef_stream_plan_status.argtypes = [vp, i32, i32]
         L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
+        L.ef_transport_step.argtypes = [vp, vp, vp, i64, dbl, dbl, vp]
         L.ef_plan_status.argtypes = [vp, i32, i32]
         L.ef_plan_set_graph.argtypes = [vp, i32]
         L.ef_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
@@ -330,6 +331,10 @@ def ef_moments_entropy(plan, F, Q, out, ncells, stream=None):
     _check(lib().ef_moments_entropy(plan, _ptr(F), _ptr(Q), _ptr(out), int(ncells), _stream(stream)))
 
 
+def ef_transport_step(plan, F_in, F_out, ncells, dx, dt, stream=None):
+    _check(lib().ef_transport_step(plan, _ptr(F_in), _ptr(F_out), int(ncells), float(dx), float(dt), _stream(stream)))
+
+
 def ef_plan_status(plan, sync=1, reset=0):
     return lib().ef_plan_status(plan, int(sync), int(reset))
 
@@ -379,6 +384,34 @@ class Plan:
 
     def moments(self, F, Q, out, ncells=None, stream=None):
         ef_moments_entropy(self.handle, F, Q, out, self._n(F, ncells), stream)
+
+    def transport(self, F_in, F_out, dx, dt, ncells=None, stream=None):
+        """One upwind free-transport step between the batch's cells (a periodic 1D spatial grid)."""
+        ef_transport_step(self.handle, F_in, F_out, self._n(F_in, ncells), dx, dt, stream)
+
+    def inhomogeneous(self, F, scratch, dx, dt, nsteps=1, rk3=False, diag=None, stream=None):
+        """Lie splitting of dF/dt + v dF/dx = Q(F) on the batch's cells as the points of a periodic 1D
+        spatial grid: each step transports the state into the other buffer (F and scratch take
+        turns) and applies one collision step (Euler or SSP-RK3) there, in place.  The result ends
+        in F (copied back from scratch after an odd number of steps).  diag (optional) receives
+        each step's collision diagnostics, [step][cell][k]."""
+        import torch
+        n = self._n(F, None)
+        a, b = F, scratch
+        for k in range(int(nsteps)):
+            self.transport(a, b, dx, dt, ncells=n, stream=stream)
+            d = None if diag is None else diag[k]
+            (self.rk3 if rk3 else self.euler)(b, dt, 1, d, ncells=n, stream=stream)
+            a, b = b, a
+        if a is not F:
+            if stream is None:
+                s = torch.cuda.current_stream()
+            elif isinstance(stream, int):
+                s = torch.cuda.ExternalStream(stream)
+            else:
+                s = stream
+            with torch.cuda.stream(s):
+                F.copy_(a)
 
     def status(self, sync=1, reset=0):
         return ef_plan_status(self.handle, sync, reset)

@@ -70,6 +70,9 @@ EF_DECLARE_FEAT(f64)
 #undef EF_DECLARE_FEAT
 
 // out = a x + b y over n values (ef_step.cu); prec 0 = FP32, 1 = FP64
+// free transport between the spatial cells of a uniform batch (ef_transport.cu), c = dt h / dx
+cudaError_t transport_launch(int prec, int d, int N, const void *Fin, void *Fout, int64_t ncells, double c,
+                             cudaStream_t s);
 cudaError_t axpby_launch(int prec, void *out, const void *x, const void *y, double a, double b, int64_t n,
                          cudaStream_t s);
 

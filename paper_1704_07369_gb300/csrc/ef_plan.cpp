@@ -1217,6 +1217,30 @@ ef_status ef_moments_entropy(ef_plan_t p, const void *F, const void *Q, double *
     return EF_OK;
 }
 
+ef_status ef_transport_step(ef_plan_t p, const void *F_in, void *F_out, int64_t ncells, double dx, double dt,
+                            ef_stream_t stream)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (p->batched) return fail(EF_ERR_INVALID_ARG, "transport needs a uniform plan (one N for every spatial cell)");
+    if (ncells < 0) return fail(EF_ERR_INVALID_ARG, "ncells < 0");
+    if (!(dx > 0.0) || !std::isfinite(dx) || !std::isfinite(dt)) return fail(EF_ERR_INVALID_ARG, "dx must be > 0, dt finite");
+    if (ncells == 0) return EF_OK;
+    if (!F_in || !F_out) return fail(EF_ERR_INVALID_ARG, "null F_in or F_out");
+    if (((uintptr_t)F_in | (uintptr_t)F_out) % 16) return fail(EF_ERR_INVALID_ARG, "F_in and F_out must be 16-byte aligned");
+    const Desc &ds = p->desc;
+    const int64_t cell = ds.d == 3 ? (int64_t)ds.N * ds.N * ds.N : (int64_t)ds.N * ds.N;
+    const uintptr_t bytes = (uintptr_t)(ncells * cell * (ds.prec == EF_PREC_F32 ? 4 : 8));
+    const uintptr_t a = (uintptr_t)F_in, b = (uintptr_t)F_out;
+    if (a < b + bytes && b < a + bytes) return fail(EF_ERR_INVALID_ARG, "F_out must not overlap F_in");
+    ef_status st = check_device(p);
+    if (st != EF_OK) return st;
+    const double h = 2.0 * ds.L / ds.N;
+    cudaError_t e = ef::transport_launch(ds.prec == EF_PREC_F32 ? 0 : 1, ds.d, ds.N, F_in, F_out, ncells, dt * h / dx,
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "transport launch");
+    return EF_OK;
+}
+
 ef_status ef_features(ef_plan_t p, const void *F, float *feat, int64_t ncells, int log_input, ef_stream_t stream)
 {
     if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");

@@ -47,6 +47,7 @@ def test_host_side_argument_checks():
     assert lib.ef_stream_plan_destroy(None) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_stream_euler_step(None, None, 0.01, 1, None, None) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_rk3_step(None, None, 0.01, 1, None, 1, None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_transport_step(None, None, None, 4, 0.1, 0.01, None) == ef.EF_ERR_INVALID_ARG
 
 
 def test_oracle_is_not_on_the_product_path():
