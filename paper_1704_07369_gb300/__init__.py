@@ -413,6 +413,24 @@ class Plan:
             with torch.cuda.stream(s):
                 F.copy_(a)
 
+    def inhomogeneous_sharded(self, F_ext, scratch_ext, dx, dt, nsteps=1, rk3=False, group=None):
+        """``inhomogeneous`` for a spatial grid split over ranks (one GPU each): this rank's cells
+        are F_ext[1 .. n] of a [n + 2, ...] array whose two ends are halo cells, refreshed before
+        every transport step by ``shard.halo_exchange`` (NCCL point-to-point).  Runs on torch's
+        current stream; the result ends in F_ext."""
+        from . import shard
+        n = F_ext.shape[0] - 2
+
+        def transport(a, b):
+            self.transport(a, b, dx, dt, ncells=n + 2)
+
+        def collide(view):
+            (self.rk3 if rk3 else self.euler)(view, dt, 1, None, ncells=n)
+
+        out = shard.lie_steps_sharded(F_ext, scratch_ext, nsteps, transport, collide, group)
+        if out is not F_ext:
+            F_ext.copy_(out)
+
     def status(self, sync=1, reset=0):
         return ef_plan_status(self.handle, sync, reset)
 

@@ -11,6 +11,12 @@ evaluates its own cells and nothing is exchanged on the data path.  Two layouts 
 
 ``allreduce_diagnostics`` sums per-rank totals of the FP64 diagnostics (mass, momentum, energy,
 entropy, entropy production) when a global figure is wanted; it is not on the data path.
+
+The spatially inhomogeneous coupling (cells as the points of a periodic 1D spatial grid, upwind
+transport between neighbours) is the one place where ranks do exchange data: each rank owns a
+contiguous block of cells (``spatial_blocks``) stored with one halo cell at each end, and before
+every transport step ``halo_exchange`` sends its first cell to the left neighbour rank and its
+last cell to the right one (periodic over ranks).  ``lie_steps_sharded`` drives the split steps.
 """
 from __future__ import annotations
 
@@ -73,3 +79,63 @@ def allreduce_diagnostics(diag):
     out[8] = maxs[0]
     out[9] = mins[1]
     return out
+
+
+def spatial_blocks(ncells: int, world: int):
+    """Contiguous blocks of a periodic 1D spatial grid of ``ncells`` cells over ``world`` ranks, in
+    rank order: a list of (first cell, cell count), counts differing by at most one."""
+    if world < 1 or ncells < world:
+        raise ValueError("need 1 <= world <= ncells")
+    base, extra = divmod(ncells, world)
+    out, start = [], 0
+    for r in range(world):
+        n = base + (1 if r < extra else 0)
+        out.append((start, n))
+        start += n
+    return out
+
+
+def halo_exchange(F_ext, group=None):
+    """Fill the halo cells of a rank's block ``F_ext`` ([n + 2, ...]: F_ext[1..n] the rank's cells in
+    spatial order, F_ext[0] and F_ext[n + 1] the halos) with the neighbouring ranks' boundary cells:
+    the left halo gets the left rank's last cell, the right halo the right rank's first cell,
+    periodically over ranks.  One rank (or no process group) wraps onto itself.  Point-to-point
+    messages, two sends and two receives per rank; on the GPU they go through NCCL, on the host
+    through gloo."""
+    import torch.distributed as dist
+    n = F_ext.shape[0] - 2
+    if n < 1:
+        raise ValueError("a block needs at least one cell besides its two halos")
+    world = dist.get_world_size(group) if dist.is_available() and dist.is_initialized() else 1
+    if world == 1:
+        F_ext[0].copy_(F_ext[n])
+        F_ext[n + 1].copy_(F_ext[1])
+        return
+    rank = dist.get_rank(group)
+    left, right = (rank - 1) % world, (rank + 1) % world
+    if group is not None:
+        left, right = dist.get_global_rank(group, left), dist.get_global_rank(group, right)
+    # send order (to the left, to the right) and receive order (from the right, from the left)
+    # pair up message by message even when left == right (two ranks)
+    reqs = [dist.isend(F_ext[1].contiguous(), left, group=group, tag=0),
+            dist.isend(F_ext[n].contiguous(), right, group=group, tag=1)]
+    rbuf, lbuf = F_ext[n + 1], F_ext[0]
+    reqs.append(dist.irecv(rbuf, right, group=group, tag=0))
+    reqs.append(dist.irecv(lbuf, left, group=group, tag=1))
+    for q in reqs:
+        q.wait()
+
+
+def lie_steps_sharded(F_ext, scratch_ext, nsteps: int, transport, collide, group=None):
+    """Lie splitting over a rank's block with halos.  ``F_ext`` and ``scratch_ext`` are [n + 2, ...];
+    each step exchanges the halos of the current buffer, ``transport(cur, other)`` writes all
+    n + 2 cells of the other buffer (the two halo outputs are never used), ``collide(view)``
+    updates the interior other[1 .. n] in place, and the buffers swap.  Returns the buffer that
+    holds the state."""
+    a, b = F_ext, scratch_ext
+    for _ in range(int(nsteps)):
+        halo_exchange(a, group)
+        transport(a, b)
+        collide(b[1:-1])
+        a, b = b, a
+    return a

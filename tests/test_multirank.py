@@ -1,7 +1,9 @@
 """Multi-rank host logic on CPU (no GPU): the work partition of a cell batch over ranks, two gloo
 ranks running the benchmark's distributed helpers and the diagnostics all-reduce, and the
-benchmark's reference arm launched as two ranks.  The data path itself exchanges nothing: cells
-are independent, so each rank only evaluates its own."""
+benchmark's reference arm launched as two ranks.  The homogeneous data path exchanges nothing:
+cells are independent, so each rank only evaluates its own.  The spatially inhomogeneous coupling
+does exchange one halo cell per neighbour and step; its split over two and three gloo ranks is
+checked against the oracle's global run."""
 import itertools
 import json
 import os
@@ -103,3 +105,72 @@ def test_bench_reference_arm_as_two_ranks():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+# ------------------------- spatially inhomogeneous coupling split over ranks (halo exchange) ----
+
+def _halo_case():
+    import oracle
+    M, N, T, dx, dt, steps = 11, 8, 4.0, 0.5, 0.05, 3
+    G = np.random.default_rng(7).uniform(0.1, 1.0, size=(M, N, N))
+    p = oracle.Params(d=2, N=N, T=T, kernel=oracle.KERNEL_MAXWELL, R=16)
+    return oracle, G, p, T, dx, dt, steps
+
+
+def _halo_block(world, rank, group=None):
+    """This rank's block of the global state after the split Lie steps (the oracle's transport and
+    Euler step as the local operators), and the same block of the oracle's global run."""
+    import torch
+    oracle, G, p, T, dx, dt, steps = _halo_case()
+    start, n = shard.spatial_blocks(G.shape[0], world)[rank]
+    F_ext = torch.zeros((n + 2,) + G.shape[1:], dtype=torch.float64)
+    F_ext[1:n + 1] = torch.from_numpy(G[start:start + n])
+    S = torch.full_like(F_ext, float("nan"))
+
+    def transport(a, b):
+        b.copy_(torch.from_numpy(oracle.transport_upwind(a.numpy(), T, dx, dt)))
+
+    def collide(v):
+        v.copy_(torch.from_numpy(np.stack([oracle.euler(p, c, dt) for c in v.numpy()])))
+
+    out = shard.lie_steps_sharded(F_ext, S, steps, transport, collide, group)
+    ref = oracle.inhomogeneous_lie(p, G, dx, dt, steps=steps)[start:start + n]
+    return out[1:n + 1].numpy(), ref
+
+
+def test_spatial_blocks_are_contiguous_and_balanced():
+    for M, world in ((11, 1), (11, 2), (11, 3), (64, 8), (8, 8)):
+        b = shard.spatial_blocks(M, world)
+        assert [s for s, _ in b] == list(np.cumsum([0] + [n for _, n in b])[:-1])
+        assert sum(n for _, n in b) == M and max(n for _, n in b) - min(n for _, n in b) <= 1
+    with pytest.raises(ValueError):
+        shard.spatial_blocks(3, 4)
+
+
+def test_split_lie_steps_single_rank_wraps_onto_itself():
+    got, ref = _halo_block(1, 0)
+    assert np.array_equal(got, ref)
+
+
+def _halo_rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world, init_method="tcp://127.0.0.1:%d" % port)
+    got, ref = _halo_block(world, rank)
+    dist.destroy_process_group()
+    with open(os.path.join(out_dir, "halo%d.json" % rank), "w") as f:
+        json.dump({"equal": bool(np.array_equal(got, ref)), "n": int(got.shape[0])}, f)
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_split_lie_steps_over_gloo_ranks_equal_the_global_run(tmp_path, world):
+    """Blocks of an 11-cell periodic grid on two and three gloo ranks, three Lie steps with halo
+    exchanges: every rank's cells equal the oracle's global run bit for bit."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    mp.spawn(_halo_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    total = 0
+    for r in range(world):
+        with open(tmp_path / ("halo%d.json" % r)) as f:
+            d = json.load(f)
+        assert d["equal"], r
+        total += d["n"]
+    assert total == 11
