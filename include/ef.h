@@ -266,6 +266,27 @@ ef_status ef_moments_entropy(ef_plan_t plan, const void *F_dev, const void *Q_de
 ef_status ef_transport_step(ef_plan_t plan, const void *F_in_dev, void *F_out_dev, int64_t ncells, double dx,
                             double dt, ef_stream_t stream);
 
+/* The entropic Fourier method on the classical form of the operator (the remark after eq. EFMk;
+ * kernel modes of eq. classical_hatB), 3D Maxwell molecules (B = 1/(4 pi)), FP64, for the grid
+ * sizes of Table 3 (Example 4).  B_hat(l, m) = 4 pi int_0^R r^2 sinc(c r |l+m|) sinc(c r |l-m|) dr
+ * with c = pi / (2L) (both sphere integrals in closed form), filtered by the modified Jackson filter
+ * of each axis (sigma_enabled = 0: no filter, the collocation method), and
+ *   Qh_k = sum_{l + m = k mod N} (Bs(l, m) - Bs(m, m)) Fh_l Fh_m
+ * is summed directly over mode pairs: the weight depends on the unaliased l + m, so the low-rank
+ * transforms of ef_collide do not apply.  O(N^6) work per cell.
+ * ef_classical_create: even N with 4 <= N <= 32, box half width L > 0, truncation radius R_tr
+ * (<= 0: the largest the classical form allows, 4L / (3 + sqrt 2)); tabulates B_hat on the host
+ * and allocates its device tables and work arrays (about 8 (3N^2 + 1)^2 bytes; 75 MB at N = 32).
+ * ef_classical_collide: F_dev, Q_dev device arrays of ncells cells of N^3 doubles (layout as
+ * ef_collide), not overlapping; cells are evaluated one after another on `stream`; calls on one
+ * object share its work arrays, so they must not run concurrently.  Errors: EF_ERR_INVALID_ARG
+ * for bad sizes or pointers, EF_ERR_OOM / EF_ERR_CUDA from the runtime. */
+typedef struct ef_classical_s *ef_classical_t;
+ef_status ef_classical_create(int N, double L, double R_tr, int sigma_enabled, ef_classical_t *out);
+ef_status ef_classical_collide(ef_classical_t c, const double *F_dev, double *Q_dev, int64_t ncells,
+                               ef_stream_t stream);
+ef_status ef_classical_destroy(ef_classical_t c);
+
 /* Streaming a batch that lives in host memory (no counterpart in the paper; the paper's method
  * is per cell).  The cells (sizes N_host[c], back to back as for ef_plan_create_batched) are cut
  * into nchunks contiguous chunks of about equal work, each with its own batched plan and CUDA

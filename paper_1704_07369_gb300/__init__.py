@@ -41,7 +41,8 @@ SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
            "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer",
            "ef_stream_plan_create", "ef_stream_plan_destroy", "ef_stream_plan_info", "ef_stream_euler_step",
-           "ef_stream_plan_status", "ef_transport_step", "ef_status_string", "ef_last_error")
+           "ef_stream_plan_status", "ef_transport_step", "ef_classical_create", "ef_classical_collide",
+           "ef_classical_destroy", "ef_status_string", "ef_last_error")
 EF_FEATURE_K = 6
 EF_FEATURE_STRIDE = 928
 
@@ -106,6 +107,9 @@ def lib():
         L.ef_stream_plan_status.argtypes = [vp, i32, i32]
         L.ef_moments_entropy.argtypes = [vp, vp, vp, vp, i64, vp]
         L.ef_transport_step.argtypes = [vp, vp, vp, i64, dbl, dbl, vp]
+        L.ef_classical_create.argtypes = [i32, dbl, dbl, i32, ctypes.POINTER(vp)]
+        L.ef_classical_collide.argtypes = [vp, vp, vp, i64, vp]
+        L.ef_classical_destroy.argtypes = [vp]
         L.ef_plan_status.argtypes = [vp, i32, i32]
         L.ef_plan_set_graph.argtypes = [vp, i32]
         L.ef_plan_info.argtypes = [vp, ctypes.POINTER(i64)]
@@ -318,6 +322,31 @@ class StreamPlan:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             lib().ef_stream_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Classical:
+    """Owning wrapper of an ``ef_classical_t``: the entropic Fourier method on the classical form of
+    the operator, 3D Maxwell molecules, FP64, summed directly over mode pairs (Table 3 sizes)."""
+
+    def __init__(self, N, L, R_tr=0.0, sigma_enabled=1):
+        self.handle = ctypes.c_void_p()
+        _check(lib().ef_classical_create(int(N), float(L), float(R_tr), int(sigma_enabled), ctypes.byref(self.handle)))
+        self.N = int(N)
+
+    def collide(self, F, Q, ncells=None, stream=None):
+        n = ncells if ncells is not None else F.numel() // self.N ** 3
+        _check(lib().ef_classical_collide(self.handle, _ptr(F), _ptr(Q), int(n), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ef_classical_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

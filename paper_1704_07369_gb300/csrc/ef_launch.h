@@ -57,6 +57,8 @@ size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paire
 cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
                            int occ, cudaStream_t s);
 void set_last_error(const char *msg);
+// the modified Jackson filter of one axis (eq. JacksonFilter2; sigma(-N/2) = 0), as the plans use it
+double jackson_filter(int N, int k, bool enabled);
 
 // low-mode features (ef_features_f32.cu / ef_features_f64.cu): nf = 1 or 2 fields; the grid is
 // capped at the CTAs that fit on the device at once (persistent over cells)

@@ -1113,6 +1113,8 @@ cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int gri
 
 void set_last_error(const char *msg) { g_last_error = msg; }
 
+double jackson_filter(int N, int k, bool enabled) { return jackson(N, k, enabled); }
+
 }  // namespace ef
 
 extern "C" {
