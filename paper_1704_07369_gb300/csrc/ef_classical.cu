@@ -214,9 +214,13 @@ ef_status ef_classical_create(int N, double L, double R_tr, int sigma_enabled, e
 ef_status ef_classical_destroy(ef_classical_t c)
 {
     if (!c) return cfail(EF_ERR_INVALID_ARG, "null classical-form object");
-    cudaSetDevice(c->device);
+    int cur = -1;
+    const bool had = cudaGetDevice(&cur) == cudaSuccess;
+    const int dev = c->device;
+    cudaSetDevice(dev);                 // free on the object's device, then restore the caller's
     cudaDeviceSynchronize();
     cfree(c);
+    if (had && cur != dev) cudaSetDevice(cur);
     return EF_OK;
 }
 

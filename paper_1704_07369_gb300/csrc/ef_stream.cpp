@@ -127,9 +127,13 @@ ef_status ef_stream_plan_create(int d, int64_t ncells, const int *N_host, double
 ef_status ef_stream_plan_destroy(ef_stream_plan_t sp)
 {
     if (!sp) return sp_fail(EF_ERR_INVALID_ARG, "null stream plan");
-    cudaSetDevice(sp->device);
+    int cur = -1;
+    const bool had = cudaGetDevice(&cur) == cudaSuccess;
+    const int dev = sp->device;
+    cudaSetDevice(dev);                 // free on the plan's device, then restore the caller's
     cudaDeviceSynchronize();
     sp_free(sp);
+    if (had && cur != dev) cudaSetDevice(cur);
     return EF_OK;
 }
 
