@@ -16,7 +16,9 @@ After the timed steps (N = 1 only) the "surrogate" object compares the learned s
 plain operator on 16384-cell batches (N = 32, hard-sphere and Maxwell kernels): throughput of both
 on the same resident batch, and the accuracy of the band the surrogate path delivers, under three
 audit policies (none; any audited miss sends the whole batch to the plain operator; more than 5%
-of audited cells missing does).  --no-surrogate skips it.
+of audited cells missing does).  --no-surrogate skips it.  The "hbm_kernels" object then times the
+library's HBM-bound kernels (moments / entropy and free transport) on resident N = 32 batches
+against the measured HBM copy rate; --no-kernels skips it.
 
 --impl reference times the FP64 CPU oracle (direct O(R N^6) sum of the paper's operator) on the
 host cores, on a bounded sample of the same workload.
@@ -368,12 +370,72 @@ def run_ours(args, world, rank, local):
             "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch * args.steps}
     if not args.no_surrogate and world == 1:
         line["surrogate"] = surrogate_leg(args, device)
+    if not args.no_kernels and world == 1:
+        line["hbm_kernels"] = hbm_kernels_leg(device)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     elif not args.no_cpu_baseline:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
     return 0
+
+
+# -------------------------------------------------------------- HBM-bound kernels ----------
+
+def _measured_hbm_gbs():
+    """The measured HBM copy rate of MEASURED_PEAKS.json (GB/s), else the 6800 GB/s fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f).get("hbm_gbs", 6800.0))
+    return 6800.0
+
+
+def hbm_kernels_leg(device):
+    """Device time and bandwidth of the library's HBM-bound kernels on resident FP32 N = 32 cells
+    (CUDA events, 3 warm-up and 20 timed calls on the current stream; inputs far larger than L2):
+    ef_moments_entropy on 16384 cells (F alone, then F and Q) and ef_transport_step on 4096
+    cells.  Bytes are the algorithmic ones: each input value read once, each output written once."""
+    import torch
+    import paper_1704_07369_gb300 as ef
+    try:
+        peak = _measured_hbm_gbs()
+        plan = ef.Plan(3, 32, 8.0, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F32)
+        cell = 32 ** 3
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+        def timed(fn, reps=20):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ev[0].record()
+            for _ in range(reps):
+                fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            return ev[0].elapsed_time(ev[1]) / reps
+
+        out = {}
+        n = 16384
+        F = torch.rand(n, 32, 32, 32, device=device) + 0.01
+        Q = torch.rand_like(F) - 0.5
+        mom = torch.zeros(n, ef.EF_DIAG_STRIDE, dtype=torch.float64, device=device)
+        for name, q in (("moments_F", None), ("moments_FQ", Q)):
+            ms = timed(lambda: plan.moments(F, q, mom, ncells=n))
+            by = n * cell * 4 * (1 if q is None else 2) + n * ef.EF_DIAG_STRIDE * 8
+            out[name] = {"cells": n, "ms": ms, "GBps": by / ms / 1e6, "frac_of_measured_hbm": by / ms / 1e6 / peak}
+        del Q, mom
+        n = 4096
+        G = torch.empty(n, 32, 32, 32, device=device)
+        ms = timed(lambda: plan.transport(F[:n], G, 0.25, 0.01, ncells=n))
+        by = 2 * n * cell * 4
+        out["transport"] = {"cells": n, "ms": ms, "GBps": by / ms / 1e6, "frac_of_measured_hbm": by / ms / 1e6 / peak}
+        out["status"] = int(plan.status(sync=1, reset=1))
+        del F, G
+        torch.cuda.empty_cache()
+        return out
+    except Exception as exc:          # reported, never fatal to the bench line
+        return {"error": "%s: %s" % (type(exc).__name__, exc)}
 
 
 # ------------------------------------------------------------------ surrogate leg ----------
@@ -511,6 +573,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-kernels", action="store_true", help="skip the HBM-bound kernels' timings")
     ap.add_argument("--chunks", type=int, default=8, help="chunks of the streamed end-to-end leg")
     ap.add_argument("--strong", action="store_true",
                     help="split one --cells batch over the ranks (default: a batch per rank)")
