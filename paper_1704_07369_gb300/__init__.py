@@ -433,6 +433,9 @@ class Plan:
             (self.rk3 if rk3 else self.euler)(b, dt, 1, d, ncells=n, stream=stream)
             a, b = b, a
         if a is not F:
+            if not F.is_cuda:
+                F.copy_(a)
+                return
             if stream is None:
                 s = torch.cuda.current_stream()
             elif isinstance(stream, int):
