@@ -2,7 +2,9 @@
 
 TEST INFRASTRUCTURE (same rules as the rest of ``oracle/``).
 
-x -> relu(W_0 x + b_0) -> ... -> W_{L-1} h + b_{L-1}; loss = sum_j w_j (y_j - t_j)^2 / (B n_out).
+x -> relu(W_0 x + b_0) -> ... -> W_{L-1} h + b_{L-1};
+loss = sum_b r_b sum_j w_j (y_bj - t_bj)^2 / (B n_out), with per-output weights w (wmask) and
+per-sample weights r (rowweight), both 1 when not given.
 With ``bf16=True`` the values the library stores in bfloat16 are rounded the same way (round to
 nearest even): weights to bf16; every layer input (features and hidden activations) to the split
 pair bf16(a) + bf16(a - bf16(a)); output and hidden gradients to bf16.  The comparison then isolates
@@ -57,16 +59,18 @@ def forward(layers, X, bf=True):
     return h, (cache, pres)
 
 
-def loss_and_grads(layers, X, T, nout, wmask=None, bf=True):
-    """MSE loss over the first nout outputs and the gradients [(dW, db)] (same shapes as layers)."""
+def loss_and_grads(layers, X, T, nout, wmask=None, bf=True, rowweight=None):
+    """Weighted MSE loss over the first nout outputs and the gradients [(dW, db)] (same shapes as
+    layers); wmask weights the outputs, rowweight the samples."""
     r = bf16 if bf else (lambda v: np.asarray(v, dtype=np.float64))
     y, (acts, pres) = forward(layers, X, bf)
     B = X.shape[0]
     w = np.ones(nout) if wmask is None else np.asarray(wmask, dtype=np.float64)
+    r_b = np.ones(B) if rowweight is None else np.asarray(rowweight, dtype=np.float64)
     d = y[:, :nout] - T[:, :nout]
-    loss = float((w * d * d).sum() / (B * nout))
+    loss = float((r_b[:, None] * w * d * d).sum() / (B * nout))
     g = np.zeros_like(y)
-    g[:, :nout] = 2.0 * w * d / (B * nout)
+    g[:, :nout] = 2.0 * r_b[:, None] * w * d / (B * nout)
     g = r(g)
     grads = [None] * len(layers)
     for li in range(len(layers) - 1, -1, -1):

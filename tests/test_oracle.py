@@ -140,6 +140,42 @@ def test_dvm_form_equals_fourier_form(case):
     assert np.abs(Q.ravel() - Qp).max() <= 1e-13 * scale
 
 
+@pytest.mark.parametrize("d,N", [(2, 6), (2, 8), (2, 12), (2, 7), (3, 6), (3, 8), (3, 12)])
+def test_fft_helper_equals_direct_dft(d, N):
+    """The NumPy-FFT helper used for large grids (dft_fft, with the phase of the centred index
+    j = i - N/2) equals the direct sum of eq. DFT, and both equal the closed form of a point mass:
+    F = delta at j0 gives Fh_k = N^-d exp(-2 pi i k.j0 / N)."""
+    rng = np.random.default_rng(N + 10 * d)
+    F = rng.random((N,) * d)
+    a = oracle.dft(F)
+    b = oracle.dft_fft(F)
+    assert np.abs(a - b).max() <= 1e-15 * np.abs(F).sum()
+    i0 = tuple(int(x) for x in rng.integers(0, N, d))
+    D = np.zeros((N,) * d)
+    D[i0] = 1.0
+    k = [((np.arange(N) + N // 2) % N) - N // 2] * d       # k in FFT order: 0..N/2-1, -N/2..-1
+    kk = np.meshgrid(*k, indexing="ij")
+    j0 = [i - N // 2 for i in i0]
+    exact = np.exp(-2j * np.pi * sum(kk[a_] * j0[a_] for a_ in range(d)) / N) / N ** d
+    assert np.abs(oracle.dft(D) - exact).max() <= 1e-15
+    assert np.abs(oracle.dft_fft(D) - exact).max() <= 1e-15
+
+
+@pytest.mark.parametrize("case", [dict(d=2, N=12, kernel=0, R=8), dict(d=3, N=8, kernel=1, R=16),
+                                  dict(d=3, N=6, kernel=2, R=16, J=3)])
+def test_sampled_evaluators_equal_the_full_sum(case):
+    """The point evaluators used at large N (rank-separated form, with Fh from the direct DFT or from
+    the FFT helper) equal the direct double sum of eq. Qsk at every grid point."""
+    rng = np.random.default_rng(11)
+    p = oracle.Params(T=8.0, **case)
+    F = rng.random((case["N"],) * case["d"]) + 0.05
+    Q = oracle.collide(p, F).ravel()
+    idx = np.arange(F.size)
+    scale = np.abs(Q).max()
+    assert np.abs(oracle.collide_points(p, F, idx) - Q).max() <= 1e-13 * scale
+    assert np.abs(oracle.collide_points_fft(p, F, idx) - Q).max() <= 1e-13 * scale
+
+
 def test_unfiltered_kernel_is_not_positive_fig1():
     """Fig. 1: 2D, B~ = 1/pi, R = 6, N = 32, z = (T/2, T/2): G takes negative values without the
     filter and is non-negative with it (Sec. 3.2.1 / 3.2.2)."""

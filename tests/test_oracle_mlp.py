@@ -1,6 +1,7 @@
 """Pin of the FP64 oracle MLP: its backpropagation (bf16 emulation off) equals central finite
 differences of its own forward pass, and its bf16 rounding matches the bfloat16 format."""
 import numpy as np
+import pytest
 
 from oracle import mlp
 
@@ -9,13 +10,15 @@ def _layers(rng, dims):
     return [(rng.normal(size=(o, i)) / np.sqrt(i), rng.normal(size=o) * 0.1) for i, o in zip(dims[:-1], dims[1:])]
 
 
-def test_backprop_matches_finite_differences():
+@pytest.mark.parametrize("use_rowweight", [False, True])
+def test_backprop_matches_finite_differences(use_rowweight):
     rng = np.random.default_rng(3)
     layers = _layers(rng, [7, 6, 5, 4])
     X = rng.normal(size=(5, 7))
     T = rng.normal(size=(5, 4))
     w = rng.uniform(0.5, 2.0, 3)
-    loss, grads = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False)
+    rw = rng.uniform(0.1, 3.0, 5) if use_rowweight else None
+    loss, grads = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False, rowweight=rw)
     eps = 1e-6
     for li, (W, b) in enumerate(layers):
         for arr, g in ((W, grads[li][0]), (b, grads[li][1])):
@@ -24,9 +27,9 @@ def test_backprop_matches_finite_differences():
                 idx = it.multi_index
                 old = arr[idx]
                 arr[idx] = old + eps
-                lp, _ = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False)
+                lp, _ = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False, rowweight=rw)
                 arr[idx] = old - eps
-                lm, _ = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False)
+                lm, _ = mlp.loss_and_grads(layers, X, T, 3, wmask=w, bf=False, rowweight=rw)
                 arr[idx] = old
                 assert abs((lp - lm) / (2 * eps) - g[idx]) <= 1e-7 * max(1.0, abs(g[idx]))
 
@@ -47,3 +50,24 @@ def test_split_precision_pair():
     assert np.max(np.abs(y - x) / np.abs(x)) <= 2.0 ** -16
     hi = mlp.bf16(x)
     assert np.all(mlp.bf16(y - hi) == y - hi)      # the low half is itself a bf16 value
+
+
+def test_rowweight_loss_is_the_weighted_mean_of_per_sample_losses():
+    """The per-sample weights scale each sample's squared error: the loss with weights r equals
+    sum_b r_b loss_b / B, where loss_b is the loss of the batch made of sample b alone (times 1)."""
+    rng = np.random.default_rng(5)
+    layers = _layers(rng, [4, 6, 3])
+    X = rng.normal(size=(6, 4))
+    T = rng.normal(size=(6, 3))
+    r = rng.uniform(0.0, 2.0, 6)
+    loss, _ = mlp.loss_and_grads(layers, X, T, 3, bf=False, rowweight=r)
+    singles = [mlp.loss_and_grads(layers, X[b:b + 1], T[b:b + 1], 3, bf=False)[0] for b in range(6)]
+    assert abs(loss - float(np.dot(r, singles)) / 6) <= 1e-14 * max(1.0, loss)
+    # zero weight on a sample removes its gradient contribution exactly
+    r0 = r.copy()
+    r0[2] = 0.0
+    _, g_all = mlp.loss_and_grads(layers, X, T, 3, bf=False, rowweight=r0)
+    keep = [b for b in range(6) if b != 2]
+    _, g_sub = mlp.loss_and_grads(layers, X[keep], T[keep], 3, bf=False, rowweight=r0[keep] * 5 / 6)
+    for (a, b_), (c, d) in zip(g_all, g_sub):
+        assert np.allclose(a, c, rtol=1e-12, atol=1e-15) and np.allclose(b_, d, rtol=1e-12, atol=1e-15)
