@@ -20,9 +20,11 @@
  *   loss term multiplies the grid value F_r (DVM form, eq. QCvr / eq. Qsr).
  * Memory: every F / Q / diag pointer is a DEVICE pointer owned by the caller, contiguous, of the
  *   plan's precision (float for EF_PREC_F32, double for EF_PREC_F64; diagnostics are always
- *   double); F and Q must start on a 16-byte boundary (EF_ERR_INVALID_ARG otherwise).  The plan owns its tables, workspace and status word.  No entry point allocates
- *   device memory, synchronises the device or blocks the host except ef_plan_create* /
- *   ef_plan_destroy and ef_plan_status(plan, 1).
+ *   double); F and Q must start on a 16-byte boundary (EF_ERR_INVALID_ARG otherwise).  The plan
+ *   owns its tables, workspaces and status word, all allocated by ef_plan_create* (and the SSP-RK3
+ *   stage buffers by ef_plan_reserve).  No other entry point of a plan allocates device memory,
+ *   synchronises the device or blocks the host, except ef_plan_destroy and ef_plan_status(plan, 1);
+ *   so the operations can be captured into a CUDA graph.
  * Streams: operations are enqueued on the given CUDA stream (0 = legacy default stream) and return
  *   immediately.  The plan's device must be current on the calling thread.
  * Errors: every function returns an ef_status; on failure nothing is launched and
@@ -121,10 +123,18 @@ ef_status ef_euler_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, doub
  * Each stage is a convex combination of forward Euler steps, so positivity carries over from the
  * Euler step under the same dt max nu <= 1.  diag_dev (nullable) receives, per step, the diagnostics
  * of the first stage ([step][cell][k] as for ef_euler_step: moments of F before the step).  The
- * plan keeps two batch-sized stage buffers, allocated on the first call (and grown, after a device
- * synchronisation, when a later call needs more).  F must be 16-byte aligned. */
+ * two batch-sized stage buffers come from ef_plan_reserve, which must have been called for at
+ * least ncells cells (EF_ERR_INVALID_ARG otherwise; nothing is launched).  F must be 16-byte
+ * aligned. */
 ef_status ef_rk3_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, double *diag_dev, int64_t ncells,
                       ef_stream_t stream);
+
+/* Allocate the plan's two SSP-RK3 stage buffers for batches of up to ncells cells (a batched plan:
+ * its whole batch; ncells 0 or the plan's count).  A set-up call like ef_plan_create: when the
+ * buffers must grow it synchronises the device, frees the old ones and allocates (EF_ERR_OOM if
+ * that fails); when they are already large enough it does nothing.  Call it before capturing
+ * ef_rk3_step into a CUDA graph. */
+ef_status ef_plan_reserve(ef_plan_t plan, int64_t ncells);
 
 /* ef_collide for callers that cannot allocate device memory when they evaluate the operator (a
  * host framework whose allocator owns all device memory, a real-time loop or callback where an
@@ -141,7 +151,10 @@ ef_status ef_rk3_step(ef_plan_t plan, void *F_dev, double dt, int nsteps, double
  *    different streams, race and must be serialised by the caller.
  *  - If one cell's cluster needs more scratch than the array holds (very large N in FP64), the
  *    call returns EF_ERR_UNSUPPORTED with the sizes in ef_last_error(); otherwise the launch
- *    uses as many clusters as fit and any ncells is accepted. */
+ *    uses as many clusters as fit and any ncells is accepted.
+ *  - The S/G accumulators always live in that array (global memory), with the plan's cluster
+ *    size, threads per CTA and prefetch choice; where ef_collide keeps them in shared memory,
+ *    this call can be slower than ef_collide. */
 ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void *Q_dev, int64_t ncells, ef_stream_t stream);
 
 /* Low-mode features of each cell: the discrete Fourier coefficients Fh_k = N^{-d} sum F E_{-k}
@@ -175,6 +188,12 @@ ef_status ef_mlp_destroy(ef_mlp_t mlp);
 /* info: [0] nin, [1] nhidden, [2] nlayers, [3] nout, [4] number of FP32 parameters (padded layout:
  * per layer W[out_p][in_p] then b[out_p]), [5] padded nin, [6] padded nout, [7] max batch. */
 ef_status ef_mlp_info(ef_mlp_t mlp, int64_t info[8]);
+
+/* The MLP's device status word, as ef_plan_status does for a plan: EF_OK, or EF_ERR_TIMEOUT when a
+ * tensor-core GEMM gave up one of its bounded mbarrier waits (that GEMM's outputs are then NaN and
+ * the work queued after it on the stream saw them).  sync = 1 synchronises the device and reads
+ * the word; sync = 0 returns the value last read.  reset = 1 clears it. */
+ef_status ef_mlp_status(ef_mlp_t mlp, int sync, int reset);
 
 /* Copy the FP32 parameters to (set = 0) or from (set = 1) a HOST buffer of info[4] floats. */
 ef_status ef_mlp_params(ef_mlp_t mlp, float *host, int set);
@@ -295,9 +314,11 @@ ef_status ef_classical_destroy(ef_classical_t c);
  * chunks run concurrently, so copies in both directions overlap the collision steps of other
  * chunks when F_host is page-locked (pageable memory works but serialises the copies).  diag_host
  * (nullable) receives nsteps * ncells * EF_DIAG_STRIDE doubles, [step][cell][k] as ef_euler_step
- * (a device buffer for them is allocated on the first call that needs it).  All work is ordered
- * after earlier work on `stream`, and later work on `stream` waits for it; the host buffers must
- * stay untouched until then. */
+ * (through a one-step device buffer allocated here, copied out after each step).  All work is
+ * ordered after earlier work on `stream`, and later work on `stream` waits for it; the host
+ * buffers must stay untouched until then.  ef_stream_euler_step allocates nothing and does not
+ * synchronise; if it fails part way, the chunks it already started are still joined into
+ * `stream` before it returns the error, so the same rule holds. */
 typedef struct ef_stream_plan_s *ef_stream_plan_t;
 ef_status ef_stream_plan_create(int d, int64_t ncells, const int *N_host, double L, ef_kernel kernel, int R,
                                 ef_precision prec, int nchunks, ef_stream_plan_t *out);

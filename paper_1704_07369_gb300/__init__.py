@@ -35,8 +35,8 @@ EF_DIAG_STRIDE = 10
 # every symbol include/ef.h declares
 SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
            "ef_collide", "ef_euler_step", "ef_rk3_step", "ef_moments_entropy", "ef_plan_status",
-           "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_collide_noalloc",
-           "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_params",
+           "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_plan_reserve", "ef_collide_noalloc",
+           "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_status", "ef_mlp_params",
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
            "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer",
@@ -87,6 +87,8 @@ def lib():
         L.ef_mlp_create.argtypes = [i32, i32, i32, i32, i64, ctypes.c_uint64, pp]
         L.ef_mlp_destroy.argtypes = [vp]
         L.ef_mlp_info.argtypes = [vp, ctypes.POINTER(i64)]
+        L.ef_mlp_status.argtypes = [vp, i32, i32]
+        L.ef_plan_reserve.argtypes = [vp, i64]
         L.ef_mlp_params.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_mlp_forward.argtypes = [vp, vp, i32, vp, i32, i64, vp]
         L.ef_mlp_grad.argtypes = [vp, vp, i32, vp, i32, vp, vp, i64, vp, vp, vp]
@@ -196,6 +198,10 @@ class MLP:
         _check(lib().ef_mlp_info(self.handle, info))
         self.nin, self.nhidden, self.nlayers, self.nout, self.nparams, self.ninp, self.noutp, self.max_batch = list(info)
 
+    def status(self, sync=1, reset=0):
+        """The MLP's device status word (EF_ERR_TIMEOUT if a GEMM gave up a bounded wait)."""
+        return lib().ef_mlp_status(self.handle, int(sync), int(reset))
+
     def params(self):
         import numpy as np
         out = np.zeros(self.nparams, dtype=np.float32)
@@ -289,6 +295,10 @@ class Surrogate:
 
 def ef_euler_step(plan, F, dt, nsteps, diag, ncells, stream=None):
     _check(lib().ef_euler_step(plan, _ptr(F), float(dt), int(nsteps), _ptr(diag), int(ncells), _stream(stream)))
+
+
+def ef_plan_reserve(plan, ncells):
+    _check(lib().ef_plan_reserve(plan, int(ncells)))
 
 
 def ef_rk3_step(plan, F, dt, nsteps, diag, ncells, stream=None):
@@ -408,8 +418,20 @@ class Plan:
     def euler(self, F, dt, nsteps=1, diag=None, ncells=None, stream=None):
         ef_euler_step(self.handle, F, dt, nsteps, diag, self._n(F, ncells), stream)
 
+    def reserve(self, ncells=None):
+        """Allocate the SSP-RK3 stage buffers for batches of up to ncells cells (a set-up call:
+        it may synchronise the device)."""
+        n = int(self.ncells if self.ncells is not None else ncells)
+        ef_plan_reserve(self.handle, n)
+        self._rk_cells = max(getattr(self, "_rk_cells", 0), n)
+
     def rk3(self, F, dt, nsteps=1, diag=None, ncells=None, stream=None):
-        ef_rk3_step(self.handle, F, dt, nsteps, diag, self._n(F, ncells), stream)
+        """SSP-RK3 steps; reserves the stage buffers first if this batch needs more than reserved
+        (call reserve() beforehand to keep this call free of allocation, e.g. before graph capture)."""
+        n = self._n(F, ncells)
+        if getattr(self, "_rk_cells", 0) < n:
+            self.reserve(n)
+        ef_rk3_step(self.handle, F, dt, nsteps, diag, n, stream)
 
     def moments(self, F, Q, out, ncells=None, stream=None):
         ef_moments_entropy(self.handle, F, Q, out, self._n(F, ncells), stream)

@@ -73,6 +73,7 @@ struct GemmArgs {
     bf16 *CbT;          // nullable bf16 transposed out [N][ldcbt]
     int ldcbt;
     int lo_off;         // > 0: also write the low halves a - bf16(a) at column / row + lo_off
+    int *status;        // nullable: device status word, EF_ERR_TIMEOUT (5) when a bounded wait gives up
 };
 
 // 4 warps in 2 x 2, each 32 x 32 (2 m16 x 4 n8 tiles).  M % 64 == N % 64 == K % 32 == 0.
@@ -189,8 +190,10 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const GemmArgs g)
 // tcgen05.commit); tcgen05.mma kind::f16 (M = 128, N = TN, K = 16) accumulates in tensor memory;
 // a stage is refilled once the MMAs that read it are complete, after the next block's MMAs have
 // been queued.  The epilogue reads the accumulator with tcgen05.ld (warp w owns tensor-memory
-// lanes, i.e. rows, 32w .. 32w+31).  Every mbarrier wait is bounded; a wait that gives up makes
-// the tile's outputs NaN instead of hanging.
+// lanes, i.e. rows, 32w .. 32w+31).  Every mbarrier wait is bounded.  A wait that gives up stops
+// the pipeline, records EF_ERR_TIMEOUT in the status word, waits (bounded) for the CTA's copies
+// and MMAs still in flight, and writes NaN for the tile without reading the accumulator; the
+// tensor memory is released in every case.
 constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
 
 __device__ __forceinline__ uint64_t tc_sdesc(uint32_t addr)
@@ -207,13 +210,22 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Bounded wait on one mbarrier phase: gives up after about one second of device time (or 2^26
+// polls), far beyond any wait of a healthy pipeline (microseconds).
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity)
 {
-    for (int it = 0; it < (1 << 24); ++it) {
+    uint64_t t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (int it = 0; it < (1 << 26); ++it) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done) : "r"(bar), "r"(parity) : "memory");
         if (done) return true;
+        if ((it & 1023) == 1023) {
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 1000000000ull) return false;
+        }
     }
     return false;
 }
@@ -254,7 +266,15 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__
 
     __shared__ int s_ok;
     if (tid == 0) {
+        // pend[st]: a TMA load into stage st was issued and its "full" phase not yet waited for;
+        // ncommit[st]: commits of MMAs reading stage st.  Each stage has at most one outstanding
+        // phase of either barrier (a stage is refilled only after both were waited for), so every
+        // parity below names one phase.
         bool ok = true;
+        bool pend[TC_STAGES];
+        uint32_t fph[TC_STAGES], eph[TC_STAGES];
+        int ncommit[TC_STAGES];
+        int kb_last = -1;                                // the last K block whose MMAs were committed
         auto issue = [&](int kb, int st) {
             const uint32_t a0 = sbase + st * STAGE, b0 = a0 + A_BYTES, bar = smem_u32(&full[st]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(STAGE));
@@ -262,15 +282,18 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__
                          ::"r"(a0), "l"(&tA), "r"(kb * TC_BK), "r"(m0), "r"(bar) : "memory");
             asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
                          ::"r"(b0), "l"(&tB), "r"(kb * TC_BK), "r"(n0), "r"(bar) : "memory");
+            pend[st] = true;
         };
-        uint32_t fph[TC_STAGES], eph[TC_STAGES];
         for (int i = 0; i < TC_STAGES; ++i) {
             fph[i] = eph[i] = 0;
+            pend[i] = false;
+            ncommit[i] = 0;
             if (i < nk) issue(i, i);
         }
-        for (int kb = 0; kb < nk && ok; ++kb) {
+        for (int kb = 0; kb < nk; ++kb) {
             const int st = kb % TC_STAGES;
-            ok = tc_wait(smem_u32(&full[st]), fph[st]);
+            if (!tc_wait(smem_u32(&full[st]), fph[st])) { ok = false; break; }
+            pend[st] = false;
             fph[st] ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
             const uint32_t a0 = sbase + st * STAGE, b0 = a0 + A_BYTES;
@@ -284,19 +307,27 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                          ::"r"(smem_u32(&empty[st])));
+            ++ncommit[st];
+            kb_last = kb;
             const int nxt = kb - 1 + TC_STAGES;          // refill the stage of kb - 1
             if (kb >= 1 && nxt < nk) {
                 const int pb = (kb - 1) % TC_STAGES;
-                ok = ok && tc_wait(smem_u32(&empty[pb]), eph[pb]);
+                if (!tc_wait(smem_u32(&empty[pb]), eph[pb])) { ok = false; break; }
                 eph[pb] ^= 1;
                 issue(nxt, pb);
             }
         }
-        if (ok) {            // the last commit covers every MMA; its parity counts the earlier waits
-            const int last = (nk - 1) % TC_STAGES;
-            int waited = 0;
-            for (int kb = last; kb + TC_STAGES < nk; kb += TC_STAGES) ++waited;
-            ok = tc_wait(smem_u32(&empty[last]), (uint32_t)(waited & 1));
+        // the last commit covers every MMA issued before it (tcgen05.commit tracks all prior
+        // asynchronous tcgen05 operations of this thread)
+        const int L = kb_last >= 0 ? kb_last % TC_STAGES : 0;
+        if (ok && kb_last >= 0) ok = tc_wait(smem_u32(&empty[L]), (uint32_t)((ncommit[L] - 1) & 1));
+        if (!ok) {
+            // a wait gave up: record it, then wait (again bounded) for this CTA's own copies and
+            // MMAs still in flight before the accumulator is released and the CTA exits
+            if (g.status) atomicCAS(g.status, 0, 5);     // EF_ERR_TIMEOUT
+            for (int i = 0; i < TC_STAGES; ++i)
+                if (pend[i]) tc_wait(smem_u32(&full[i]), fph[i]);
+            if (kb_last >= 0) tc_wait(smem_u32(&empty[L]), (uint32_t)((ncommit[L] - 1) & 1));
         }
         s_ok = ok ? 1 : 0;
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -309,12 +340,14 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const __grid_constant__
     const float bad = __int_as_float(0x7fc00000);
 #pragma unroll 1
     for (int c0 = 0; c0 < TN; c0 += 8) {
-        uint32_t r[8];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                     : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+        uint32_t r[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (ok) {            // CTA-uniform: after a give-up the accumulator is not read
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+        }
         const int col = n0 + c0;
         float v[8];
 #pragma unroll
@@ -593,6 +626,8 @@ struct ef_mlp_s {
     bf16 *dY = nullptr, *dYT = nullptr;
     int64_t step = 0;
     int device = 0;
+    int *status = nullptr;          // device status word (EF_ERR_TIMEOUT from a GEMM's bounded waits)
+    int h_status = 0;
 };
 
 namespace {
@@ -628,6 +663,7 @@ void mlp_free(ef_mlp_s *n)
     cudaFree(n->dW2);
     cudaFree(n->dY);
     cudaFree(n->dYT);
+    cudaFree(n->status);
     delete n;
 }
 
@@ -653,6 +689,7 @@ ef_status mlp_forward_packed(ef_mlp_s *n, int64_t B, float *Yout, int ldy, bool 
         g.CbT = (last || !keep_T) ? nullptr : n->actT[l];
         g.ldcbt = (int)B;
         g.lo_off = n->dout[l];
+        g.status = n->status;
         cudaError_t e = gemm(g, s);
         if (e != cudaSuccess) return cuda_err(e, "mlp gemm");
     }
@@ -728,6 +765,7 @@ ef_status ef_mlp_create(int nin, int nhidden, int nlayers, int nout, int64_t max
     alloc((void **)&n->dA, (size_t)max_batch * maxd * 4);
     alloc((void **)&n->dY, (size_t)max_batch * maxd * 2);
     alloc((void **)&n->dYT, (size_t)max_batch * maxd * 2);
+    alloc((void **)&n->status, sizeof(int));
     if (e != cudaSuccess) {
         mlp_free(n);
         return cuda_err(e, "mlp allocation");
@@ -750,6 +788,24 @@ ef_status ef_mlp_destroy(ef_mlp_t n)
     if (!n) return mlp_fail(EF_ERR_INVALID_ARG, "null mlp");
     mlp_free(n);
     return EF_OK;
+}
+
+ef_status ef_mlp_status(ef_mlp_t n, int sync, int reset)
+{
+    if (!n) return mlp_fail(EF_ERR_INVALID_ARG, "null mlp");
+    if (sync) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_err(e, "device synchronize");
+        e = cudaMemcpy(&n->h_status, n->status, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_err(e, "status read");
+        if (reset) {
+            e = cudaMemset(n->status, 0, sizeof(int));
+            if (e != cudaSuccess) return cuda_err(e, "status reset");
+        }
+    }
+    const int st = n->h_status;
+    if (reset) n->h_status = 0;
+    return (ef_status)st;
 }
 
 ef_status ef_mlp_info(ef_mlp_t n, int64_t info[8])
@@ -822,6 +878,7 @@ static ef_status mlp_grad_impl(ef_mlp_s *n, const float *X, int ldx, const float
         g.K = (int)B;
         g.Cf = n->dW2;
         g.ldcf = 2 * in;
+        g.status = n->status;
         e = gemm(g, s);
         if (e != cudaSuccess) return cuda_err(e, "mlp grad gemm");
         fold_split_kernel<<<grid_for((int64_t)out * in), 256, 0, s>>>(n->dW2, out, in, n->g + n->woff[l]);
@@ -838,6 +895,7 @@ static ef_status mlp_grad_impl(ef_mlp_s *n, const float *X, int ldx, const float
         h.K = out;
         h.Cf = n->dA;
         h.ldcf = in;
+        h.status = n->status;
         e = gemm(h, s);
         if (e != cudaSuccess) return cuda_err(e, "mlp backprop gemm");
         relu_back_kernel<<<grid_for(B * in), 256, 0, s>>>(n->dA, n->pre[l - 1], B, in, n->dY, n->dYT);

@@ -4,12 +4,14 @@
 // Some callers cannot call cudaMalloc at the point where they evaluate the operator: code that
 // runs inside a memory-budgeted host framework whose allocator owns all device memory, code that
 // is enqueued from callbacks or real-time loops where an allocation may block or fail, or code
-// that must not change the device's memory footprint after start-up.  ef_collide itself never
-// allocates on a uniform plan whose accumulators fit in shared memory, but it does keep its
-// scratch (the per-class cell queue and, for shapes whose S/G accumulators live in global memory,
-// that workspace) in plan-owned device buffers, one of which is allocated on first use.
-// This entry point instead takes all scratch from one file-scope static device array of fixed
-// size, which every GPU that loads the library holds until the process exits.
+// that must not change the device's memory footprint after start-up.  ef_collide keeps its
+// scratch (the forward-spectrum slots and, for shapes whose S/G accumulators live in global
+// memory, that workspace) in buffers the plan allocates when it is created.  This entry point
+// instead takes all scratch from one file-scope static device array of fixed size, which every
+// GPU that loads the library holds until the process exits.  It always keeps the S/G accumulators
+// in that array (global memory), whatever shape the plan's autotuner chose, with the plan's
+// cluster size, threads per CTA, occupancy variant and L1-prefetch choice; on shapes whose
+// accumulators ef_collide keeps in shared memory it can therefore be slower than ef_collide.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -129,6 +131,7 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
     a.status = v.status;
     a.counter = static_cast<unsigned long long *>(base);
     a.paired = v.paired;
+    a.prefetch = v.prefetch;
     e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, smem, v.occ, s);
     if (e != cudaSuccess) {
         ef::set_last_error(cudaGetErrorString(e));

@@ -678,24 +678,32 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
     return choose_shape(ds, cp, cp.ncells > 0 ? std::min<int64_t>(cp.ncells, 512) : 0);
 }
 
-ef_status ensure_sg(ef_plan_s *p, ClassPlan &cp, int grid_clusters)
+// Workspaces of one class for every cluster that can be resident at once (max_clusters, fixed by
+// the chosen launch shape): the forward-spectrum slots and, for the global-accumulator shapes, the
+// S/G slots.  Called once at plan creation, so that no operation allocates.
+ef_status alloc_workspaces(ef_plan_s *p, ClassPlan &cp)
 {
-    if (grid_clusters > cp.fh_slots) {
-        if (cp.d_fh) cudaFree(cp.d_fh);
-        cudaError_t e = cudaMalloc(&cp.d_fh, (size_t)grid_clusters * ef::collide_fh_bytes(p->desc.prec, p->desc.d, cp.N));
-        if (e != cudaSuccess) { cp.d_fh = nullptr; cp.fh_slots = 0; return cuda_fail(e, "spectrum workspace"); }
-        cp.fh_slots = grid_clusters;
-    }
+    const int slots_c = std::max(1, cp.max_clusters);
+    cudaError_t e = cudaMalloc(&cp.d_fh, (size_t)slots_c * ef::collide_fh_bytes(p->desc.prec, p->desc.d, cp.N));
+    if (e != cudaSuccess) { cp.d_fh = nullptr; return cuda_fail(e, "spectrum workspace"); }
+    cp.fh_slots = slots_c;
     if (!cp.sg_global) return EF_OK;
     const int N = cp.N, N1 = p->desc.d == 3 ? N : 1;
     const int64_t rows = (int64_t)cp.planes * N1;
-    const int64_t slots = (int64_t)grid_clusters * cp.cluster;
-    if (slots <= cp.sg_slots) return EF_OK;
-    if (cp.d_sg) cudaFree(cp.d_sg);
+    const int64_t slots = (int64_t)slots_c * cp.cluster;
     const size_t el = p->desc.prec == EF_PREC_F32 ? 4 : 8;
-    cudaError_t e = cudaMalloc(&cp.d_sg, (size_t)slots * 2 * rows * N * el);
-    if (e != cudaSuccess) { cp.d_sg = nullptr; cp.sg_slots = 0; return cuda_fail(e, "S/G workspace"); }
+    e = cudaMalloc(&cp.d_sg, (size_t)slots * 2 * rows * N * el);
+    if (e != cudaSuccess) { cp.d_sg = nullptr; return cuda_fail(e, "S/G workspace"); }
     cp.sg_slots = slots;
+    return EF_OK;
+}
+
+// The launch of grid_clusters clusters fits the workspaces made at plan creation (always true,
+// since the grid never exceeds max_clusters; checked so that a violation fails loudly).
+ef_status check_workspaces(const ClassPlan &cp, int grid_clusters)
+{
+    if (grid_clusters > cp.fh_slots || (cp.sg_global && (int64_t)grid_clusters * cp.cluster > cp.sg_slots))
+        return fail(EF_ERR_INVALID_ARG, "launch exceeds the plan's workspaces");
     return EF_OK;
 }
 
@@ -806,7 +814,7 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
         const int64_t n = p->batched ? cp.ncells : ncells;
         if (n <= 0) continue;
         const int grid = (int)std::min<int64_t>(n, cp.max_clusters);
-        ef_status st = ensure_sg(p, cp, grid);
+        ef_status st = check_workspaces(cp, grid);
         if (st != EF_OK) return st;
         cudaStream_t cs = s;
         if (multi) {
@@ -858,6 +866,8 @@ ef_status finish_plan(ef_plan_s *p)
     if (e != cudaSuccess) return cuda_fail(e, "status word");
     for (ClassPlan &cp : p->classes) {
         ef_status st = build_class(p->desc, cp);
+        if (st != EF_OK) return st;
+        st = alloc_workspaces(p, cp);
         if (st != EF_OK) return st;
     }
     if (p->classes.size() > 1) {
@@ -1018,14 +1028,6 @@ ef_status step(ef_plan_s *p, const void *F, void *Q, int64_t ncells, int mode, d
     if (!hit) {
         if (p->gexec) { cudaGraphExecDestroy(p->gexec); p->gexec = nullptr; }
         ef_status st;
-        // shapes and workspaces are settled outside the capture
-        for (ClassPlan &cp : p->classes) {
-            const int64_t n = p->batched ? cp.ncells : ncells;
-            if (n > 0) {
-                st = ensure_sg(p, cp, (int)std::min<int64_t>(n, cp.max_clusters));
-                if (st != EF_OK) return st;
-            }
-        }
         cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "graph capture");
         st = run(p, F, Q, ncells, mode, dt, diag, s);
@@ -1069,6 +1071,7 @@ bool plan_view(const ef_plan_s *p, PlanView *out)
     out->sg_global = cp.sg_global;
     out->nfeat = cp.nfeat;
     out->occ = cp.occ;
+    out->prefetch = cp.prefetch;
     out->smem = cp.smem;
     out->modes = cp.d_modes;
     out->L = p->desc.L;
@@ -1152,6 +1155,48 @@ ef_status ef_euler_step(ef_plan_t p, void *F, double dt, int nsteps, double *dia
     return EF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// values (grid points) in a batch of ncells cells of the plan (the whole batch for a batched plan)
+int64_t batch_values(const ef_plan_s *p, int64_t ncells)
+{
+    const Desc &ds = p->desc;
+    int64_t total = 0;
+    if (p->batched) {
+        for (const ClassPlan &cp : p->classes) total += cp.ncells * (int64_t)cp.N * cp.N * (ds.d == 3 ? cp.N : 1);
+    } else {
+        total = ncells * (int64_t)ds.N * ds.N * (ds.d == 3 ? ds.N : 1);
+    }
+    return total;
+}
+
+}  // namespace
+
+extern "C" {
+
+ef_status ef_plan_reserve(ef_plan_t p, int64_t ncells)
+{
+    if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
+    if (ncells < 0) return fail(EF_ERR_INVALID_ARG, "ncells < 0");
+    if (p->batched && ncells != 0 && ncells != p->ncells) return fail(EF_ERR_INVALID_ARG, "ncells differs from the batched plan");
+    ef_status st = check_device(p);
+    if (st != EF_OK) return st;
+    const size_t el = p->desc.prec == EF_PREC_F32 ? 4 : 8;
+    const int64_t total = batch_values(p, p->batched ? p->ncells : ncells);
+    const size_t half = ((size_t)total * el + 255) / 256 * 256;
+    if (2 * half <= p->rk_bytes) return EF_OK;
+    cudaError_t e = cudaDeviceSynchronize();             // the old buffers may still be in use
+    if (e == cudaSuccess && p->d_rk) e = cudaFree(p->d_rk);
+    p->d_rk = nullptr;
+    p->rk_bytes = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_rk, 2 * half);
+    if (e != cudaSuccess) { p->d_rk = nullptr; return cuda_fail(e, "SSP-RK3 stage buffers"); }
+    p->rk_bytes = 2 * half;
+    return EF_OK;
+}
+
 ef_status ef_rk3_step(ef_plan_t p, void *F, double dt, int nsteps, double *diag, int64_t ncells, ef_stream_t stream)
 {
     if (!p) return fail(EF_ERR_INVALID_ARG, "null plan");
@@ -1164,24 +1209,12 @@ ef_status ef_rk3_step(ef_plan_t p, void *F, double dt, int nsteps, double *diag,
     ef_status st = check_device(p);
     if (st != EF_OK) return st;
     const Desc &ds = p->desc;
-    int64_t total = 0;                                   // values in the batch
-    if (p->batched) {
-        for (const ClassPlan &cp : p->classes)
-            total += cp.ncells * (int64_t)cp.N * cp.N * (ds.d == 3 ? cp.N : 1);
-    } else {
-        total = ncells * (int64_t)ds.N * ds.N * (ds.d == 3 ? ds.N : 1);
-    }
+    const int64_t total = batch_values(p, ncells);
     const size_t el = ds.prec == EF_PREC_F32 ? 4 : 8;
     const size_t half = ((size_t)total * el + 255) / 256 * 256;
-    if (2 * half > p->rk_bytes) {
-        cudaError_t e = cudaDeviceSynchronize();          // the old buffers may still be in use
-        if (e == cudaSuccess && p->d_rk) e = cudaFree(p->d_rk);
-        p->d_rk = nullptr;
-        p->rk_bytes = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&p->d_rk, 2 * half);
-        if (e != cudaSuccess) return cuda_fail(e, "RK3 stage buffers");
-        p->rk_bytes = 2 * half;
-    }
+    if (2 * half > p->rk_bytes)
+        return fail(EF_ERR_INVALID_ARG, "SSP-RK3 stage buffers too small for " + std::to_string(ncells) +
+                                            " cells: call ef_plan_reserve(plan, ncells) first");
     void *A = p->d_rk, *B = static_cast<unsigned char *>(p->d_rk) + half;
     cudaStream_t s = (cudaStream_t)stream;
     const int prec = ds.prec == EF_PREC_F32 ? 0 : 1;

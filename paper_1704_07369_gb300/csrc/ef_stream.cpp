@@ -26,8 +26,7 @@ struct ef_stream_plan_s {
     };
     std::vector<Chunk> chunks;
     void *F_dev = nullptr;
-    double *diag_dev = nullptr;
-    int64_t diag_steps = 0;            // capacity of diag_dev in steps
+    double *diag_dev = nullptr;        // one step's diagnostics of the whole batch (made at create)
     cudaEvent_t fork = nullptr;
     int device = 0;
 };
@@ -119,6 +118,7 @@ ef_status ef_stream_plan_create(int d, int64_t ncells, const int *N_host, double
     }
     e = cudaEventCreateWithFlags(&sp->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&sp->F_dev, (size_t)elem * sp->el);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&sp->diag_dev, (size_t)ncells * EF_DIAG_STRIDE * sizeof(double));
     if (e != cudaSuccess) { sp_free(sp); return sp_cuda(e, "stream plan buffers"); }
     *out = sp;
     return EF_OK;
@@ -159,39 +159,44 @@ ef_status ef_stream_euler_step(ef_stream_plan_t sp, void *F_host, double dt, int
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev != sp->device) return sp_fail(EF_ERR_INVALID_ARG, "the stream plan's device is not current");
-    if (diag_host && nsteps > sp->diag_steps) {
-        e = cudaDeviceSynchronize();                  // the old buffer may still be in use
-        if (e == cudaSuccess) e = cudaFree(sp->diag_dev);
-        sp->diag_dev = nullptr;
-        sp->diag_steps = 0;
-        if (e == cudaSuccess) e = cudaMalloc((void **)&sp->diag_dev, (size_t)nsteps * sp->ncells * EF_DIAG_STRIDE * sizeof(double));
-        if (e != cudaSuccess) return sp_cuda(e, "stream plan diagnostics buffer");
-        sp->diag_steps = nsteps;
-    }
     cudaStream_t cs = (cudaStream_t)stream;
     e = cudaEventRecord(sp->fork, cs);
     if (e != cudaSuccess) return sp_cuda(e, "fork");
     unsigned char *Fh = static_cast<unsigned char *>(F_host);
     unsigned char *Fd = static_cast<unsigned char *>(sp->F_dev);
     const size_t row = EF_DIAG_STRIDE * sizeof(double);
+    size_t started = 0;                                // chunks with work enqueued on their stream
+    ef_status st = EF_OK;
     for (auto &c : sp->chunks) {
         e = cudaStreamWaitEvent(c.s, sp->fork, 0);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(Fd + c.e0 * sp->el, Fh + c.e0 * sp->el, c.ne * sp->el, cudaMemcpyHostToDevice, c.s);
-        if (e != cudaSuccess) return sp_cuda(e, "upload");
-        // chunk diagnostics: [step][chunk cell][k], contiguous per chunk in the device buffer
-        double *dd = diag_host ? sp->diag_dev + (size_t)nsteps * c.c0 * EF_DIAG_STRIDE : nullptr;
-        ef_status st = ef_euler_step(c.plan, Fd + c.e0 * sp->el, dt, nsteps, dd, c.nc, (ef_stream_t)c.s);
-        if (st != EF_OK) return st;
+        if (e != cudaSuccess) { st = sp_cuda(e, "fork wait"); break; }
+        ++started;
+        e = cudaMemcpyAsync(Fd + c.e0 * sp->el, Fh + c.e0 * sp->el, c.ne * sp->el, cudaMemcpyHostToDevice, c.s);
+        if (e != cudaSuccess) { st = sp_cuda(e, "upload"); break; }
+        // one step at a time: the chunk's slice of the one-step diagnostics buffer is copied out
+        // on the chunk's stream before the next step overwrites it
+        double *dd = diag_host ? sp->diag_dev + (size_t)c.c0 * EF_DIAG_STRIDE : nullptr;
+        for (int k = 0; k < nsteps && st == EF_OK; ++k) {
+            st = ef_euler_step(c.plan, Fd + c.e0 * sp->el, dt, 1, dd, c.nc, (ef_stream_t)c.s);
+            if (st == EF_OK && diag_host) {
+                e = cudaMemcpyAsync(diag_host + ((size_t)k * sp->ncells + c.c0) * EF_DIAG_STRIDE, dd, c.nc * row,
+                                    cudaMemcpyDeviceToHost, c.s);
+                if (e != cudaSuccess) st = sp_cuda(e, "diagnostics download");
+            }
+        }
+        if (st != EF_OK) break;
         e = cudaMemcpyAsync(Fh + c.e0 * sp->el, Fd + c.e0 * sp->el, c.ne * sp->el, cudaMemcpyDeviceToHost, c.s);
-        for (int k = 0; e == cudaSuccess && diag_host && k < nsteps; ++k)
-            e = cudaMemcpyAsync(diag_host + ((size_t)k * sp->ncells + c.c0) * EF_DIAG_STRIDE,
-                                dd + (size_t)k * c.nc * EF_DIAG_STRIDE, c.nc * row, cudaMemcpyDeviceToHost, c.s);
-        if (e == cudaSuccess) e = cudaEventRecord(c.done, c.s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c.done, 0);
-        if (e != cudaSuccess) return sp_cuda(e, "download");
+        if (e != cudaSuccess) { st = sp_cuda(e, "download"); break; }
     }
-    return EF_OK;
+    // join every chunk that has work enqueued into the caller's stream, on success and on an error
+    // part way (so that F_host and diag_host are free for reuse once `stream` has completed)
+    for (size_t i = 0; i < started; ++i) {
+        auto &c = sp->chunks[i];
+        e = cudaEventRecord(c.done, c.s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c.done, 0);
+        if (e != cudaSuccess && st == EF_OK) st = sp_cuda(e, "join");
+    }
+    return st;
 }
 
 ef_status ef_stream_plan_status(ef_stream_plan_t sp, int sync, int reset)

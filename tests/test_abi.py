@@ -55,6 +55,35 @@ def test_host_side_argument_checks():
     assert lib.ef_classical_create(16, 8.0, 0.0, 1, None) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_classical_collide(None, None, None, 1, None) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_classical_destroy(None) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_plan_reserve(None, 4) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_mlp_status(None, 0, 0) == ef.EF_ERR_INVALID_ARG
+    assert lib.ef_status_string(ef.EF_ERR_TIMEOUT) == b"EF_ERR_TIMEOUT"
+
+
+def test_no_operation_allocates_or_synchronises():
+    """The operations of a plan take every buffer from the plan (made at creation or by
+    ef_plan_reserve): no allocation, free or device synchronisation inside them.  Checked on the
+    source of the operation bodies: every cudaMalloc / cudaFree / cudaDeviceSynchronize sits in a
+    create, reserve, destroy, status, autotune or table-building function."""
+    allowed = re.compile(r"^(ef_plan_create\w*|ef_plan_reserve|ef_plan_destroy|ef_plan_status|ef_mlp_status|"
+                         r"ef_mlp_create|ef_mlp_destroy|ef_mlp_params|ef_surrogate_create|ef_surrogate_destroy|"
+                         r"ef_surrogate_stats|ef_stream_plan_create|ef_stream_plan_destroy|ef_classical_create|"
+                         r"ef_classical_destroy|choose_shape|upload_table|build_class|alloc_workspaces|"
+                         r"destroy_plan|finish_plan|cfree|\w*_free)$")
+    csrc = os.path.join(ROOT, "paper_1704_07369_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if not fn.endswith((".cpp", ".cu")):
+            continue
+        with open(os.path.join(csrc, fn)) as f:
+            lines = f.read().split("\n")
+        func = None
+        for ln in lines:
+            m = re.match(r"^(?:static\s+)?[A-Za-z_][\w:<>\s\*&]*?\b(\w+)\s*\([^;]*$", ln)
+            if m and not ln.startswith((" ", "\t", "#", "//")) and m.group(1) not in ("if", "for", "while", "switch"):
+                func = m.group(1)
+            code = ln.split("//")[0]
+            if re.search(r"\b(cudaMalloc|cudaFree|cudaDeviceSynchronize|cudaMallocAsync)\s*\(", code):
+                assert func is not None and allowed.match(func), (fn, func, ln.strip())
 
 
 def test_oracle_is_not_on_the_product_path():

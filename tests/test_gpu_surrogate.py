@@ -125,6 +125,51 @@ def test_mlp_forward_and_gradients_match_oracle():
         assert np.sqrt(((gb - db) ** 2).sum() / (db ** 2).sum()) <= 2e-3
 
 
+def test_mlp_rowweight_gradients_and_exact_fp64_bound():
+    """Per-sample loss weights (rowweight, as the surrogate's training uses them) against the oracle
+    MLP with the same weights and the library's bf16 roundings; and the GPU against EXACT FP64
+    backpropagation (no roundings), within the bound the bf16 format implies: with unit roundoff
+    u = 2^-8, each layer rounds its weights and (backward) its gradient signal once, so to first
+    order the outputs are within nl u and the gradients within 2 nl u (relative, L2) of exact."""
+    rng = np.random.default_rng(12)
+    nin, nh, nl, nout, B = 96, 128, 3, 80, 256
+    net = ef.MLP(nin, nh, nl, nout, B, seed=21)
+    layers = omlp.unpack(net.params(), net.layout())
+    X = rng.normal(size=(B, nin)).astype(np.float32)
+    T = rng.normal(size=(B, nout)).astype(np.float32)
+    rw = rng.uniform(0.2, 3.0, B).astype(np.float32)
+    Xd, Td, rwd = (torch.tensor(a, device="cuda") for a in (X, T, rw))
+    Y = torch.zeros(B, net.noutp, device="cuda")
+    net.forward(Xd, Y, B)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(net.nparams, device="cuda")
+    net.grad(Xd, Td, B, loss, grad, rowweight=rwd)
+    torch.cuda.synchronize()
+    assert net.status() == ef.EF_OK
+    Xp = np.zeros((B, net.ninp))
+    Xp[:, :nin] = X
+    gh = grad.cpu().numpy()
+    u = 2.0 ** -8
+
+    def rel(a, b):
+        return np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
+
+    # same roundings: accumulation order only
+    l_bf, g_bf = omlp.loss_and_grads(layers, Xp, T.astype(np.float64), nout, bf=True, rowweight=rw)
+    assert abs(loss.item() - l_bf) <= 1e-4 * l_bf
+    for (woff, o, i, boff), (dW, db) in zip(net.layout(), g_bf):
+        assert rel(gh[woff:woff + o * i].reshape(o, i), dW) <= 2e-3
+        assert rel(gh[boff:boff + o], db) <= 2e-3
+    # exact FP64
+    y_ex, _ = omlp.forward(layers, Xp, bf=False)
+    assert rel(Y.cpu().numpy(), y_ex) <= nl * u
+    l_ex, g_ex = omlp.loss_and_grads(layers, Xp, T.astype(np.float64), nout, bf=False, rowweight=rw)
+    assert abs(loss.item() - l_ex) <= 2 * nl * u * l_ex
+    for (woff, o, i, boff), (dW, db) in zip(net.layout(), g_ex):
+        assert rel(gh[woff:woff + o * i].reshape(o, i), dW) <= 2 * nl * u
+        assert rel(gh[boff:boff + o], db) <= 2 * nl * u
+
+
 def test_mlp_tcgen05_shapes_match_oracle():
     """A batch of 152 x 128 rows: the forward products and the input-gradient products then run on
     the tcgen05 kernel (N tiles of 256 and 192); outputs, loss and gradients against the FP64
