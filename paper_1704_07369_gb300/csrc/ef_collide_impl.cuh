@@ -46,13 +46,6 @@ __host__ __device__ constexpr bool occ2_built()
 }
 
 template <typename T>
-__device__ __forceinline__ void sincospi_t(T x, T *s, T *c);
-template <>
-__device__ __forceinline__ void sincospi_t<float>(float x, float *s, float *c) { sincospif(x, s, c); }
-template <>
-__device__ __forceinline__ void sincospi_t<double>(double x, double *s, double *c) { sincospi(x, s, c); }
-
-template <typename T>
 __device__ __forceinline__ T log_t(T x);
 template <>
 __device__ __forceinline__ float log_t<float>(float x) { return logf(x); }
@@ -90,7 +83,7 @@ __device__ __forceinline__ void record_status(int *status, int code)
 // z = IFFT(R0) + i IFFT(R1) (unscaled, inverse sign): the two-for-one inverse of c2r_pair, built
 // straight from shared memory so that no half-spectrum copy lives in registers.
 template <int N, typename T>
-__device__ __forceinline__ void c2r_rows_from(const C2<T> *R0, const C2<T> *R1, C2<T> (&z)[N], const C2<T> *tw)
+__device__ __forceinline__ void c2r_rows_from(const C2<T> *R0, const C2<T> *R1, C2<T> (&z)[N])
 {
     z[0] = C2<T>{R0[0].x, R1[0].x};
 #pragma unroll
@@ -100,7 +93,19 @@ __device__ __forceinline__ void c2r_rows_from(const C2<T> *R0, const C2<T> *R1, 
         z[N - k] = C2<T>{x0.x + x1.y, x1.x - x0.y};
     }
     z[N / 2] = C2<T>{R0[N / 2].x, R1[N / 2].x};
-    fft<N, 1, N>(z, tw);
+    fft<N, 1, N>(z);
+}
+
+// Row stride (complex values) of one axis-0 plane in a spectral slab.  The FP32 paired pencil
+// scatter stores 16 bytes per lane, even lanes into plane z and odd lanes into plane z + 1: a
+// plane stride of 8 mod 16 complex values puts the two halves of a quarter warp on different
+// banks (a multiple of 16 would make every store a two-way bank conflict).
+template <typename T, int D, int N>
+__host__ __device__ constexpr int slab_stride()
+{
+    constexpr int NP = ((D == 3) ? N : 1) * (N / 2 + 1);
+    if constexpr (sizeof(T) == 4 && NP % 2 == 0) return NP + ((8 - NP % 16) + 16) % 16;
+    else return NP;
 }
 
 // shared-memory bytes of one CTA (must match the carve-up in the kernel).  Paired mode holds two
@@ -108,14 +113,12 @@ __device__ __forceinline__ void c2r_rows_from(const C2<T> *R0, const C2<T> *R1, 
 template <typename T, int D, int N>
 __host__ __device__ constexpr size_t smem_bytes_for(int planes, int sg_global, int paired)
 {
-    constexpr int H = N / 2 + 1;
     constexpr int N1 = (D == 3) ? N : 1;
-    size_t is = (size_t)(paired ? 2 : 1) * planes * N1 * H * sizeof(C2<T>);
+    size_t is = (size_t)(paired ? 2 : 1) * planes * slab_stride<T, D, N>() * sizeof(C2<T>);
     size_t sg = sg_global ? 0 : (size_t)(paired ? 1 : 2) * planes * N1 * N * sizeof(T);
     sg = (sg + 15) / 16 * 16;
-    size_t tw = (size_t)N * sizeof(C2<T>);
     size_t part = (32 + 1) * kDiag * sizeof(double);
-    return is + sg + tw + part + 16;        // + the cluster's current cell index and a flag
+    return is + sg + part + 16;             // + the cluster's current cell index and a flag
 }
 
 // Per-cell diagnostics of one thread (FP64 sums of per-row FP32/FP64 partial sums).
@@ -283,8 +286,12 @@ __device__ __forceinline__ void ld_cluster(uint32_t a, C2<double> &v)
 // lanes 2j and 2j+1 hold the adjacent pencils p, p+1 (p even); one shuffle per z pair lets each
 // lane write both pencils of one z as a single 16-byte store, halving the number of (mostly
 // remote, distributed shared memory) store transactions.
+// owner CTA and local plane of axis-0 index z, for planes-per-CTA P with pm = floor((2^32 - 1) / P) + 1:
+// exact for z < 2^16 (a multiply-high instead of an integer division)
+__device__ __forceinline__ int plane_owner(int z, unsigned pm) { return (int)__umulhi((unsigned)z, pm); }
+
 template <typename T, int N, bool WIDE>
-__device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab, int P, int NP, int pencil,
+__device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab, int P, unsigned pm, int NP, int pencil,
                                                unsigned mask)
 {
     const uint32_t base = smem_u32addr(slab);
@@ -300,14 +307,14 @@ __device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab,
             const int z = odd ? z0 + 1 : z0;
             const C2<T> lo = odd ? recv : v[z0];
             const C2<T> hi = odd ? v[z0 + 1] : recv;
-            const int owner = z / P, zl = z - owner * P;
+            const int owner = plane_owner(z, pm), zl = z - owner * P;
             const uint32_t dst = cluster_map(base + (uint32_t)((zl * NP + pbase) * sizeof(C2<T>)), owner);
             st_cluster(dst, make_float4(lo.x, lo.y, hi.x, hi.y));
         }
     } else {
 #pragma unroll
         for (int z = 0; z < N; ++z) {
-            const int owner = z / P, zl = z - owner * P;
+            const int owner = plane_owner(z, pm), zl = z - owner * P;
             st_cluster(cluster_map(base + (uint32_t)((zl * NP + pencil) * sizeof(C2<T>)), owner), v[z]);
         }
     }
@@ -315,7 +322,8 @@ __device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab,
 
 // The matching gather (forward pass F2): 16-byte loads of both pencils of one z, one shuffle.
 template <typename T, int N, bool WIDE>
-__device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P, int NP, int pencil, unsigned mask)
+__device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P, unsigned pm, int NP, int pencil,
+                                              unsigned mask)
 {
     const uint32_t base = smem_u32addr(slab);
     if constexpr (WIDE) {
@@ -324,7 +332,7 @@ __device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P,
 #pragma unroll
         for (int z0 = 0; z0 < N; z0 += 2) {
             const int z = odd ? z0 + 1 : z0;
-            const int owner = z / P, zl = z - owner * P;
+            const int owner = plane_owner(z, pm), zl = z - owner * P;
             const float4 w = ld_cluster_f4(cluster_map(base + (uint32_t)((zl * NP + pbase) * sizeof(C2<T>)), owner));
             const C2<T> lo = C2<T>{w.x, w.y}, hi = C2<T>{w.z, w.w};
             const C2<T> send = odd ? lo : hi;
@@ -337,7 +345,7 @@ __device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P,
     } else {
 #pragma unroll
         for (int z = 0; z < N; ++z) {
-            const int owner = z / P, zl = z - owner * P;
+            const int owner = plane_owner(z, pm), zl = z - owner * P;
             ld_cluster(cluster_map(base + (uint32_t)((zl * NP + pencil) * sizeof(C2<T>)), owner), v[z]);
         }
     }
@@ -349,6 +357,7 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
     constexpr int H = N / 2 + 1;
     constexpr int N1 = (D == 3) ? N : 1;
     constexpr int NP = N1 * H;         // spectral columns of one axis-0 plane = pencils
+    constexpr int NPP = slab_stride<T, D, N>();   // plane stride of the slabs (padded NP)
     constexpr int64_t CELL = (int64_t)N * N1 * N;
     // 16-byte paired pencil stores need FP32 and an even pencil count (so that every slab row
     // starts on a 16-byte boundary and lane pairs hold pencil pairs)
@@ -366,8 +375,8 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2<T> *Is0 = reinterpret_cast<C2<T> *>(smem_raw);
-    C2<T> *Is1 = Is0 + (size_t)P * NP;                  // paired mode only
-    size_t off = (size_t)nbuf * P * NP * sizeof(C2<T>);
+    C2<T> *Is1 = Is0 + (size_t)P * NPP;                 // paired mode only
+    size_t off = (size_t)nbuf * P * NPP * sizeof(C2<T>);
     T *Sb = nullptr, *Gb;
     if (a.sg_global) {
         const int64_t slot = blockIdx.x;
@@ -383,19 +392,12 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
         off += (size_t)rows * N * sizeof(T);
         off = (off + 15) / 16 * 16;
     }
-    C2<T> *tw = reinterpret_cast<C2<T> *>(smem_raw + off);
-    off += (size_t)N * sizeof(C2<T>);
     double *part = reinterpret_cast<double *>(smem_raw + off);      // [32 warps + 1][kDiag]
     off += (32 + 1) * kDiag * sizeof(double);
     long long *s_cell = reinterpret_cast<long long *>(smem_raw + off);
     int *s_nubig = reinterpret_cast<int *>(smem_raw + off + 8);
 
-    for (int j = tid; j < N; j += nt) {
-        T s, c;
-        sincospi_t<T>(T(2 * j) / T(N), &s, &c);
-        tw[j] = C2<T>{c, -s};
-    }
-    __syncthreads();
+    const unsigned pm = 0xFFFFFFFFu / (unsigned)P + 1u;      // plane_owner's multiplier for P
 
     const int64_t nclusters = gridDim.x / C;
     const int64_t cid = blockIdx.x / C;
@@ -433,22 +435,22 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
             load_row<T, N>(src0, x0);
             load_row<T, N>(src1, x1);
             C2<T> X0[H], X1[H];
-            r2c_pair<N, T>(x0, x1, X0, X1, tw);
+            r2c_pair<N, T>(x0, x1, X0, X1);
 #pragma unroll
             for (int k = 0; k < H; ++k) {
-                Is0[r0 * H + k] = X0[k];
-                Is0[r1 * H + k] = X1[k];
+                Is0[(r0 / N1) * NPP + (r0 % N1) * H + k] = X0[k];
+                Is0[(r1 / N1) * NPP + (r1 % N1) * H + k] = X1[k];
             }
         }
         if constexpr (D == 3) {
             __syncthreads();
             for (int q = tid; q < P * H; q += nt) {            // axis 1, forward
                 const int zl = q / H, lx = q % H;
-                C2<T> *col = Is0 + (size_t)zl * NP + lx;
+                C2<T> *col = Is0 + (size_t)zl * NPP + lx;
                 C2<T> v[N];
 #pragma unroll
                 for (int y = 0; y < N; ++y) v[y] = col[y * H];
-                fft<N, -1, N>(v, tw);
+                fft<N, -1, N>(v);
 #pragma unroll
                 for (int y = 0; y < N; ++y) col[y * H] = v[y];
             }
@@ -463,8 +465,8 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
             const unsigned mask = __ballot_sync(0xffffffffu, has);
             if (has) {
                 C2<T> v[N];
-                gather_pencil<T, N, WIDE>(v, Is0, P, NP, pencil, mask);
-                fft<N, -1, N>(v, tw);
+                gather_pencil<T, N, WIDE>(v, Is0, P, pm, NPP, pencil, mask);
+                fft<N, -1, N>(v);
 #pragma unroll
                 for (int z = 0; z < N; ++z) Fh[(size_t)z * NP + pencil] = cscale(v[z], scale);
             }
@@ -494,8 +496,8 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
                     C2<T> v[N];
 #pragma unroll
                     for (int z = 0; z < N; ++z) v[z] = cscale(Fh[(size_t)z * NP + pencil], __ldg(M + (size_t)z * NP));
-                    fft<N, 1, N>(v, tw);
-                    scatter_pencil<T, N, WIDE>(v, b ? Is1 : Is0, P, NP, pencil, mask);
+                    fft<N, 1, N>(v);
+                    scatter_pencil<T, N, WIDE>(v, b ? Is1 : Is0, P, pm, NPP, pencil, mask);
                     if (a.prefetch && o + 1 < a.nops) {   // pull the next op's multipliers towards L1
                         const Op nx = a.ops[o + 1];
                         const T *Mn = Mbase + (size_t)(b ? nx.dir2 : nx.dir) * N * NP + pencil;
@@ -513,11 +515,11 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
                     const int b = q >= P * H;
                     const int rem = q - b * P * H;
                     const int zl = rem / H, lx = rem % H;
-                    C2<T> *col = (b ? Is1 : Is0) + (size_t)zl * NP + lx;
+                    C2<T> *col = (b ? Is1 : Is0) + (size_t)zl * NPP + lx;
                     C2<T> v[N];
 #pragma unroll
                     for (int y = 0; y < N; ++y) v[y] = col[y * H];
-                    fft<N, 1, N>(v, tw);
+                    fft<N, 1, N>(v);
 #pragma unroll
                     for (int y = 0; y < N; ++y) col[y * H] = v[y];
                 }
@@ -532,7 +534,8 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
                     // two Hermitian half rows -> one complex row z (a_e + i S_e), built straight
                     // from shared memory (the two-for-one inverse of c2r_pair)
                     C2<T> z[N];
-                    c2r_rows_from<N, T>(Is0 + r * H, Is1 + r * H, z, tw);
+                    const int ro = (r / N1) * NPP + (r % N1) * H;
+                    c2r_rows_from<N, T>(Is0 + ro, Is1 + ro, z);
                     T *Gr = Gb + r;
                     if (!last) {
 #pragma unroll
@@ -551,7 +554,7 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
                 for (int q = tid; q < npairs; q += nt) {
                     const int r0 = q, r1 = q + npairs;
                     C2<T> z[N];                      // z[n] = (row r0, row r1) at x = n
-                    c2r_rows_from<N, T>(Is0 + r0 * H, Is0 + r1 * H, z, tw);
+                    c2r_rows_from<N, T>(Is0 + (r0 / N1) * NPP + (r0 % N1) * H, Is0 + (r1 / N1) * NPP + (r1 % N1) * H, z);
                     // S and G are stored column-major ([x][row]): consecutive threads own
                     // consecutive rows, so every access below is conflict free without padding
                     T *S0 = Sb + r0, *S1 = Sb + r1;

@@ -2,8 +2,9 @@
 // factors 2, 3, 4, 5) for one thread, plus two-for-one real<->half-complex transforms.
 //
 // Convention: fft<L, SIGN> computes X[k] = sum_n x[n] exp(SIGN 2 pi i n k / L) in place, input
-// and output in natural order.  Twiddles come from a shared-memory table tw[j] = exp(-2 pi i j /
-// NTOP) of the top-level length (uniform indices: broadcast reads).
+// and output in natural order.  Twiddles exp(-2 pi i j / NTOP) of the top-level length come from a
+// constant-memory table built at compile time; every index is known after unrolling, so each
+// twiddle is a constant-bank operand of the multiply (no shared-memory table, no loads).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -33,16 +34,92 @@ __device__ __forceinline__ C2<T> mul_si(C2<T> a) { return SIGN > 0 ? C2<T>{-a.y,
 
 __host__ __device__ constexpr int first_radix(int L) { return (L % 4 == 0) ? 4 : (L % 2 == 0) ? 2 : (L % 3 == 0) ? 3 : 5; }
 
-// exp(SIGN 2 pi i e / L) with L | NTOP and 0 <= e < L, from tw[j] = exp(-2 pi i j / NTOP)
+// ---- compile-time twiddle table: exp(-2 pi i j / n) for the built lengths n, j < n
+constexpr int kTwLens[8] = {8, 12, 16, 24, 32, 40, 48, 64};
+constexpr int kTwTotal = 8 + 12 + 16 + 24 + 32 + 40 + 48 + 64;
+__host__ __device__ constexpr int tw_offset(int n)
+{
+    int off = 0;
+    for (int a = 0; a < 8 && kTwLens[a] != n; ++a) off += kTwLens[a];
+    return off;
+}
+struct TwTable {
+    double c[kTwTotal], s[kTwTotal];     // cos, -sin
+    float cf[kTwTotal], sf[kTwTotal];
+};
+// cos and sin of x in [0, pi/4] by their Taylor series (30 terms: converged in double)
+constexpr void taylor_cs(double x, double &c, double &s)
+{
+    double x2 = x * x, tc = 1.0, ts = x;
+    c = 0.0;
+    s = 0.0;
+    for (int k = 0; k < 30; ++k) {
+        c += tc;
+        s += ts;
+        tc *= -x2 / ((2.0 * k + 1.0) * (2.0 * k + 2.0));
+        ts *= -x2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+    }
+}
+// cos and sin of 2 pi num / den: exact integer reduction to an octant, then the series on the
+// distance r in [0, pi/4] to the octant's even boundary (cos / sin swapped on odd octants)
+constexpr void cs_turn(long num, long den, double &c, double &s)
+{
+    constexpr double pi = 3.14159265358979323846264338327950288;
+    num %= den;
+    if (num < 0) num += den;
+    const long o = (8 * num) / den;
+    const long rnum = (o % 2 == 0) ? 8 * num - o * den : (o + 1) * den - 8 * num;
+    double c0 = 0.0, s0 = 0.0;
+    taylor_cs(2.0 * pi * (double)rnum / (8.0 * (double)den), c0, s0);
+    switch (o) {
+    case 0: c = c0; s = s0; break;
+    case 1: c = s0; s = c0; break;
+    case 2: c = -s0; s = c0; break;
+    case 3: c = -c0; s = s0; break;
+    case 4: c = -c0; s = -s0; break;
+    case 5: c = -s0; s = -c0; break;
+    case 6: c = s0; s = -c0; break;
+    default: c = c0; s = -s0; break;
+    }
+}
+constexpr TwTable make_tw_table()
+{
+    TwTable t{};
+    int off = 0;
+    for (int a = 0; a < 8; ++a) {
+        for (int j = 0; j < kTwLens[a]; ++j) {
+            double c = 0.0, s = 0.0;
+            cs_turn(j, kTwLens[a], c, s);
+            t.c[off + j] = c;
+            t.s[off + j] = -s;
+            t.cf[off + j] = (float)c;
+            t.sf[off + j] = (float)(-s);
+        }
+        off += kTwLens[a];
+    }
+    return t;
+}
+static __constant__ TwTable c_tw = make_tw_table();
+
+template <int NTOP, typename T>
+__device__ __forceinline__ C2<T> tw_value(int j)
+{
+    constexpr int off = tw_offset(NTOP);
+    static_assert(off < kTwTotal, "twiddle length not in the table");
+    if constexpr (sizeof(T) == 4) return C2<T>{c_tw.cf[off + j], c_tw.sf[off + j]};
+    else return C2<T>{c_tw.c[off + j], c_tw.s[off + j]};
+}
+
+// exp(SIGN 2 pi i e / L) with L | NTOP and 0 <= e < L
 template <int L, int SIGN, int NTOP, typename T>
-__device__ __forceinline__ C2<T> twiddle_mul(C2<T> v, int e, const C2<T> *tw)
+__device__ __forceinline__ C2<T> twiddle_mul(C2<T> v, int e)
 {
     const int j = e * (NTOP / L);
     if (j == 0) return v;
     if (2 * j == NTOP) return C2<T>{-v.x, -v.y};
     if (4 * j == NTOP) return mul_si<SIGN>(v);            // exp(SIGN i pi/2) = SIGN i
     if (4 * j == 3 * NTOP) return mul_si<-SIGN>(v);
-    C2<T> w = tw[j];
+    C2<T> w = tw_value<NTOP, T>(j);
     if (SIGN > 0) w.y = -w.y;
     return cmul(v, w);
 }
@@ -95,7 +172,7 @@ __device__ __forceinline__ void butterfly(C2<T> (&t)[P])
 
 // Decimation in time: X[k1 + Q k2] = sum_p W_L^{p k1} W_P^{p k2} Y_p[k1], Y_p = DFT_Q(x[p + P m]).
 template <int L, int SIGN, int NTOP, typename T>
-__device__ __forceinline__ void fft(C2<T> (&x)[L], const C2<T> *tw)
+__device__ __forceinline__ void fft(C2<T> (&x)[L])
 {
     if constexpr (L == 1) {
         return;
@@ -111,12 +188,12 @@ __device__ __forceinline__ void fft(C2<T> (&x)[L], const C2<T> *tw)
 #pragma unroll
                 for (int m = 0; m < Qn; ++m) y[p][m] = x[p + P * m];
 #pragma unroll
-            for (int p = 0; p < P; ++p) fft<Qn, SIGN, NTOP>(y[p], tw);
+            for (int p = 0; p < P; ++p) fft<Qn, SIGN, NTOP>(y[p]);
 #pragma unroll
             for (int k1 = 0; k1 < Qn; ++k1) {
                 C2<T> t[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) t[p] = twiddle_mul<L, SIGN, NTOP>(y[p][k1], p * k1, tw);
+                for (int p = 0; p < P; ++p) t[p] = twiddle_mul<L, SIGN, NTOP>(y[p][k1], p * k1);
                 butterfly<P, SIGN>(t);
 #pragma unroll
                 for (int k2 = 0; k2 < P; ++k2) x[k1 + Qn * k2] = t[k2];
@@ -128,12 +205,12 @@ __device__ __forceinline__ void fft(C2<T> (&x)[L], const C2<T> *tw)
 // Two real rows -> their half spectra (k = 0 .. N/2), forward sign, unscaled.
 template <int N, typename T>
 __device__ __forceinline__ void r2c_pair(const T (&r1)[N], const T (&r2)[N], C2<T> (&X1)[N / 2 + 1],
-                                         C2<T> (&X2)[N / 2 + 1], const C2<T> *tw)
+                                         C2<T> (&X2)[N / 2 + 1])
 {
     C2<T> z[N];
 #pragma unroll
     for (int n = 0; n < N; ++n) z[n] = C2<T>{r1[n], r2[n]};
-    fft<N, -1, N>(z, tw);
+    fft<N, -1, N>(z);
 #pragma unroll
     for (int k = 0; k <= N / 2; ++k) {
         C2<T> a = z[k], b = cconj(z[(N - k) % N]);
@@ -147,7 +224,7 @@ __device__ __forceinline__ void r2c_pair(const T (&r1)[N], const T (&r2)[N], C2<
 // imaginary parts of the k = 0 and k = N/2 entries are ignored, as for any real inverse.
 template <int N, typename T>
 __device__ __forceinline__ void c2r_pair(const C2<T> (&X1)[N / 2 + 1], const C2<T> (&X2)[N / 2 + 1], T (&r1)[N],
-                                         T (&r2)[N], const C2<T> *tw)
+                                         T (&r2)[N])
 {
     C2<T> z[N];
     z[0] = C2<T>{X1[0].x, X2[0].x};
@@ -157,7 +234,7 @@ __device__ __forceinline__ void c2r_pair(const C2<T> (&X1)[N / 2 + 1], const C2<
         z[N - k] = C2<T>{X1[k].x + X2[k].y, X2[k].x - X1[k].y};
     }
     z[N / 2] = C2<T>{X1[N / 2].x, X2[N / 2].x};
-    fft<N, 1, N>(z, tw);
+    fft<N, 1, N>(z);
 #pragma unroll
     for (int n = 0; n < N; ++n) {
         r1[n] = z[n].x;
