@@ -157,6 +157,17 @@ ef_status ef_plan_reserve(ef_plan_t plan, int64_t ncells);
  *    this call can be slower than ef_collide. */
 ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void *Q_dev, int64_t ncells, ef_stream_t stream);
 
+/* The kernel function of the plan's discretisation on the grid: G_dev[y] = G^sigma(y, z) for every
+ * grid point y (flat C-order index, N^d doubles, caller-owned device memory) at the grid point z of
+ * flat index z_index, where G^sigma(y, z) = sum_{i,j in K} B^sigma_fast(i, j) E_i(y) E_j(z) is the
+ * weight of eq. tildeG (through eq. A_simplified) with the plan's low-rank kernel (eq. fastAlg).
+ * Sec. 3.2.2: G^sigma >= 0 with the filter (every pair weight of the DVM form is non-negative);
+ * without it (sigma_enabled = 0) G takes negative values (Fig. 1).  FP64 direct sums over the
+ * modes; a diagnostic of the kernel decomposition, not a step of the collision operator (cost
+ * N^{2d} n_e per call).  Uniform plans only (EF_ERR_INVALID_ARG for a batched plan, a null G_dev
+ * or z_index outside [0, N^d)). */
+ef_status ef_kernel_G(ef_plan_t plan, int64_t z_index, double *G_dev, ef_stream_t stream);
+
 /* Low-mode features of each cell: the discrete Fourier coefficients Fh_k = N^{-d} sum F E_{-k}
  * (eq. DFT, index-origin convention of the library's FFTs) at the modes |k| <= EF_FEATURE_K in the
  * canonical half space (k_last > 0; or k_last = 0 and k_1 > 0; or k_last = k_1 = 0 and k_0 >= 0),

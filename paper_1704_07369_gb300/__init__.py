@@ -35,7 +35,7 @@ EF_DIAG_STRIDE = 10
 # every symbol include/ef.h declares
 SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
            "ef_collide", "ef_euler_step", "ef_rk3_step", "ef_moments_entropy", "ef_plan_status",
-           "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_plan_reserve", "ef_collide_noalloc",
+           "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_plan_reserve", "ef_collide_noalloc", "ef_kernel_G",
            "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_status", "ef_mlp_params",
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
@@ -89,6 +89,7 @@ def lib():
         L.ef_mlp_info.argtypes = [vp, ctypes.POINTER(i64)]
         L.ef_mlp_status.argtypes = [vp, i32, i32]
         L.ef_plan_reserve.argtypes = [vp, i64]
+        L.ef_kernel_G.argtypes = [vp, i64, vp, vp]
         L.ef_mlp_params.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_mlp_forward.argtypes = [vp, vp, i32, vp, i32, i64, vp]
         L.ef_mlp_grad.argtypes = [vp, vp, i32, vp, i32, vp, vp, i64, vp, vp, vp]
@@ -182,6 +183,11 @@ def ef_collide(plan, F, Q, ncells, stream=None):
 def ef_collide_noalloc(plan, F, Q, ncells, stream=None):
     """ef_collide without any device allocation (scratch in the library's static device array)."""
     _check(lib().ef_collide_noalloc(plan, _ptr(F), _ptr(Q), int(ncells), _stream(stream)))
+
+
+def ef_kernel_G(plan, z_index, G, stream=None):
+    """G[y] = G^sigma(y, z) of the plan's kernel decomposition at the grid point z (flat index)."""
+    _check(lib().ef_kernel_G(plan, int(z_index), _ptr(G), _stream(stream)))
 
 
 def ef_features(plan, F, feat, ncells, log_input=0, stream=None):

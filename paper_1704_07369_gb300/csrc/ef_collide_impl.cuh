@@ -286,12 +286,15 @@ __device__ __forceinline__ void ld_cluster(uint32_t a, C2<double> &v)
 // lanes 2j and 2j+1 hold the adjacent pencils p, p+1 (p even); one shuffle per z pair lets each
 // lane write both pencils of one z as a single 16-byte store, halving the number of (mostly
 // remote, distributed shared memory) store transactions.
-// owner CTA and local plane of axis-0 index z, for planes-per-CTA P with pm = floor((2^32 - 1) / P) + 1:
-// exact for z < 2^16 (a multiply-high instead of an integer division)
-__device__ __forceinline__ int plane_owner(int z, unsigned pm) { return (int)__umulhi((unsigned)z, pm); }
+// owner CTA of axis-0 index z for P planes per CTA: floor(z / P) = floor(z pm / 2^32) with the 64-bit
+// multiplier pm = ceil(2^32 / P) (pm = 2^32 for P = 1), exact for 0 <= z < 2^16 and P < 2^16
+__device__ __forceinline__ int plane_owner(int z, unsigned long long pm)
+{
+    return (int)(((unsigned long long)(unsigned)z * pm) >> 32);
+}
 
 template <typename T, int N, bool WIDE>
-__device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab, int P, unsigned pm, int NP, int pencil,
+__device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab, int P, unsigned long long pm, int NP, int pencil,
                                                unsigned mask)
 {
     const uint32_t base = smem_u32addr(slab);
@@ -322,7 +325,7 @@ __device__ __forceinline__ void scatter_pencil(const C2<T> (&v)[N], C2<T> *slab,
 
 // The matching gather (forward pass F2): 16-byte loads of both pencils of one z, one shuffle.
 template <typename T, int N, bool WIDE>
-__device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P, unsigned pm, int NP, int pencil,
+__device__ __forceinline__ void gather_pencil(C2<T> (&v)[N], C2<T> *slab, int P, unsigned long long pm, int NP, int pencil,
                                               unsigned mask)
 {
     const uint32_t base = smem_u32addr(slab);
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(OCC == 1 ? max_threads<T, N>() : kOcc2Threads,
     long long *s_cell = reinterpret_cast<long long *>(smem_raw + off);
     int *s_nubig = reinterpret_cast<int *>(smem_raw + off + 8);
 
-    const unsigned pm = 0xFFFFFFFFu / (unsigned)P + 1u;      // plane_owner's multiplier for P
+    const unsigned long long pm = (0x100000000ull + (unsigned)P - 1u) / (unsigned)P;   // plane_owner's multiplier
 
     const int64_t nclusters = gridDim.x / C;
     const int64_t cid = blockIdx.x / C;

@@ -32,6 +32,7 @@ struct PlanView {
     int cluster, tpb, planes, paired, nops, max_clusters, sg_global, nfeat;   // nfeat: band modes
     int occ;                  // kernel instantiation: 1 or 2 CTAs per SM
     int prefetch;             // 1: L1 prefetch of the next op's multipliers
+    int ndir;                 // rows of the multiplier table: n_e directions, n_e partner sums, the loss
     size_t smem;
     double L;
     const void *mult;

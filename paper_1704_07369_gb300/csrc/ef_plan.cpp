@@ -1072,6 +1072,7 @@ bool plan_view(const ef_plan_s *p, PlanView *out)
     out->nfeat = cp.nfeat;
     out->occ = cp.occ;
     out->prefetch = cp.prefetch;
+    out->ndir = cp.ndir;
     out->smem = cp.smem;
     out->modes = cp.d_modes;
     out->L = p->desc.L;

@@ -13,7 +13,7 @@ def _declared():
     with open(os.path.join(ROOT, "include", "ef.h")) as f:
         src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return set(re.findall(r"\b(ef_[a-z0-9_]+)\s*\(", src))
+    return set(re.findall(r"\b(ef_[A-Za-z0-9_]+)\s*\(", src))
 
 
 def test_library_exports_every_declared_symbol():

@@ -183,3 +183,33 @@ def test_rk3_without_reserve_is_refused_before_any_launch():
         ef.ef_rk3_step(plan.handle, F, 0.01, 1, None, 3)      # more cells than reserved
     torch.cuda.synchronize()
     assert plan.status() == ef.EF_OK
+
+
+def test_kernel_function_fig1_on_the_gpu():
+    """Fig. 1 from the GPU: 2D, B~ = 1/pi, R_tr = 6, T = (3 sqrt 2 + 1) R_tr / 4, N = 32, R = 64,
+    z = (T/2, T/2).  G^sigma(y, z) of the plan's low-rank kernel takes negative values without the
+    filter and none with it (Sec. 3.2.1 / 3.2.2), and equals the oracle's G to FP64 round-off."""
+    N, R, Rtr = 32, 64, 6.0
+    T = (3.0 * np.sqrt(2.0) + 1.0) * Rtr / 4.0
+    z = (N // 2 + N // 4) * N + (N // 2 + N // 4)
+    for sigma in (0, 1):
+        plan = ef.Plan(2, N, T, ef.EF_KERNEL_MAXWELL, R, ef.EF_PREC_F64, R_tr=Rtr, sigma_enabled=sigma)
+        G = torch.zeros(N * N, dtype=torch.float64, device="cuda")
+        ef.ef_kernel_G(plan.handle, z, G)
+        torch.cuda.synchronize()
+        g = G.cpu().numpy()
+        ref = oracle.G_slice(oracle.Params(d=2, N=N, T=T, kernel=0, R=R, Rtr=Rtr, filter=bool(sigma)), z).ravel()
+        assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+        if sigma:
+            assert g.min() >= -1e-12 * g.max()
+        else:
+            assert g.min() < -1e-2 * g.max()
+    # 3D hard spheres, N = 8: the filtered G is non-negative and matches the oracle
+    plan = ef.Plan(3, 8, 8.0, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F64)
+    G = torch.zeros(8 ** 3, dtype=torch.float64, device="cuda")
+    ef.ef_kernel_G(plan.handle, 3 * 64 + 5 * 8 + 2, G)
+    torch.cuda.synchronize()
+    ref = oracle.G_slice(oracle.Params(d=3, N=8, T=8.0, kernel=1, R=32, J=6), 3 * 64 + 5 * 8 + 2).ravel()
+    g = G.cpu().numpy()
+    assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert g.min() >= -1e-12 * g.max()
