@@ -1,0 +1,410 @@
+// ef_collide_rg.cuh -- the FP32 3D collision kernel with the gain accumulator in registers and
+// the forward spectrum in shared memory (one thread-block cluster per cell).
+//
+// Same arithmetic as collide_kernel (Sec. 4.1, eq. fastAlg, paired op list: G = -F nu, then
+// G += a_e S_e for every first direction e, where S_e is the inverse transform of the weighted sum
+// of e's partner multipliers; the last pass writes Q or F + dt Q with the FP64 diagnostics), laid
+// out for sm_103a:
+//   * every thread owns RPT fixed real rows for the whole cell, so G lives in its registers: the
+//     accumulate pass touches no shared memory for G, and the shared memory this frees holds the
+//     CTA's axis-0 pencils of the forward spectrum, so stage A reads Fhat from shared memory
+//     instead of L2;
+//   * the multiplier of every op vanishes on the modes with a component -N/2 (sigma_N(-N/2) = 0,
+//     Sec. 4.1), so the Nyquist column k_x = -N/2 is neither stored nor transformed: the axis-0
+//     pencils (k_y, k_x < N/2) number N^2/2, the axis-1 columns of a plane N/2, and each stage has
+//     exactly one work item per real row (N^2 / C per CTA for a paired op), which matches the
+//     thread count rows / RPT with no partial rounds;
+//   * slab rows of N/2 + 2 complex values (an odd count of 16-byte pairs) and float4 row access
+//     keep the row passes free of bank conflicts; a plane stride of 8 mod 16 complex values does
+//     the same for the paired 16-byte pencil stores of stage A.
+// Per cell: F1 (own planes: real -> half complex along the last axis, axis 1 forward), F2 (own
+// pencils: gather through distributed shared memory, axis 0 forward, keep in shared memory), then
+// per op: A (multiply, axis 0 inverse, scatter to the owners' slabs), B (axis 1 inverse, then the
+// two-for-one half complex -> real row transform and the accumulate / output).
+#pragma once
+
+#include "ef_collide_impl.cuh"
+
+namespace ef {
+
+// row stride (complex) of the slabs: N/2 + 2, an odd number of 16-byte pairs
+template <int N>
+__host__ __device__ constexpr int rg_row_stride() { return N / 2 + 2; }
+// plane stride: N rows, padded to 8 mod 16 complex values
+template <int N>
+__host__ __device__ constexpr int rg_plane_stride()
+{
+    constexpr int s = N * rg_row_stride<N>();
+    return s + ((8 - s % 16) + 16) % 16;
+}
+// threads per CTA the (N, RPT) instantiation is compiled for (launch bound, one CTA per SM)
+template <int N, int RPT>
+__host__ __device__ constexpr int rg_max_threads()
+{
+    return N == 40 ? 320 : (N == 32 || N == 64) ? 256 : 288;
+}
+template <int N>
+__host__ __device__ constexpr bool rg_built() { return N == 16 || N == 24 || N == 32 || N == 40 || N == 48 || N == 64; }
+
+// pencils (k_y, k_x < N/2) per CTA of a C-CTA cluster; 0 if the split is not even
+__host__ __device__ inline int rg_npc(int N, int C)
+{
+    const int np = N * N / 2;
+    return (np % C == 0 && (np / C) % 2 == 0) ? np / C : 0;
+}
+
+template <int N>
+__host__ __device__ constexpr size_t rg_smem_bytes(int planes, int npc)
+{
+    return (size_t)2 * planes * rg_plane_stride<N>() * 8 + (size_t)N * npc * 8 + (32 + 1) * kDiag * sizeof(double) + 16;
+}
+
+// in-plane offset of the even pencil of a lane pair: pencil q (even) -> (k_y, k_x) = (q / (N/2), q % (N/2))
+template <int N>
+__device__ __forceinline__ int rg_poff(int q) { return (q / (N / 2)) * rg_row_stride<N>() + (q % (N / 2)); }
+
+// stage-A scatter of one pencil (lane pairs hold pencils q, q + 1 of one slab row; one shuffle per
+// z pair so that each lane issues 16-byte stores; owner CTA of z by multiply-high)
+template <int N>
+__device__ __forceinline__ void rg_scatter(const C2<float> (&v)[N], uint32_t slab_base, int P, unsigned long long pm,
+                                           int poff, bool odd, unsigned mask)
+{
+    constexpr int NPP = rg_plane_stride<N>();
+#pragma unroll
+    for (int z0 = 0; z0 < N; z0 += 2) {
+        const C2<float> send = odd ? v[z0] : v[z0 + 1];
+        C2<float> recv;
+        recv.x = __shfl_xor_sync(mask, send.x, 1);
+        recv.y = __shfl_xor_sync(mask, send.y, 1);
+        const int z = odd ? z0 + 1 : z0;
+        const C2<float> lo = odd ? recv : v[z0];
+        const C2<float> hi = odd ? v[z0 + 1] : recv;
+        const int owner = plane_owner(z, pm), zl = z - owner * P;
+        st_cluster(cluster_map(slab_base + (uint32_t)((zl * NPP + poff) * 8), owner), make_float4(lo.x, lo.y, hi.x, hi.y));
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void rg_gather(C2<float> (&v)[N], uint32_t slab_base, int P, unsigned long long pm, int poff,
+                                          bool odd, unsigned mask)
+{
+    constexpr int NPP = rg_plane_stride<N>();
+#pragma unroll
+    for (int z0 = 0; z0 < N; z0 += 2) {
+        const int z = odd ? z0 + 1 : z0;
+        const int owner = plane_owner(z, pm), zl = z - owner * P;
+        const float4 w = ld_cluster_f4(cluster_map(slab_base + (uint32_t)((zl * NPP + poff) * 8), owner));
+        const C2<float> lo = C2<float>{w.x, w.y}, hi = C2<float>{w.z, w.w};
+        const C2<float> send = odd ? lo : hi;
+        C2<float> recv;
+        recv.x = __shfl_xor_sync(mask, send.x, 1);
+        recv.y = __shfl_xor_sync(mask, send.y, 1);
+        v[z0] = odd ? recv : lo;
+        v[z0 + 1] = odd ? hi : recv;
+    }
+}
+
+// two Hermitian half rows (k < N/2; the k = N/2 entry is zero for every op) -> z = IFFT(R0) + i
+// IFFT(R1), read as 16-byte pairs
+template <int N>
+__device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, const C2<float> *R1, C2<float> (&z)[N])
+{
+    const float4 *A = reinterpret_cast<const float4 *>(R0);
+    const float4 *B = reinterpret_cast<const float4 *>(R1);
+#pragma unroll
+    for (int k2 = 0; k2 < N / 2; k2 += 2) {
+        const float4 a = A[k2 / 2], b = B[k2 / 2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = k2 + h;
+            const C2<float> x0 = h ? C2<float>{a.z, a.w} : C2<float>{a.x, a.y};
+            const C2<float> x1 = h ? C2<float>{b.z, b.w} : C2<float>{b.x, b.y};
+            if (k == 0) {
+                z[0] = C2<float>{x0.x, x1.x};
+            } else {
+                z[k] = C2<float>{x0.x - x1.y, x0.y + x1.x};
+                z[N - k] = C2<float>{x0.x + x1.y, x1.x - x0.y};
+            }
+        }
+    }
+    z[N / 2] = C2<float>{0.f, 0.f};
+    fft<N, 1, N>(z);
+}
+
+template <int D, int N, int RPT>
+__global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg(const CollideArgs a)
+{
+    static_assert(D == 3, "3D only");
+    using T = float;
+    constexpr int RS = rg_row_stride<N>();
+    constexpr int NPP = rg_plane_stride<N>();
+    constexpr int NH = N / 2;              // stored k_x values per row
+    constexpr int64_t CELL = (int64_t)N * N * N;
+
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int P = a.planes;
+    const int tid = threadIdx.x, nt = blockDim.x;          // nt * RPT = rows
+    Sync bar{cl, C};
+    const int rows = P * N;
+    const int NPC = a.npc;                 // pencils per CTA = N^2 / (2 C), even
+    // the launch shape this layout needs (the same for every CTA, so all return together):
+    // RPT rows per thread exactly, an even pencil split over the cluster
+    if (nt * RPT != rows || P * C != N || 2 * NPC * C != N * N || NPC % 2) {
+        if (tid == 0) record_status(a.status, 2);       // EF_ERR_UNSUPPORTED
+        return;
+    }
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2<T> *Is0 = reinterpret_cast<C2<T> *>(smem_raw);
+    C2<T> *Is1 = Is0 + (size_t)P * NPP;
+    C2<T> *Fs = Is1 + (size_t)P * NPP;                       // [z][local pencil] forward spectrum
+    double *part = reinterpret_cast<double *>(Fs + (size_t)N * NPC);     // [32 warps + 1][kDiag]
+    long long *s_cell = reinterpret_cast<long long *>(part + (32 + 1) * kDiag);
+    int *s_nubig = reinterpret_cast<int *>(s_cell + 1);
+    const uint32_t base0 = smem_u32addr(Is0), base1 = smem_u32addr(Is1);
+
+    const unsigned long long pm = (0x100000000ull + (unsigned)P - 1u) / (unsigned)P;
+    const int64_t nclusters = gridDim.x / C;
+    const int64_t cid = blockIdx.x / C;
+    const int lane = tid & 31;
+    const T scale = T(1) / T(CELL);
+    const T *Mbase = reinterpret_cast<const T *>(a.mult);
+    constexpr int H = N / 2 + 1;
+    constexpr int NPT = N * H;             // multiplier table: [dir][k_z][k_y * H + k_x]
+
+    const int64_t ncells = a.dev_ncells ? (int64_t)*a.dev_ncells : a.ncells;
+    int64_t c = cid - nclusters;
+    for (;;) {
+        if (a.counter) {
+            if (rank == 0 && tid == 0) *s_cell = (long long)atomicAdd(a.counter, 1ULL);
+            bar.full();
+            c = *cl.map_shared_rank(s_cell, 0);
+        } else {
+            c += nclusters;
+        }
+        if (c >= ncells) break;
+        const int64_t coff = a.cell_off ? a.cell_off[c] : c * CELL;
+        const int64_t cglob = a.cell_id ? a.cell_id[c] : c;
+        const T *F = reinterpret_cast<const T *>(a.F) + coff;
+        T *Out = reinterpret_cast<T *>(a.Q) + coff;
+        if (tid == 0) *s_nubig = 0;
+
+        // ---------------- F1: own rows real -> half complex (k_x < N/2 kept), two rows per item
+        for (int q = tid; q < rows / 2; q += nt) {
+            const int r0 = q, r1 = q + rows / 2;
+            T x0[N], x1[N];
+            load_row<T, N>(F + ((int64_t)rank * rows + r0) * N, x0);
+            load_row<T, N>(F + ((int64_t)rank * rows + r1) * N, x1);
+            C2<T> X0[H], X1[H];
+            r2c_pair<N, T>(x0, x1, X0, X1);
+            float4 *d0 = reinterpret_cast<float4 *>(Is0 + (r0 / N) * NPP + (r0 % N) * RS);
+            float4 *d1 = reinterpret_cast<float4 *>(Is0 + (r1 / N) * NPP + (r1 % N) * RS);
+#pragma unroll
+            for (int k = 0; k < NH; k += 2) {
+                d0[k / 2] = make_float4(X0[k].x, X0[k].y, X0[k + 1].x, X0[k + 1].y);
+                d1[k / 2] = make_float4(X1[k].x, X1[k].y, X1[k + 1].x, X1[k + 1].y);
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < P * NH; q += nt) {            // axis 1 forward, k_x < N/2
+            const int zl = q / NH, lx = q % NH;
+            C2<T> *col = Is0 + (size_t)zl * NPP + lx;
+            C2<T> v[N];
+#pragma unroll
+            for (int y = 0; y < N; ++y) v[y] = col[y * RS];
+            fft<N, -1, N>(v);
+#pragma unroll
+            for (int y = 0; y < N; ++y) col[y * RS] = v[y];
+        }
+        bar.full();
+
+        // ---------------- F2: own pencils, gathered, axis 0 forward, kept in shared memory
+        for (int q0 = tid - lane; q0 < NPC; q0 += nt) {
+            const int ql = q0 + lane;
+            const bool has = ql < NPC;
+            const unsigned mask = __ballot_sync(0xffffffffu, has);
+            if (has) {
+                const int q = rank * NPC + ql;
+                C2<T> v[N];
+                rg_gather<N>(v, base0, P, pm, rg_poff<N>(q & ~1), q & 1, mask);
+                fft<N, -1, N>(v);
+#pragma unroll
+                for (int z = 0; z < N; ++z) Fs[(size_t)z * NPC + ql] = cscale(v[z], scale);
+            }
+        }
+        bar.full();                        // Fs complete; every slab free again
+
+        Diag dg;
+        dg.reset();
+        T g[RPT][N];                       // gain accumulator of this thread's rows tid + j nt
+
+        for (int o = 0; o < a.nops; ++o) {
+            const Op op = a.ops[o];
+            const bool pair = op.kind >= OP_PAIR;
+            // ---------------- A: multiply, axis 0 inverse, scatter (one (direction, pencil) item
+            // per thread; lanes of a pair share the direction since NPC is even)
+            const int nitems = (pair ? 2 : 1) * NPC;
+            for (int q0 = tid - lane; q0 < nitems; q0 += nt) {
+                const int qi = q0 + lane;
+                const bool has = qi < nitems;
+                const unsigned mask = __ballot_sync(0xffffffffu, has);
+                if (has) {
+                    const int b = qi >= NPC;
+                    const int ql = qi - b * NPC;
+                    const int q = rank * NPC + ql;
+                    const int ky = q / NH, kx = q % NH;
+                    const T *M = Mbase + (size_t)(b ? op.dir2 : op.dir) * N * NPT + ky * H + kx;
+                    C2<T> v[N];
+#pragma unroll
+                    for (int z = 0; z < N; ++z) v[z] = cscale(Fs[(size_t)z * NPC + ql], __ldg(M + (size_t)z * NPT));
+                    fft<N, 1, N>(v);
+                    rg_scatter<N>(v, b ? base1 : base0, P, pm, rg_poff<N>(q & ~1), q & 1, mask);
+                }
+            }
+            bar.full();
+
+            // ---------------- B: axis 1 inverse on the stored k_x < N/2 columns of each slab
+            const int ncol = (pair ? 2 : 1) * P * NH;
+            for (int q = tid; q < ncol; q += nt) {
+                const int b = q >= P * NH;
+                const int rem = q - b * P * NH;
+                const int zl = rem / NH, lx = rem % NH;
+                C2<T> *col = (b ? Is1 : Is0) + (size_t)zl * NPP + lx;
+                C2<T> v[N];
+#pragma unroll
+                for (int y = 0; y < N; ++y) v[y] = col[y * RS];
+                fft<N, 1, N>(v);
+#pragma unroll
+                for (int y = 0; y < N; ++y) col[y * RS] = v[y];
+            }
+            __syncthreads();
+
+            // ---------------- rows: half complex -> real, accumulate in registers / output
+            if (pair) {
+                const bool last = op.kind == OP_PAIR_LAST;
+                const bool big = *s_nubig != 0;
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    const int r = tid + j * nt;
+                    const int ro = (r / N) * NPP + (r % N) * RS;
+                    C2<T> z[N];
+                    rg_c2r_rows<N>(Is0 + ro, Is1 + ro, z);
+                    if (!last) {
+#pragma unroll
+                        for (int n = 0; n < N; ++n) g[j][n] += z[n].x * z[n].y;
+                    } else {
+                        T qv[N];
+#pragma unroll
+                        for (int n = 0; n < N; ++n) qv[n] = g[j][n] + z[n].x * z[n].y;
+                        const int64_t grow = (int64_t)rank * rows + r;
+                        T fr[N];
+                        load_row<T, N>(F + grow * N, fr);
+                        emit_row<T, D, N>(a, fr, Out + grow * N, qv, nullptr, big, grow, dg);
+                    }
+                }
+            } else {
+                // the loss (first op): nu of this thread's rows, G = -F nu.  With two rows per
+                // thread they share one complex transform; with one, the second input is zero.
+                bool bigt = false;
+                if constexpr (RPT == 2) {
+                    const int r0 = tid, r1 = tid + nt;
+                    C2<T> z[N];
+                    rg_c2r_rows<N>(Is0 + (r0 / N) * NPP + (r0 % N) * RS, Is0 + (r1 / N) * NPP + (r1 % N) * RS, z);
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int r = j ? r1 : r0;
+                        T fr[N];
+                        load_row<T, N>(F + ((int64_t)rank * rows + r) * N, fr);
+                        T mx = j ? z[0].y : z[0].x;
+#pragma unroll
+                        for (int n = 0; n < N; ++n) {
+                            const T nu = j ? z[n].y : z[n].x;
+                            g[j][n] = -fr[n] * nu;
+                            mx = nu > mx ? nu : mx;
+                            if (T(a.dt) * nu > T(1)) bigt = true;
+                        }
+                        dg.max_nu = fmax(dg.max_nu, (double)mx);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) {
+                        const int r = tid + j * nt;
+                        const C2<T> *R0 = Is0 + (r / N) * NPP + (r % N) * RS;
+                        // real row from one half spectrum: z = IFFT(R0) (the second input zero)
+                        C2<T> z[N];
+#pragma unroll
+                        for (int k = 1; k < NH; ++k) {
+                            z[k] = R0[k];
+                            z[N - k] = cconj(R0[k]);
+                        }
+                        z[0] = C2<T>{R0[0].x, 0.f};
+                        z[NH] = C2<T>{0.f, 0.f};
+                        fft<N, 1, N>(z);
+                        T fr[N];
+                        load_row<T, N>(F + ((int64_t)rank * rows + r) * N, fr);
+                        T mx = z[0].x;
+#pragma unroll
+                        for (int n = 0; n < N; ++n) {
+                            const T nu = z[n].x;
+                            g[j][n] = -fr[n] * nu;
+                            mx = nu > mx ? nu : mx;
+                            if (T(a.dt) * nu > T(1)) bigt = true;
+                        }
+                        dg.max_nu = fmax(dg.max_nu, (double)mx);
+                    }
+                }
+                if (bigt && a.out_mode == OUT_EULER) *s_nubig = 1;
+            }
+            bar.war();
+        }
+
+        // ---------------- per-cell FP64 reduction of the diagnostics
+        if (a.diag) {
+            dg.sum[7] = dg.min_f;
+            dg.sum[8] = dg.max_nu;
+            dg.sum[9] = dg.min_out;
+            const int warp = tid >> 5, nw = (nt + 31) >> 5;
+#pragma unroll
+            for (int k = 0; k < kDiag; ++k) {
+                double v = dg.sum[k];
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) {
+                    const double u = __shfl_xor_sync(0xffffffffu, v, s);
+                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                }
+                if (lane == 0) part[warp * kDiag + k] = v;
+            }
+            __syncthreads();
+            if (tid < kDiag) {
+                const int k = tid;
+                double v = part[k];
+                for (int w2 = 1; w2 < nw; ++w2) {
+                    const double u = part[w2 * kDiag + k];
+                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                }
+                part[32 * kDiag + k] = v;
+            }
+            bar.full();
+            if (rank == 0 && tid < kDiag) {
+                const int k = tid;
+                double v = part[32 * kDiag + k];
+                for (int r = 1; r < C; ++r) {
+                    const double *rp = cl.map_shared_rank(part, r);
+                    const double u = rp[32 * kDiag + k];
+                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                }
+                const double hd = a.h * a.h * a.h;
+                if (k == 0 || k == 5) v *= hd;
+                else if (k >= 1 && k <= 3) v *= hd * a.h;
+                else if (k == 4) v *= 0.5 * hd * a.h * a.h;
+                a.diag[cglob * kDiag + k] = v;
+            }
+            bar.war();
+        }
+    }
+    bar.war();   // no CTA leaves while a peer may still read its shared memory
+}
+
+}  // namespace ef

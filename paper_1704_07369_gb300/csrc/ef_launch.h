@@ -13,10 +13,17 @@ namespace ef {
 #define EF_DECLARE_VARIANT(SUF)                                                                      \
     bool collide_supported_##SUF(int N);                                                             \
     int collide_maxthreads_##SUF(int N, int occ);                                                    \
-    size_t collide_smem_##SUF(int N, int planes, int sg_global, int paired);                         \
+    size_t collide_smem_##SUF(int N, int planes, int sg_global, int paired, int occ);                \
     cudaError_t collide_setup_##SUF(int N, size_t smem, int cluster, int tpb, int occ, int *max_clusters); \
     cudaError_t collide_launch_##SUF(int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, \
                                      int occ, cudaStream_t s);
+
+// FP32 3D register-accumulator kernel (ef_collide_rg_f32.cu); rpt = rows per thread (1 or 2).
+// rg_maxthreads_f32 returns 0 for a size it is not built for.
+int rg_maxthreads_f32(int N, int rpt);
+size_t rg_smem_f32(int N, int planes);
+cudaError_t rg_setup_f32(int N, int rpt, size_t smem, int cluster, int tpb, int *max_clusters);
+cudaError_t rg_launch_f32(int N, int rpt, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s);
 
 EF_DECLARE_VARIANT(f32_2d)
 EF_DECLARE_VARIANT(f32_3d)
@@ -55,7 +62,18 @@ inline size_t collide_fh_bytes(int prec, int d, int N)
 {
     return (size_t)N * (d == 3 ? N : 1) * (N / 2 + 1) * (prec == 0 ? 8 : 16);
 }
-size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired);
+size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired, int occ);
+// Kernel variants ("occ"): 1 = one CTA per SM, 2 = two CTAs per SM (shared-memory accumulators);
+// 3 / 4 = FP32 3D register-accumulator kernel with one / two real rows per thread, which keeps the
+// forward spectrum in shared memory and skips the Nyquist column (pencils: N^2 / (2 C) per CTA).
+inline int collide_npc_v(int d, int N, int C, int occ)
+{
+    if (occ >= 3) {
+        const int np = N * N / 2;
+        return (np % C == 0 && (np / C) % 2 == 0) ? np / C : 0;
+    }
+    return collide_npc(d, N, C);
+}
 cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,
                            int occ, cudaStream_t s);
 void set_last_error(const char *msg);

@@ -88,14 +88,16 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
     if (st != EF_OK) return st;
 
     // per cluster: S and G of each CTA in global memory (2 * rows * N values per CTA) and the
-    // forward-spectrum workspace; layout [counter][S/G of grid * C CTAs][spectra of grid clusters]
+    // forward-spectrum workspace; layout [counter][S/G of grid * C CTAs][spectra of grid clusters].
+    // The register-accumulator variants (occ 3, 4) keep both on chip and need only the counter.
+    const bool onchip = v.occ >= 3;
     const int64_t rows = (int64_t)v.planes * (v.d == 3 ? v.N : 1);
     const size_t el = v.prec == EF_PREC_F32 ? 4 : 8;
-    const size_t per_cta = ((size_t)2 * rows * v.N * el + 255) / 256 * 256;
-    const size_t per_fh = (ef::collide_fh_bytes(v.prec, v.d, v.N) + 255) / 256 * 256;
+    const size_t per_cta = onchip ? 0 : ((size_t)2 * rows * v.N * el + 255) / 256 * 256;
+    const size_t per_fh = onchip ? 0 : (ef::collide_fh_bytes(v.prec, v.d, v.N) + 255) / 256 * 256;
     const size_t per_cluster = per_cta * v.cluster + per_fh;
     const size_t avail = kScratchBytes - kCounterBytes;
-    const int64_t clusters_fit = (int64_t)(avail / per_cluster);
+    const int64_t clusters_fit = onchip ? (int64_t)v.max_clusters : (int64_t)(avail / per_cluster);
     if (clusters_fit < 1) {
         char buf[200];
         std::snprintf(buf, sizeof(buf),
@@ -105,7 +107,7 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
         return EF_ERR_UNSUPPORTED;
     }
     const int grid = (int)std::min<int64_t>(std::min<int64_t>(ncells, v.max_clusters), clusters_fit);
-    const size_t smem = ef::collide_smem(v.prec, v.d, v.N, v.planes, 1, v.paired);
+    const size_t smem = onchip ? v.smem : ef::collide_smem(v.prec, v.d, v.N, v.planes, 1, v.paired, v.occ);
 
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(base, 0, sizeof(unsigned long long), s);      // the cell queue starts at 0
@@ -122,10 +124,10 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
     a.nops = v.nops;
     a.cluster = v.cluster;
     a.planes = v.planes;
-    a.sg_global = 1;
+    a.sg_global = onchip ? 0 : 1;
     a.sg_ws = static_cast<unsigned char *>(base) + kCounterBytes;
     a.fh_ws = static_cast<unsigned char *>(base) + kCounterBytes + (size_t)grid * v.cluster * per_cta;
-    a.npc = ef::collide_npc(v.d, v.N, v.cluster);
+    a.npc = ef::collide_npc_v(v.d, v.N, v.cluster, v.occ);
     a.out_mode = ef::OUT_COLLIDE;
     a.h = 2.0 * v.L / v.N;
     a.status = v.status;

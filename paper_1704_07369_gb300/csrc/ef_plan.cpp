@@ -304,11 +304,11 @@ int maxthreads_for(int prec, int d, int N, int occ)
     return d == 3 ? ef::collide_maxthreads_f64_3d(N, occ) : ef::collide_maxthreads_f64_2d(N, occ);
 }
 
-size_t smem_for(int prec, int d, int N, int planes, int sg, int paired)
+size_t smem_for(int prec, int d, int N, int planes, int sg, int paired, int occ = 1)
 {
     if (prec == EF_PREC_F32)
-        return d == 3 ? ef::collide_smem_f32_3d(N, planes, sg, paired) : ef::collide_smem_f32_2d(N, planes, sg, paired);
-    return d == 3 ? ef::collide_smem_f64_3d(N, planes, sg, paired) : ef::collide_smem_f64_2d(N, planes, sg, paired);
+        return d == 3 ? ef::collide_smem_f32_3d(N, planes, sg, paired, occ) : ef::collide_smem_f32_2d(N, planes, sg, paired, occ);
+    return d == 3 ? ef::collide_smem_f64_3d(N, planes, sg, paired, occ) : ef::collide_smem_f64_2d(N, planes, sg, paired, occ);
 }
 
 cudaError_t setup_for(int prec, int d, int N, size_t smem, int cl, int tpb, int occ, int *mc)
@@ -349,7 +349,33 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int cands[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
     std::vector<Shape> out;
-    for (int sg = 0; sg <= 1 && out.empty(); ++sg) {
+    // FP32 3D: the register-accumulator kernel first (one or two rows per thread, threads = rows / RPT)
+    if (ds.prec == EF_PREC_F32 && d == 3) {
+        for (int C : cands) {
+            if (N % C || ef::collide_npc_v(d, N, C, 3) == 0) continue;
+            const int planes = N / C, rows = planes * N;
+            for (int rpt = 2; rpt >= 1; --rpt) {
+                const int occ = 2 + rpt;
+                const int tmax = maxthreads_for(ds.prec, d, N, occ);
+                if (tmax == 0 || rows % rpt) continue;
+                const int tpb = rows / rpt;
+                if (tpb > tmax || tpb < 32) continue;
+                const size_t smem = smem_for(ds.prec, d, N, planes, 0, 1, occ);
+                if ((long)smem > smem_max) continue;
+                int mc = 0;
+                cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, occ, &mc);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    why = cudaGetErrorString(e);
+                    continue;
+                }
+                if (mc <= 0) continue;
+                out.push_back(Shape{C, tpb, planes, 0, 1, occ, smem, mc});
+            }
+        }
+    }
+    const size_t n_rg = out.size();
+    for (int sg = 0; sg <= 1 && out.size() == n_rg; ++sg) {
         for (int paired = 1; paired >= 0; --paired) {
             for (int C : cands) {
                 if (N % C) continue;
@@ -359,7 +385,7 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
                 const int nb = paired ? 2 : 1;
                 const int need = std::max({nb * ef::collide_npc(d, N, C), paired ? rows : rows / 2,
                                            d == 3 ? nb * planes * H : 1});
-                const size_t smem = smem_for(ds.prec, d, N, planes, sg, paired);
+                const size_t smem = smem_for(ds.prec, d, N, planes, sg, paired, 1);
                 if ((long)smem > smem_max) continue;
                 for (int occ = 1; occ <= 2; ++occ) {
                     const int tmax = maxthreads_for(ds.prec, d, N, occ);
@@ -414,8 +440,8 @@ std::string device_key()
 std::string tune_key(const Desc &ds, int N)
 {
     char buf[256];
-    // "v3": kernel layout generation (threads per CTA count stage-A items; occupancy variants)
-    std::snprintf(buf, sizeof(buf), "v3 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
+    // "v4": kernel layout generation (variants 3 / 4: register-accumulator kernel)
+    std::snprintf(buf, sizeof(buf), "v4 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
                   ds.d, N, (int)ds.kernel, ds.R, ds.J, ds.nmu, ds.nphi, ds.nc, ds.sigma);
     return buf;
 }
@@ -460,6 +486,25 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
         return fail(EF_ERR_UNSUPPORTED, "no launch shape fits N=" + std::to_string(cp.N) + " on this device " + why);
     apply_shape(cp, shapes[0]);
     cp.prefetch = 0;
+    // EF_SHAPE="N:cluster:threads:variant[,...]" pins the launch shape of size N (tests, experiments);
+    // an entry that matches no candidate shape is ignored
+    if (const char *pin = std::getenv("EF_SHAPE")) {
+        std::string spec(pin);
+        size_t pos = 0;
+        while (pos < spec.size()) {
+            size_t end = spec.find(',', pos);
+            if (end == std::string::npos) end = spec.size();
+            int n = 0, C = 0, tpb = 0, occ = 0;
+            if (std::sscanf(spec.substr(pos, end - pos).c_str(), "%d:%d:%d:%d", &n, &C, &tpb, &occ) == 4 && n == cp.N) {
+                for (const Shape &sh : shapes)
+                    if (sh.cluster == C && sh.tpb == tpb && sh.occ == occ && sh.sg_global == 0) {
+                        apply_shape(cp, sh);
+                        return EF_OK;
+                    }
+            }
+            pos = end + 1;
+        }
+    }
     const char *env = std::getenv("EF_AUTOTUNE");
     const bool tune = ncells_tune > 0 && !(env && env[0] == '0') && shapes.size() > 1;
     if (!tune) return EF_OK;
@@ -515,7 +560,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
             a.sg_global = sh.sg_global;
             a.sg_ws = sgws;
             a.fh_ws = fhws;
-            a.npc = ef::collide_npc(d, cp.N, sh.cluster);
+            a.npc = ef::collide_npc_v(d, cp.N, sh.cluster, sh.occ);
             a.out_mode = ef::OUT_COLLIDE;
             a.h = 1.0;
             a.prefetch = pfv;
@@ -838,7 +883,7 @@ ef_status run(ef_plan_s *p, const void *F, void *Out, int64_t ncells, int mode, 
         a.sg_global = cp.sg_global;
         a.sg_ws = cp.d_sg;
         a.fh_ws = cp.d_fh;
-        a.npc = ef::collide_npc(ds.d, cp.N, cp.cluster);
+        a.npc = ef::collide_npc_v(ds.d, cp.N, cp.cluster, cp.occ);
         a.out_mode = mode;
         a.dt = dt;
         a.h = 2.0 * ds.L / cp.N;
@@ -1104,9 +1149,9 @@ cudaError_t features_launch(int prec, int d, int N, const FeatArgs &a, cudaStrea
     return prec == EF_PREC_F32 ? features_launch_f32(d, N, a, s) : features_launch_f64(d, N, a, s);
 }
 
-size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired)
+size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired, int occ)
 {
-    return smem_for(prec, d, N, planes, sg_global, paired);
+    return smem_for(prec, d, N, planes, sg_global, paired, occ);
 }
 
 cudaError_t collide_launch(int prec, int d, int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem,

@@ -558,7 +558,7 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
         a.planes = v.planes;
         a.paired = v.paired;
         a.fh_ws = s->fh;
-        a.npc = ef::collide_npc(v.d, v.N, v.cluster);
+        a.npc = ef::collide_npc_v(v.d, v.N, v.cluster, v.occ);
         a.out_mode = ef::OUT_COLLIDE;
         a.h = 2.0 * v.L / v.N;
         a.status = v.status;
