@@ -317,6 +317,25 @@ ef_status ef_classical_collide(ef_classical_t c, const double *F_dev, double *Q_
                                ef_stream_t stream);
 ef_status ef_classical_destroy(ef_classical_t c);
 
+/* The Fourier Galerkin method (FGM), the comparison method of Fig. 2 (Sec. 1.2, eq. FGM_Q, fast form
+ * eq. fastFGM): for cells of the N grid described by desc (uniform; N even with 2N a built size,
+ * i.e. N <= 32), Q = the grid values of sum_{k in K} Qh^G_k E_k with
+ *   Qh^G_k = sum_{l, m in K, l + m = k} (B(l,m) - B(m,m)) Fh_l Fh_m,   K = {-(N/2-1), ..., N/2-1}^d,
+ * the sum NOT reduced mod N (no aliasing), Fh the DFT of the grid values F (interpolation data),
+ * B the low-rank kernel of desc (its filter only if desc->sigma_enabled is 1; the FGM of the
+ * literature has none: pass 0).  Evaluated by zero padding: F is interpolated to the grid of 2N
+ * points, the collision kernels of ef_collide run there with multipliers restricted to K, and the
+ * result is projected back onto K.  ef_galerkin_create allocates the doubled-grid plan and
+ * scratch for max_cells cells (the only allocation); ef_galerkin_collide takes ncells <= max_cells
+ * cells (device pointers, layout as ef_collide) and allocates nothing; calls on one object share
+ * its scratch and must not overlap.  ef_galerkin_status reads the doubled-grid plan's status word
+ * (as ef_plan_status).  EF_ERR_UNSUPPORTED if 2N is not a built size. */
+typedef struct ef_galerkin_s *ef_galerkin_t;
+ef_status ef_galerkin_create(const ef_plan_desc *desc, int64_t max_cells, ef_galerkin_t *out);
+ef_status ef_galerkin_collide(ef_galerkin_t g, const void *F_dev, void *Q_dev, int64_t ncells, ef_stream_t stream);
+ef_status ef_galerkin_status(ef_galerkin_t g, int sync, int reset);
+ef_status ef_galerkin_destroy(ef_galerkin_t g);
+
 /* Streaming a batch that lives in host memory (no counterpart in the paper; the paper's method
  * is per cell).  The cells (sizes N_host[c], back to back as for ef_plan_create_batched) are cut
  * into nchunks contiguous chunks of about equal work, each with its own batched plan and CUDA

@@ -82,6 +82,7 @@ def _load():
                                               ctypes.c_double, ctypes.c_double]
         lib.oracle_classical_bhat.restype = ctypes.c_double
         lib.oracle_collide_classical.argtypes = [pp, dp, dp]
+        lib.oracle_collide_galerkin.argtypes = [pp, dp, dp]
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -200,6 +201,18 @@ def collide_classical(p: Params, F: np.ndarray) -> np.ndarray:
     assert p.d == 3 and F.shape == (p.N,) * 3
     Q = np.zeros_like(F)
     if _load().oracle_collide_classical(ctypes.byref(p.c()), _dp(F), _dp(Q)):
+        raise ValueError("bad parameters")
+    return Q
+
+
+def collide_galerkin(p: Params, F: np.ndarray) -> np.ndarray:
+    """The Fourier Galerkin method's collision term (eq. FGM_Q) on the grid: the unaliased sum over
+    l + m = k in K (even N: modes with a component -N/2 dropped), the plan's low-rank kernel, the
+    filter only if p.filter; Fh from the DFT of the grid values."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    assert F.shape == (p.N,) * p.d
+    Q = np.zeros_like(F)
+    if _load().oracle_collide_galerkin(ctypes.byref(p.c()), _dp(F), _dp(Q)):
         raise ValueError("bad parameters")
     return Q
 

@@ -27,6 +27,8 @@
  *   - the DVM form eq. Qsr with A^sigma from eq. A_simplified / tildetildeA, by brute force over
  *     (p, q, s), O(N^{3d}), for tiny grids (oracle_dvm);
  *   - G(y, z) of eq. G / tildeG on the grid (oracle_G), for the positivity checks of Sec. 3.2;
+ *   - the Fourier Galerkin method's unaliased sum (oracle_collide_galerkin, eq. FGM_Q), the
+ *     comparison method of Fig. 2;
  *   - the entropic Fourier method on the classical form of the collision operator (remark after
  *     eq. EFMk) for 3D Maxwell molecules, B_hat from eq. classical_hatB with its angular and
  *     radial integrals done in closed form, by the plain double sum (oracle_collide_classical).
@@ -422,6 +424,66 @@ int oracle_collide(const oracle_params *p, const double *F, double *Q)
     }
     oracle_idft_real(p->d, p->N, Qr, Qi, Q);
     free(Fr); free(Fi); free(Qr); free(Qi); free(bmm); free_tables(&kt);
+    return 0;
+}
+
+/* ------------------------------------------ Fourier Galerkin method (Sec. 1.2) ------------ */
+
+/* The Fourier Galerkin method (FGM, eq. FGM_Q / eq. FG): the unaliased sum
+ *   Qh^G_k = sum_{l, m in K, l + m = k} (B(l,m) - B(m,m)) Fh_l Fh_m,   k in K,
+ * with K = {-n, ..., n}^d, n = (N-1)/2 (odd N) or N/2 - 1 (even N: the modes with a component
+ * -N/2 are dropped, Sec. 4.1), B the plan's low-rank kernel (eq. fastFGM) with the filter if
+ * p->filter is set (the FGM of the literature has none), and Fh the DFT of the grid values (the
+ * interpolation initial data of Fig. 2).  Q = the grid values of sum_k Qh^G_k E_k.  Unlike the
+ * collocation sum (oracle_collide) the index l + m is not reduced mod N: modes that leave K are
+ * discarded.  O(R N^{2d}). */
+int oracle_collide_galerkin(const oracle_params *p, const double *F, double *Q)
+{
+    kern_tables kt;
+    if (make_tables(p, &kt)) { free_tables(&kt); return -1; }
+    const int64_t M = kt.M;
+    const int N = p->N, d = p->d;
+    const int n = (N % 2) ? (N - 1) / 2 : N / 2 - 1;
+    double *Fr = malloc(sizeof(double) * M), *Fi = malloc(sizeof(double) * M);
+    double *Qr = malloc(sizeof(double) * M), *Qi = malloc(sizeof(double) * M);
+    double *bmm = malloc(sizeof(double) * M);
+    int *in = malloc(sizeof(int) * M);
+    oracle_dft(d, N, F, Fr, Fi);
+    for (int64_t l = 0; l < M; ++l) {
+        int64_t r = l;
+        int ok = 1;
+        for (int a = 0; a < d; ++a) { int k = mode_of(N, (int)(r % N)); r /= N; if (k < -n || k > n) ok = 0; }
+        in[l] = ok;
+        if (!ok) { Fr[l] = 0.0; Fi[l] = 0.0; }
+        bmm[l] = bsig(&kt, l, l);
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < M; ++k) {
+        double re = 0.0, im = 0.0;
+        if (in[k]) {
+            for (int64_t l = 0; l < M; ++l) {
+                if (!in[l]) continue;
+                /* m = k - l componentwise, without reduction; skip if it leaves K */
+                int64_t kk = k, ll = l, m = 0, mul = 1;
+                int ok = 1;
+                for (int a = 0; a < d; ++a) {
+                    const int ka = mode_of(N, (int)(kk % N)), la = mode_of(N, (int)(ll % N));
+                    kk /= N; ll /= N;
+                    const int ma = ka - la;
+                    if (ma < -n || ma > n) { ok = 0; break; }
+                    m += (int64_t)((ma + N) % N) * mul;
+                    mul *= N;
+                }
+                if (!ok) continue;
+                const double b = bsig(&kt, l, m) - bmm[m];
+                re += b * (Fr[l] * Fr[m] - Fi[l] * Fi[m]);
+                im += b * (Fr[l] * Fi[m] + Fi[l] * Fr[m]);
+            }
+        }
+        Qr[k] = re; Qi[k] = im;
+    }
+    oracle_idft_real(d, N, Qr, Qi, Q);
+    free(Fr); free(Fi); free(Qr); free(Qi); free(bmm); free(in); free_tables(&kt);
     return 0;
 }
 

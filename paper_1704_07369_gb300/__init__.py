@@ -36,6 +36,7 @@ EF_DIAG_STRIDE = 10
 SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_plan_destroy",
            "ef_collide", "ef_euler_step", "ef_rk3_step", "ef_moments_entropy", "ef_plan_status",
            "ef_plan_set_graph", "ef_plan_info", "ef_plan_class_info", "ef_plan_reserve", "ef_collide_noalloc", "ef_kernel_G",
+           "ef_galerkin_create", "ef_galerkin_collide", "ef_galerkin_status", "ef_galerkin_destroy",
            "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_status", "ef_mlp_params",
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
@@ -90,6 +91,10 @@ def lib():
         L.ef_mlp_status.argtypes = [vp, i32, i32]
         L.ef_plan_reserve.argtypes = [vp, i64]
         L.ef_kernel_G.argtypes = [vp, i64, vp, vp]
+        L.ef_galerkin_create.argtypes = [ctypes.POINTER(ef_plan_desc), i64, pp]
+        L.ef_galerkin_collide.argtypes = [vp, vp, vp, i64, vp]
+        L.ef_galerkin_status.argtypes = [vp, i32, i32]
+        L.ef_galerkin_destroy.argtypes = [vp]
         L.ef_mlp_params.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_mlp_forward.argtypes = [vp, vp, i32, vp, i32, i64, vp]
         L.ef_mlp_grad.argtypes = [vp, vp, i32, vp, i32, vp, vp, i64, vp, vp, vp]
@@ -338,6 +343,35 @@ class StreamPlan:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             lib().ef_stream_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Galerkin:
+    """Owning wrapper of an ``ef_galerkin_t``: the Fourier Galerkin method (unaliased sum over the
+    mode set K of the N grid, by zero padding to the 2N grid), the comparison method of Fig. 2."""
+
+    def __init__(self, d, N, L, kernel, R, prec, max_cells, R_tr=0.0, n_mu=0, n_phi=0, n_c=0, J=0, sigma_enabled=0):
+        desc = ef_plan_desc(d, N, float(L), kernel, R, prec, float(R_tr), n_mu, n_phi, n_c, J, sigma_enabled)
+        self.handle = ctypes.c_void_p()
+        _check(lib().ef_galerkin_create(ctypes.byref(desc), int(max_cells), ctypes.byref(self.handle)))
+        self.d, self.N = d, N
+
+    def collide(self, F, Q, ncells=None, stream=None):
+        n = ncells if ncells is not None else F.numel() // self.N ** self.d
+        _check(lib().ef_galerkin_collide(self.handle, _ptr(F), _ptr(Q), int(n), _stream(stream)))
+
+    def status(self, sync=1, reset=0):
+        return lib().ef_galerkin_status(self.handle, int(sync), int(reset))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ef_galerkin_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -6,6 +6,7 @@
 
 #include <cstddef>
 
+#include "ef.h"
 #include "ef_internal.h"
 
 namespace ef {
@@ -49,6 +50,8 @@ struct PlanView {
     int device;
 };
 bool plan_view(const struct ef_plan_s *p, PlanView *out);
+// uniform plan on the doubled grid 2N with multipliers restricted to the N grid's Galerkin modes
+ef_status plan_create_padded(const ef_plan_desc *desc, struct ef_plan_s **out);
 
 // Axis-0 pencils per CTA of a C-CTA cluster (even, so that lane pairs never straddle CTAs) and the
 // bytes of one cluster's forward-spectrum workspace (N x NP complex).

@@ -137,6 +137,8 @@ struct Desc {
     double L, T, Rtr;
     ef_kernel kernel;
     ef_precision prec;
+    int gal_N = 0;      // > 0: a zero-padded Galerkin plan (grid N = 2 gal_N) whose multipliers keep
+                        // only the modes of the gal_N grid's set K (|k_a| <= gal_N/2 - 1)
 };
 
 // Directions and gain pairs of the low-rank kernel (independent of N).
@@ -619,7 +621,11 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
     const int64_t per = (int64_t)N * NP;
     std::vector<double> tab((size_t)(ndir + 1) * per, 0.0);
     std::vector<double> sig1(N);
-    for (int i = 0; i < N; ++i) sig1[i] = jackson(N, mode_of(N, i), ds.sigma != 0);
+    for (int i = 0; i < N; ++i) {
+        const int k = mode_of(N, i);
+        if (ds.gal_N > 0) sig1[i] = std::abs(k) <= ds.gal_N / 2 - 1 ? jackson(ds.gal_N, k, ds.sigma != 0) : 0.0;
+        else sig1[i] = jackson(N, k, ds.sigma != 0);
+    }
     RadialEval rad(ds.T, ds.Rtr);
     parallel_for((int64_t)ndir * per, [&](int64_t idx) {
         const int u = (int)(idx / per);
@@ -975,6 +981,42 @@ ef_status ef_plan_create_ex(const ef_plan_desc *desc, ef_plan_t *out)
     *out = p;
     return EF_OK;
 }
+
+}  // extern "C"
+
+namespace ef {
+
+// A uniform plan on the grid of 2 N points per axis whose multiplier tables keep only the modes of
+// the N grid's Galerkin set (used by ef_galerkin_*: products of band-limited factors do not wrap on
+// the doubled grid).  desc describes the N-grid discretisation.
+ef_status plan_create_padded(const ef_plan_desc *desc, ef_plan_t *out)
+{
+    if (!out) return fail(EF_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    Desc ds;
+    ef_status st = fill_desc(desc, ds);
+    if (st != EF_OK) return st;
+    if (desc->N < 8 || desc->N % 2) return fail(EF_ERR_INVALID_ARG, "N must be even and >= 8");
+    ds.gal_N = desc->N;
+    ds.N = 2 * desc->N;
+    st = check_N(ds, ds.N);
+    if (st != EF_OK) return fail(EF_ERR_UNSUPPORTED, "the doubled grid 2N = " + std::to_string(ds.N) + " is not a built size");
+    ef_plan_s *p = new ef_plan_s();
+    p->desc = ds;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaGetDevice"); }
+    ClassPlan cp;
+    cp.N = ds.N;
+    p->classes.push_back(cp);
+    st = finish_plan(p);
+    if (st != EF_OK) { destroy_plan(p); return st; }
+    *out = p;
+    return EF_OK;
+}
+
+}  // namespace ef
+
+extern "C" {
 
 ef_status ef_plan_create(int d, int N, double L, ef_kernel kernel, int R, ef_precision prec, ef_plan_t *out)
 {

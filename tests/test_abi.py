@@ -68,7 +68,7 @@ def test_no_operation_allocates_or_synchronises():
     allowed = re.compile(r"^(ef_plan_create\w*|ef_plan_reserve|ef_plan_destroy|ef_plan_status|ef_mlp_status|"
                          r"ef_mlp_create|ef_mlp_destroy|ef_mlp_params|ef_surrogate_create|ef_surrogate_destroy|"
                          r"ef_surrogate_stats|ef_stream_plan_create|ef_stream_plan_destroy|ef_classical_create|"
-                         r"ef_classical_destroy|choose_shape|upload_table|build_class|alloc_workspaces|"
+                         r"ef_classical_destroy|ef_galerkin_create|gfree|choose_shape|upload_table|build_class|alloc_workspaces|"
                          r"destroy_plan|finish_plan|cfree|\w*_free)$")
     csrc = os.path.join(ROOT, "paper_1704_07369_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):

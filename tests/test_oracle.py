@@ -176,6 +176,34 @@ def test_sampled_evaluators_equal_the_full_sum(case):
     assert np.abs(oracle.collide_points_fft(p, F, idx) - Q).max() <= 1e-13 * scale
 
 
+@pytest.mark.parametrize("case", [dict(d=2, N=12, kernel=0, R=8, filter=False), dict(d=2, N=12, kernel=0, R=8, filter=True),
+                                  dict(d=3, N=8, kernel=1, R=16, filter=False)])
+def test_galerkin_sum_equals_collocation_for_band_limited_data(case):
+    """The Fourier Galerkin sum (eq. FGM_Q) differs from the collocation sum (eq. Qsk) only by the
+    products l + m that leave the mode set and wrap mod N.  For F whose spectrum lies in
+    |k_a| <= N/4 - 1 no product wraps, so the two must agree; for generic F they must not."""
+    rng = np.random.default_rng(21)
+    N, d = case["N"], case["d"]
+    p = oracle.Params(T=8.0, **case)
+    X = np.zeros((N,) * d, dtype=complex)
+    band = N // 4 - 1
+    ks = [list(range(0, band + 1)) + list(range(N - band, N))] * d
+    for idx in np.ndindex(*[len(k) for k in ks]):
+        X[tuple(ks[a][i] for a, i in enumerate(idx))] = rng.normal() + 1j * rng.normal()
+    F = np.real(np.fft.ifftn(X)) * N ** d + 3.0
+    Qg = oracle.collide_galerkin(p, F)
+    Qc = oracle.collide(p, F)
+    assert np.abs(Qg - Qc).max() <= 1e-12 * np.abs(Qc).max()
+    G = rng.random((N,) * d) + 0.1                          # generic data: aliasing present
+    Qg, Qc = oracle.collide_galerkin(p, G), oracle.collide(p, G)
+    assert np.abs(Qg - Qc).max() >= 1e-4 * np.abs(Qc).max()
+    # mass is conserved exactly (B(l,-l) = B(-l,-l) by eq. sym_B) and translation commutes
+    assert abs(Qg.sum()) <= 1e-13 * np.abs(Qg).sum()
+    shift = tuple(range(d))
+    Qs = oracle.collide_galerkin(p, np.roll(G, 1, axis=shift))
+    assert np.abs(Qs - np.roll(Qg, 1, axis=shift)).max() <= 1e-12 * np.abs(Qg).max()
+
+
 def test_unfiltered_kernel_is_not_positive_fig1():
     """Fig. 1: 2D, B~ = 1/pi, R = 6, N = 32, z = (T/2, T/2): G takes negative values without the
     filter and is non-negative with it (Sec. 3.2.1 / 3.2.2)."""
