@@ -66,9 +66,22 @@ def n_ops(R=R_RANK):
 
 
 def flops_per_cell(N, R=R_RANK):
-    """Algorithmic FP32 flops of one collision evaluation of one cell: (1 + n_ops) real 3D FFTs at
-    2.5 M log2 M flops each (M = N^3), the spectral multiply (2 flops per half-spectrum complex
-    value, M per op) and the accumulate (2 flops per real point per op)."""
+    """Algorithmic FP32 flops of one collision evaluation of one cell, counted as the work model of
+    the hot-path scope: (#transforms) real 3D FFTs at 2.5 M log2 M flops each (M = N^3) plus 2 R M
+    for the R-term products, with #transforms = n_mu n_phi (1 + n_c) + 2 for the hard-sphere
+    decomposition (a transform per first direction, one per partner direction, the forward
+    transform and the loss): 26 for R = 32.  The kernel itself runs fewer transforms (see
+    executed_flops_per_cell), so this is the work of the method, not of the implementation."""
+    table = {32: (2, 4, 2), 64: (2, 4, 4)}
+    nmu, nphi, nc = table[R]
+    M = float(N) ** 3
+    return (nmu * nphi * (1 + nc) + 2) * 2.5 * M * np.log2(M) + 2.0 * R * M
+
+
+def executed_flops_per_cell(N, R=R_RANK):
+    """The flops the kernel actually executes under the same per-transform count: 1 forward and
+    n_ops inverse transforms (partners folded by linearity), the spectral multiply (2 flops per
+    half-spectrum complex value) and the accumulate (2 flops per point per op)."""
     M = float(N) ** 3
     ops = n_ops(R)
     return (1 + ops) * 2.5 * M * np.log2(M) + ops * (M + 2.0 * M)
@@ -322,8 +335,12 @@ def run_ours(args, world, rank, local):
             tj = json.load(f)
         if tj.get("kernel_hash") == ef_kernel_hash():
             traffic = tj.get("bytes_per_launch_full_step")
+    exec_tf = float(sum(executed_flops_per_cell(int(n)) for n in Ns)) / nlaunch / per_launch_s / 1e12
     roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved_tf / fp32_peak, "traffic": traffic,
+            "work_model": "(n_mu n_phi (1 + n_c) + 2) 2.5 M log2 M + 2 R M flops per cell, M = N^3 (26 transforms at R = 32)",
+            "executed": {"TFLOP_s": exec_tf, "frac": exec_tf / fp32_peak,
+                         "model": "18 transforms per cell actually run (partners folded by linearity)"},
             "peak_source": "FP32 CUDA-core peak from unit counts: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
             "hbm_view": {"achieved_GBps": bytes_step / step_s / 1e9, "peak_GBps": hbm_peak,
                          "frac": bytes_step / step_s / 1e9 / hbm_peak, "peak_source": hbm_src}}
@@ -372,12 +389,144 @@ def run_ours(args, world, rank, local):
         line["surrogate"] = surrogate_leg(args, device)
     if not args.no_kernels and world == 1:
         line["hbm_kernels"] = hbm_kernels_leg(device)
+    if not args.no_precision and world == 1:
+        line["precision"] = precision_leg(device)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline()
     elif not args.no_cpu_baseline:
         line["cpu_baseline"] = None
     print(json.dumps(line), flush=True)
     return 0
+
+
+# -------------------------------------------------------------- precision and small configs -
+
+def precision_leg(device):
+    """The workloads besides the batched step, each timed on the GPU (CUDA events) and compared with
+    the FP64 oracle:
+      config 4 (precision study): 256 BKW-family cells, 3D, N = 64, L = 10, hard spheres, R = 64, in
+        FP32 and FP64; errors against the oracle at sampled points of two cells (the points where
+        |Q| peaks among them), the mass each path puts into Q (exactly zero for the oracle's sum,
+        eq. Qsk at k = 0), and the entropy production sum Q ln F per cell, FP32 against FP64 (the
+        FP64 path being the one that matches the oracle to 1e-12);
+      config 2: one BKW cell (t0 = 5.5), 3D, N = 32, L = 8, Maxwell molecules, R = 32, 200 Euler
+        steps in FP64 and FP32: time per step, distance to the BKW solution at the end, FP32
+        against FP64; the oracle's time per evaluation measured at N = 16 and extrapolated to
+        N = 32 with the direct sum's N^6 cost;
+      config 1: the 2D bi-Gaussian, N = 16, L = 8, Maxwell, R = 16, FP64: one evaluation plus 100
+        Euler steps, GPU against the oracle step by step (time per step on both)."""
+    import torch
+
+    import oracle
+    import paper_1704_07369_gb300 as ef
+    from paper_1704_07369_gb300 import inputs
+    out = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    try:
+        oracle.build()
+        # ---- config 4
+        N, L, R, n = 64, 10.0, 64, 256
+        cells = inputs.bkw_family_cells(3, N, L, n, seed=4321)
+        c4 = {"workload": "256 BKW-family cells, 3D, N=64, L=10, hard spheres, R=64", "cells": n}
+        Q = {}
+        for prec, name in ((ef.EF_PREC_F32, "fp32"), (ef.EF_PREC_F64, "fp64")):
+            plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, R, prec)
+            dt = torch.float32 if prec == ef.EF_PREC_F32 else torch.float64
+            F = torch.tensor(cells, dtype=dt, device=device)
+            Qd = torch.empty_like(F)
+            ms = timed(lambda: plan.collide(F, Qd, ncells=n), 3)
+            mom = torch.zeros(n, ef.EF_DIAG_STRIDE, dtype=torch.float64, device=device)
+            plan.moments(F, Qd, mom, ncells=n)
+            torch.cuda.synchronize()
+            c4[name + "_ms"] = ms
+            c4[name + "_cells_per_s"] = n / ms * 1e3
+            c4[name + "_status"] = int(plan.status(sync=1, reset=1))
+            h3 = (2 * L / N) ** 3
+            mass = mom[:, 0].double().cpu().numpy()
+            dmass = Qd.double().sum(dim=(1, 2, 3)).cpu().numpy() * h3
+            c4.setdefault("mass_of_Q_rel", {})[name] = float(np.abs(dmass / mass).max())
+            Q[name] = (Qd[:2].double().cpu().numpy(), mom[:, 6].cpu().numpy())
+            del F, Qd, plan
+            torch.cuda.empty_cache()
+        p4 = oracle.Params(d=3, N=N, T=L, kernel=oracle.KERNEL_HARD_SPHERE, R=R, J=6)
+        err32, err64, npts = 0.0, 0.0, 0
+        for i in range(2):
+            q32, q64 = Q["fp32"][0][i].ravel(), Q["fp64"][0][i].ravel()
+            idx = np.unique(np.concatenate([np.argsort(np.abs(q64))[-8:], np.random.default_rng(i).integers(0, q64.size, 56)]))
+            ref = oracle.collide_points_fft(p4, cells[i], idx)
+            sc = np.abs(ref).max()
+            err32 = max(err32, float(np.abs(q32[idx] - ref).max() / sc))
+            err64 = max(err64, float(np.sqrt(((q64[idx] - ref) ** 2).sum() / (ref ** 2).sum())))
+            npts += idx.size
+        c4["Q_vs_oracle_sampled"] = {"fp32_rel_linf_of_max": err32, "fp64_rel_l2": err64, "points": npts, "cells": 2}
+        P32, P64 = Q["fp32"][1], Q["fp64"][1]
+        c4["entropy_production_fp32_vs_fp64"] = {"max_rel": float(np.abs((P32 - P64) / P64).max()),
+                                                 "same_sign": bool(np.all(np.sign(P32) == np.sign(P64))),
+                                                 "all_nonpositive_fp64": bool(np.all(P64 <= 0))}
+        out["config4"] = c4
+        # ---- config 2
+        N, L, R, steps = 32, 8.0, 32, 200
+        F0 = inputs.bkw(3, N, L, 5.5)
+        c2 = {"workload": "BKW t0=5.5, 3D, N=32, L=8, Maxwell, R=32, 200 Euler steps dt=0.01"}
+        fin = {}
+        for prec, name in ((ef.EF_PREC_F64, "fp64"), (ef.EF_PREC_F32, "fp32")):
+            plan = ef.Plan(3, N, L, ef.EF_KERNEL_MAXWELL, R, prec)
+            dt = torch.float32 if prec == ef.EF_PREC_F32 else torch.float64
+            F = torch.tensor(F0[None], dtype=dt, device=device)
+            torch.cuda.synchronize()
+            ev[0].record()
+            plan.euler(F, 0.01, nsteps=steps, ncells=1)
+            ev[1].record()
+            torch.cuda.synchronize()
+            c2[name + "_ms_per_step"] = ev[0].elapsed_time(ev[1]) / steps
+            c2[name + "_status"] = int(plan.status(sync=1, reset=1))
+            fin[name] = F[0].double().cpu().numpy()
+        ex = inputs.bkw(3, N, L, 5.5 + steps * 0.01)
+        for name in ("fp64", "fp32"):
+            c2[name + "_rel_l2_vs_bkw_end"] = float(np.sqrt(((fin[name] - ex) ** 2).sum() / (ex ** 2).sum()))
+        c2["fp32_vs_fp64_rel_linf"] = float(np.abs(fin["fp32"] - fin["fp64"]).max() / np.abs(fin["fp64"]).max())
+        t0 = time.perf_counter()
+        oracle.collide(oracle.Params(d=3, N=16, T=L, kernel=ef.EF_KERNEL_MAXWELL, R=R, J=6), inputs.bkw(3, 16, L, 5.5))
+        t16 = time.perf_counter() - t0
+        c2["oracle_s_per_eval"] = {"N16_measured": t16, "N32_extrapolated_N6": t16 * 64.0, "cores": oracle.num_threads()}
+        out["config2"] = c2
+        # ---- config 1
+        N, L, R = 16, 8.0, 16
+        F0 = inputs.bigauss2d(N, L)
+        plan = ef.Plan(2, N, L, ef.EF_KERNEL_MAXWELL, R, ef.EF_PREC_F64)
+        F = torch.tensor(F0[None], dtype=torch.float64, device=device)
+        Qd = torch.empty_like(F)
+        ms_q = timed(lambda: plan.collide(F, Qd, ncells=1), 20)
+        torch.cuda.synchronize()
+        ev[0].record()
+        plan.euler(F, 0.01, nsteps=100, ncells=1)
+        ev[1].record()
+        torch.cuda.synchronize()
+        gpu_step = ev[0].elapsed_time(ev[1]) / 100
+        p1 = oracle.Params(d=2, N=N, T=L, kernel=oracle.KERNEL_MAXWELL, R=R)
+        t0 = time.perf_counter()
+        Fo = oracle.euler(p1, F0, 0.01, steps=100)
+        o_step = (time.perf_counter() - t0) / 100 * 1e3
+        out["config1"] = {"workload": "2D bi-Gaussian, N=16, L=8, Maxwell, R=16, FP64, 1 evaluation + 100 Euler steps",
+                          "gpu_ms_per_eval": ms_q, "gpu_ms_per_step": gpu_step, "oracle_ms_per_step": o_step,
+                          "oracle_cores": oracle.num_threads(),
+                          "rel_l2_vs_oracle_after_100": float(np.sqrt(((F[0].cpu().numpy() - Fo) ** 2).sum() / (Fo ** 2).sum())),
+                          "status": int(plan.status(sync=1, reset=1))}
+        return out
+    except Exception as exc:          # reported, never fatal to the bench line
+        out["error"] = "%s: %s" % (type(exc).__name__, exc)
+        return out
 
 
 # -------------------------------------------------------------- HBM-bound kernels ----------
@@ -574,6 +723,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-kernels", action="store_true", help="skip the HBM-bound kernels' timings")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision study (N = 64) and the small configurations' timings")
     ap.add_argument("--chunks", type=int, default=8, help="chunks of the streamed end-to-end leg")
     ap.add_argument("--strong", action="store_true",
                     help="split one --cells batch over the ranks (default: a batch per rank)")

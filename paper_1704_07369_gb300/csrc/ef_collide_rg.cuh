@@ -37,12 +37,20 @@ __host__ __device__ constexpr int rg_plane_stride()
     constexpr int s = N * rg_row_stride<N>();
     return s + ((8 - s % 16) + 16) % 16;
 }
-// threads per CTA the (N, RPT) instantiation is compiled for (launch bound, one CTA per SM)
-template <int N, int RPT>
-__host__ __device__ constexpr int rg_max_threads()
+// Instantiations ("variants", one CTA per SM each): 1 = one row per thread with the size's widest
+// launch bound, 2 = two rows per thread, 3 = one row per thread with at most 200 threads (N = 40,
+// 48: 7 warps keep 255 registers, where the widest bound leaves 168).  rg_bound is the launch bound
+// (0: not built).
+template <int N, int V>
+__host__ __device__ constexpr int rg_bound()
 {
-    return N == 40 ? 320 : (N == 32 || N == 64) ? 256 : 288;
+    if (V == 1) return N == 40 ? 320 : (N == 32 || N == 64) ? 256 : 288;
+    if (V == 2) return N == 16 ? 128 : N == 24 ? 288 : N == 32 ? 256 : N == 40 ? 200 : N == 48 ? 192 : 128;
+    if (V == 3) return (N == 40 || N == 48) ? 200 : 0;
+    return 0;
 }
+template <int V>
+__host__ __device__ constexpr int rg_rpt() { return V == 2 ? 2 : 1; }
 template <int N>
 __host__ __device__ constexpr bool rg_built() { return N == 16 || N == 24 || N == 32 || N == 40 || N == 48 || N == 64; }
 
@@ -56,7 +64,8 @@ __host__ __device__ inline int rg_npc(int N, int C)
 template <int N>
 __host__ __device__ constexpr size_t rg_smem_bytes(int planes, int npc)
 {
-    return (size_t)2 * planes * rg_plane_stride<N>() * 8 + (size_t)N * npc * 8 + (32 + 1) * kDiag * sizeof(double) + 16;
+    return (size_t)2 * planes * rg_plane_stride<N>() * 8 + (size_t)N * npc * 8 + (32 + 1) * kDiag * sizeof(double) + 16 +
+           32 * sizeof(float);
 }
 
 // in-plane offset of the even pencil of a lane pair: pencil q (even) -> (k_y, k_x) = (q / (N/2), q % (N/2))
@@ -131,8 +140,8 @@ __device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, const C2<float>
     fft<N, 1, N>(z);
 }
 
-template <int D, int N, int RPT>
-__global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg(const CollideArgs a)
+template <int D, int N, int RPT, int LB>
+__global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
 {
     static_assert(D == 3, "3D only");
     using T = float;
@@ -163,6 +172,7 @@ __global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg
     double *part = reinterpret_cast<double *>(Fs + (size_t)N * NPC);     // [32 warps + 1][kDiag]
     long long *s_cell = reinterpret_cast<long long *>(part + (32 + 1) * kDiag);
     int *s_nubig = reinterpret_cast<int *>(s_cell + 1);
+    float *s_maxnu = reinterpret_cast<float *>(s_cell + 2);          // [32 warps] max nu of the loss op
     const uint32_t base0 = smem_u32addr(Is0), base1 = smem_u32addr(Is1);
 
     const unsigned long long pm = (0x100000000ull + (unsigned)P - 1u) / (unsigned)P;
@@ -236,8 +246,9 @@ __global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg
         }
         bar.full();                        // Fs complete; every slab free again
 
+        // the diagnostics accumulate only in the last op (reset there), so they hold no registers
+        // through the earlier ops; the loss op's max nu goes to shared memory per warp
         Diag dg;
-        dg.reset();
         T g[RPT][N];                       // gain accumulator of this thread's rows tid + j nt
 
         for (int o = 0; o < a.nops; ++o) {
@@ -285,6 +296,7 @@ __global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg
             if (pair) {
                 const bool last = op.kind == OP_PAIR_LAST;
                 const bool big = *s_nubig != 0;
+                if (last) dg.reset();
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
                     const int r = tid + j * nt;
@@ -308,6 +320,7 @@ __global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg
                 // the loss (first op): nu of this thread's rows, G = -F nu.  With two rows per
                 // thread they share one complex transform; with one, the second input is zero.
                 bool bigt = false;
+                T mxt = T(-3.0e38);
                 if constexpr (RPT == 2) {
                     const int r0 = tid, r1 = tid + nt;
                     C2<T> z[N];
@@ -325,7 +338,7 @@ __global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg
                             mx = nu > mx ? nu : mx;
                             if (T(a.dt) * nu > T(1)) bigt = true;
                         }
-                        dg.max_nu = fmax(dg.max_nu, (double)mx);
+                        mxt = mx > mxt ? mx : mxt;
                     }
                 } else {
 #pragma unroll
@@ -352,20 +365,26 @@ __global__ void __launch_bounds__(rg_max_threads<N, RPT>(), 1) collide_kernel_rg
                             mx = nu > mx ? nu : mx;
                             if (T(a.dt) * nu > T(1)) bigt = true;
                         }
-                        dg.max_nu = fmax(dg.max_nu, (double)mx);
+                        mxt = mx > mxt ? mx : mxt;
                     }
                 }
                 if (bigt && a.out_mode == OUT_EULER) *s_nubig = 1;
+#pragma unroll
+                for (int o2 = 16; o2 > 0; o2 >>= 1) {
+                    const T u = __shfl_xor_sync(0xffffffffu, mxt, o2);
+                    mxt = u > mxt ? u : mxt;
+                }
+                if (lane == 0) s_maxnu[tid >> 5] = mxt;
             }
             bar.war();
         }
 
         // ---------------- per-cell FP64 reduction of the diagnostics
         if (a.diag) {
-            dg.sum[7] = dg.min_f;
-            dg.sum[8] = dg.max_nu;
-            dg.sum[9] = dg.min_out;
             const int warp = tid >> 5, nw = (nt + 31) >> 5;
+            dg.sum[7] = dg.min_f;
+            dg.sum[8] = lane == 0 ? (double)s_maxnu[warp] : -1e300;
+            dg.sum[9] = dg.min_out;
 #pragma unroll
             for (int k = 0; k < kDiag; ++k) {
                 double v = dg.sum[k];

@@ -7,19 +7,31 @@ namespace ef {
 
 namespace {
 
-template <int N>
-cudaError_t rg_setup_n(int rpt, size_t smem, int cluster, int tpb, int *max_clusters)
+template <int N, int V>
+constexpr auto rg_kernel()
 {
-    if (rpt == 1) return setup_kernel(collide_kernel_rg<3, N, 1>, smem, cluster, tpb, max_clusters);
-    if (rpt == 2) return setup_kernel(collide_kernel_rg<3, N, 2>, smem, cluster, tpb, max_clusters);
+    return collide_kernel_rg<3, N, rg_rpt<V>(), (rg_bound<N, V>() > 0 ? rg_bound<N, V>() : 32)>;
+}
+
+template <int N>
+cudaError_t rg_setup_n(int v, size_t smem, int cluster, int tpb, int *max_clusters)
+{
+    if (v == 1) return setup_kernel(rg_kernel<N, 1>(), smem, cluster, tpb, max_clusters);
+    if (v == 2) return setup_kernel(rg_kernel<N, 2>(), smem, cluster, tpb, max_clusters);
+    if constexpr (rg_bound<N, 3>() > 0) {
+        if (v == 3) return setup_kernel(rg_kernel<N, 3>(), smem, cluster, tpb, max_clusters);
+    }
     return cudaErrorInvalidValue;
 }
 
 template <int N>
-cudaError_t rg_launch_n(int rpt, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s)
+cudaError_t rg_launch_n(int v, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s)
 {
-    if (rpt == 1) return launch_kernel(collide_kernel_rg<3, N, 1>, a, grid_clusters, tpb, smem, s);
-    if (rpt == 2) return launch_kernel(collide_kernel_rg<3, N, 2>, a, grid_clusters, tpb, smem, s);
+    if (v == 1) return launch_kernel(rg_kernel<N, 1>(), a, grid_clusters, tpb, smem, s);
+    if (v == 2) return launch_kernel(rg_kernel<N, 2>(), a, grid_clusters, tpb, smem, s);
+    if constexpr (rg_bound<N, 3>() > 0) {
+        if (v == 3) return launch_kernel(rg_kernel<N, 3>(), a, grid_clusters, tpb, smem, s);
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -27,16 +39,18 @@ cudaError_t rg_launch_n(int rpt, const CollideArgs &a, int grid_clusters, int tp
 
 #define EF_RG_SIZES(X) X(16) X(24) X(32) X(40) X(48) X(64)
 
-int rg_maxthreads_f32(int N, int rpt)
+int rg_maxthreads_f32(int N, int v)
 {
-    if (rpt != 1 && rpt != 2) return 0;
+    if (v < 1 || v > 3) return 0;
     switch (N) {
-#define EF_CASE(n) case n: return rpt == 1 ? rg_max_threads<n, 1>() : rg_max_threads<n, 2>();
+#define EF_CASE(n) case n: return v == 1 ? rg_bound<n, 1>() : v == 2 ? rg_bound<n, 2>() : rg_bound<n, 3>();
         EF_RG_SIZES(EF_CASE)
 #undef EF_CASE
     default: return 0;
     }
 }
+
+int rg_rows_per_thread(int v) { return v == 2 ? 2 : 1; }
 
 size_t rg_smem_f32(int N, int planes)
 {
@@ -48,20 +62,20 @@ size_t rg_smem_f32(int N, int planes)
     }
 }
 
-cudaError_t rg_setup_f32(int N, int rpt, size_t smem, int cluster, int tpb, int *max_clusters)
+cudaError_t rg_setup_f32(int N, int v, size_t smem, int cluster, int tpb, int *max_clusters)
 {
     switch (N) {
-#define EF_CASE(n) case n: return rg_setup_n<n>(rpt, smem, cluster, tpb, max_clusters);
+#define EF_CASE(n) case n: return rg_setup_n<n>(v, smem, cluster, tpb, max_clusters);
         EF_RG_SIZES(EF_CASE)
 #undef EF_CASE
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t rg_launch_f32(int N, int rpt, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s)
+cudaError_t rg_launch_f32(int N, int v, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s)
 {
     switch (N) {
-#define EF_CASE(n) case n: return rg_launch_n<n>(rpt, a, grid_clusters, tpb, smem, s);
+#define EF_CASE(n) case n: return rg_launch_n<n>(v, a, grid_clusters, tpb, smem, s);
         EF_RG_SIZES(EF_CASE)
 #undef EF_CASE
     default: return cudaErrorInvalidValue;

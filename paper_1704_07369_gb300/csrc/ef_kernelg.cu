@@ -45,6 +45,7 @@ __global__ void kernel_g_kernel(const T *mult, int ne, int d, int N, int64_t zid
     extern __shared__ double shg[];
     double *cs = shg;                 // [N] cos(2 pi m / N)
     double *ge = shg + N;             // [ne] g_e(z)
+    double *mz = shg + N + ne;        // [ne] m_e(z)
     const int M1 = N, Md = d == 3 ? N * N * N : N * N;
     for (int m = threadIdx.x; m < N; m += blockDim.x) cs[m] = cospi(2.0 * m / N);
     // grid index of z: components j (0 .. N-1 stand for j - N/2)
@@ -57,15 +58,23 @@ __global__ void kernel_g_kernel(const T *mult, int ne, int d, int N, int64_t zid
     // g_e(z) for every direction e: one warp per e, FP64 sum over the modes
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int e = warp; e < ne; e += nw) {
-        double acc = 0.0;
+        double acc = 0.0, accm = 0.0;
         for (int i = lane; i < Md; i += 32) {
             const int k2 = i % M1, k1 = (i / M1) % M1, k0 = d == 3 ? i / (M1 * M1) : 0;
             const int m0 = k0 < N / 2 ? k0 : k0 - N, m1 = k1 < N / 2 ? k1 : k1 - N, m2 = k2 < N / 2 ? k2 : k2 - N;
             const int ph = d == 3 ? m0 * zj[0] + m1 * zj[1] + m2 * zj[2] : m1 * zj[0] + m2 * zj[1];
-            acc += table_at<T>(mult, ne + e, d, N, k0, k1, k2) * cs[((ph % N) + N) % N];
+            const double c = cs[((ph % N) + N) % N];
+            acc += table_at<T>(mult, ne + e, d, N, k0, k1, k2) * c;
+            accm += table_at<T>(mult, e, d, N, k0, k1, k2) * c;
         }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) ge[e] = acc;
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            accm += __shfl_xor_sync(0xffffffffu, accm, o);
+        }
+        if (lane == 0) {
+            ge[e] = acc;
+            mz[e] = accm;
+        }
     }
     __syncthreads();
     for (int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; y < Md; y += (int64_t)gridDim.x * blockDim.x) {
@@ -74,14 +83,16 @@ __global__ void kernel_g_kernel(const T *mult, int ne, int d, int N, int64_t zid
         for (int a = d - 1; a >= 0; --a) { yj[a] = (int)(s % N) - N / 2; s /= N; }
         double g = 0.0;
         for (int e = 0; e < ne; ++e) {
-            double me = 0.0;
+            double me = 0.0, gy = 0.0;
             for (int i = 0; i < Md; ++i) {
                 const int k2 = i % M1, k1 = (i / M1) % M1, k0 = d == 3 ? i / (M1 * M1) : 0;
                 const int m0 = k0 < N / 2 ? k0 : k0 - N, m1 = k1 < N / 2 ? k1 : k1 - N, m2 = k2 < N / 2 ? k2 : k2 - N;
                 const int ph = d == 3 ? m0 * yj[0] + m1 * yj[1] + m2 * yj[2] : m1 * yj[0] + m2 * yj[1];
-                me += table_at<T>(mult, e, d, N, k0, k1, k2) * cs[((ph % N) + N) % N];
+                const double c = cs[((ph % N) + N) % N];
+                me += table_at<T>(mult, e, d, N, k0, k1, k2) * c;
+                gy += table_at<T>(mult, ne + e, d, N, k0, k1, k2) * c;
             }
-            g += me * ge[e];
+            g += 0.5 * (me * ge[e] + gy * mz[e]);
         }
         G[y] = g;
     }
@@ -109,7 +120,7 @@ extern "C" ef_status ef_kernel_G(ef_plan_t plan, int64_t z_index, double *G_dev,
     const int ne = (v.ndir - 1) / 2;
     const int threads = 256;
     const int blocks = (int)((Md + threads - 1) / threads);
-    const size_t smem = (size_t)(v.N + ne) * sizeof(double);
+    const size_t smem = (size_t)(v.N + 2 * ne) * sizeof(double);
     cudaStream_t s = (cudaStream_t)stream;
     if (v.prec == EF_PREC_F32)
         kernel_g_kernel<float><<<blocks, threads, smem, s>>>(static_cast<const float *>(v.mult), ne, v.d, v.N, z_index, G_dev);

@@ -356,8 +356,9 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
         for (int C : cands) {
             if (N % C || ef::collide_npc_v(d, N, C, 3) == 0) continue;
             const int planes = N / C, rows = planes * N;
-            for (int rpt = 2; rpt >= 1; --rpt) {
-                const int occ = 2 + rpt;
+            for (int v = 1; v <= 3; ++v) {
+                const int occ = 2 + v;
+                const int rpt = ef::rg_rows_per_thread(v);
                 const int tmax = maxthreads_for(ds.prec, d, N, occ);
                 if (tmax == 0 || rows % rpt) continue;
                 const int tpb = rows / rpt;
@@ -581,6 +582,17 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
                 best_sh = sh;
                 best_pf = pfv;
             }
+            if (e == cudaSuccess) {
+                // EF_AUTOTUNE_LOG names a file that receives every timed candidate (tuning records)
+                if (const char *lp = std::getenv("EF_AUTOTUNE_LOG")) {
+                    if (FILE *lf = std::fopen(lp, "a")) {
+                        std::fprintf(lf, "N=%d cells=%lld cluster=%d threads=%d variant=%d sg=%d paired=%d prefetch=%d ms=%.4f\n",
+                                     cp.N, (long long)ncells_tune, sh.cluster, sh.tpb, sh.occ, sh.sg_global, sh.paired, pfv, tmin);
+                        std::fclose(lf);
+                    }
+                }
+            }
+            if (sh.occ >= 3) break;              // the register-accumulator kernel has no prefetch option
         }
     }
     cudaFree(F);

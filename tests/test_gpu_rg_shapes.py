@@ -5,7 +5,8 @@ against the FP64 oracle (whole cells at N = 16, sampled points above) on a ragge
 with the dynamic cell queue and the Euler diagnostics (mass against the oracle's).
 
 The shapes are those the kernel's layout admits: C | N, an even split of the N^2 / 2 pencils,
-threads = N^2 / (C RPT) within the instantiation's bound, shared memory within the 227 KB limit."""
+threads = N^2 / (C RPT) within the instantiation's launch bound, shared memory within the 227 KB
+limit."""
 import os
 
 import numpy as np
@@ -19,7 +20,13 @@ import paper_1704_07369_gb300 as ef  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-MAXT = {16: 288, 24: 288, 32: 256, 40: 320, 48: 288, 64: 256}
+def rg_bound(N, v):
+    """Launch bound of instantiation v (1: one row per thread, 2: two rows, 3: one row, <= 200 threads)."""
+    if v == 1:
+        return 320 if N == 40 else 256 if N in (32, 64) else 288
+    if v == 2:
+        return {16: 128, 24: 288, 32: 256, 40: 200, 48: 192, 64: 128}[N]
+    return 200 if N in (40, 48) else 0
 
 
 def _npp(N):
@@ -34,13 +41,14 @@ def rg_shapes(N):
             continue
         P = N // C
         npc = N * N // (2 * C)
-        smem = 2 * P * _npp(N) * 8 + N * npc * 8 + 33 * 10 * 8 + 16
+        smem = 2 * P * _npp(N) * 8 + N * npc * 8 + 33 * 10 * 8 + 16 + 128
         if smem > 232448:
             continue
-        for rpt in (1, 2):
+        for v in (1, 2, 3):
+            rpt = 2 if v == 2 else 1
             t = N * P // rpt
-            if 32 <= t <= MAXT[N] and (N * P) % rpt == 0:
-                out.append((C, t, 2 + rpt))
+            if (N * P) % rpt == 0 and 32 <= t <= rg_bound(N, v):
+                out.append((C, t, 2 + v))
     return out
 
 
