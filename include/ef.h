@@ -304,9 +304,11 @@ ef_status ef_transport_step(ef_plan_t plan, const void *F_in_dev, void *F_out_de
  *   Qh_k = sum_{l + m = k mod N} (Bs(l, m) - Bs(m, m)) Fh_l Fh_m
  * is summed directly over mode pairs: the weight depends on the unaliased l + m, so the low-rank
  * transforms of ef_collide do not apply.  O(N^6) work per cell.
- * ef_classical_create: even N with 4 <= N <= 32, box half width L > 0, truncation radius R_tr
- * (<= 0: the largest the classical form allows, 4L / (3 + sqrt 2)); tabulates B_hat on the host
- * and allocates its device tables and work arrays (about 8 (3N^2 + 1)^2 bytes; 75 MB at N = 32).
+ * ef_classical_create: even N with 4 <= N <= 128, box half width L > 0, truncation radius R_tr
+ * (<= 0: the largest the classical form allows, 4L / (3 + sqrt 2)); allocates its device table and
+ * work arrays (about 8 (3N^2 + 1)^2 bytes: 75 MB at N = 32, 1.2 GB at N = 64, 19 GB at N = 128),
+ * tabulates B_hat on the device and synchronises (a set-up call).  N = 64 takes about a second of
+ * FP64 work per evaluation, N = 128 about a minute (N^6 pairs). 
  * ef_classical_collide: F_dev, Q_dev device arrays of ncells cells of N^3 doubles (layout as
  * ef_collide), not overlapping; cells are evaluated one after another on `stream`; calls on one
  * object share its work arrays, so they must not run concurrently.  Errors: EF_ERR_INVALID_ARG

@@ -7,7 +7,9 @@
 //   B_hat(l, m) = 4 pi int_0^R r^2 sinc(c r |l+m|) sinc(c r |l-m|) dr,
 // and the radial integral has a closed form (below).  B_hat depends on (l, m) only through the
 // integers |l+m|^2 and |l-m|^2 (at most 3 N^2), so it is tabulated over those when the object is
-// created.  The weight needs the true l + m, not its alias mod N, which is why this path sums mode
+// created (on the device: (3 N^2 + 1)^2 FP64 values, 75 MB at N = 32, 1.2 GB at N = 64, 19 GB at
+// N = 128; for one output mode the pairs touch at most 2^3 rows, |l + m| taking at most two
+// values per axis, so the lookups stay in L2).  The weight needs the true l + m, not its alias mod N, which is why this path sums mode
 // pairs directly (O(N^6) a cell, for the grid sizes of Table 3) instead of the low-rank transforms
 // of the Carleman path.
 //
@@ -41,25 +43,40 @@ namespace {
 constexpr double kPiC = 3.14159265358979323846264338327950288;
 
 // sin(x R) / x, its limit R at x = 0
-double sin_over(double x, double R)
+__host__ __device__ double sin_over(double x, double R)
 {
     const double y = x * R;
-    return std::fabs(y) < 1e-6 ? R * (1.0 - y * y / 6.0) : std::sin(y) / x;
+    return fabs(y) < 1e-6 ? R * (1.0 - y * y / 6.0) : sin(y) / x;
 }
 
 // I(a, b) = int_0^R r^2 sinc(a r) sinc(b r) dr for a, b >= 0, sinc(x) = sin(x) / x:
 //   a, b > 0:  (1 / (2ab)) [S(a - b) - S(a + b)],  S(x) = sin(xR) / x  (cos(a-b)r - cos(a+b)r = 2 sin ar sin br)
 //   a = 0:     (sin(bR) - bR cos(bR)) / b^3  (series near bR = 0),   a = b = 0:  R^3 / 3
-double radial_integral(double a, double b, double R)
+__host__ __device__ double radial_integral(double a, double b, double R)
 {
-    if (a < b) std::swap(a, b);
+    if (a < b) {
+        const double t = a;
+        a = b;
+        b = t;
+    }
     if (a == 0.0) return R * R * R / 3.0;
     if (b == 0.0) {
         const double y = a * R;
         if (y < 1e-2) return R * R * R * (1.0 / 3.0 - y * y / 30.0 + y * y * y * y / 840.0);
-        return (std::sin(y) - y * std::cos(y)) / (a * a * a);
+        return (sin(y) - y * cos(y)) / (a * a * a);
     }
     return (sin_over(a - b, R) - sin_over(a + b, R)) / (2.0 * a * b);
+}
+
+// tab[i][j] = 4 pi I(c sqrt(i), c sqrt(j)) over the integers i, j <= 3 N^2 (built on the device:
+// (3 N^2 + 1)^2 entries, 1.2 GB at N = 64)
+__global__ void classical_table_kernel(double *tab, int64_t nn, double cc, double R)
+{
+    const double fourpi = 4.0 * 3.14159265358979323846264338327950288;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nn * nn; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nn, j = t % nn;
+        tab[t] = fourpi * radial_integral(cc * sqrt((double)i), cc * sqrt((double)j), R);
+    }
 }
 
 int mode_at(int N, int i) { return i < N / 2 ? i : i - N; }
@@ -169,7 +186,7 @@ ef_status ef_classical_create(int N, double L, double R_tr, int sigma_enabled, e
 {
     if (!out) return cfail(EF_ERR_INVALID_ARG, "null output handle");
     *out = nullptr;
-    if (N < 4 || N % 2 || N > 32) return cfail(EF_ERR_INVALID_ARG, "classical form: N must be even, 4 <= N <= 32");
+    if (N < 4 || N % 2 || N > 128) return cfail(EF_ERR_INVALID_ARG, "classical form: N must be even, 4 <= N <= 128");
     if (!(L > 0.0) || !std::isfinite(L)) return cfail(EF_ERR_INVALID_ARG, "L must be > 0");
     const double R = R_tr > 0.0 ? R_tr : 4.0 * L / (3.0 + std::sqrt(2.0));
     if (!std::isfinite(R)) return cfail(EF_ERR_INVALID_ARG, "R_tr must be finite");
@@ -184,10 +201,6 @@ ef_status ef_classical_create(int N, double L, double R_tr, int sigma_enabled, e
     c->nn = 3 * (int64_t)N * N + 1;
     const int64_t nn = c->nn;
     const double cc = kPiC / (2.0 * L);
-    std::vector<double> tab((size_t)(nn * nn));
-    for (int64_t i = 0; i < nn; ++i)
-        for (int64_t j = 0; j < nn; ++j)
-            tab[(size_t)(i * nn + j)] = 4.0 * kPiC * radial_integral(cc * std::sqrt((double)i), cc * std::sqrt((double)j), R);
     std::vector<double> s1(N);
     for (int i = 0; i < N; ++i) s1[i] = ef::jackson_filter(N, mode_at(N, i), sigma_enabled != 0);
     std::vector<double> sig((size_t)M), bmm((size_t)M);
@@ -196,14 +209,19 @@ ef_status ef_classical_create(int N, double L, double R_tr, int sigma_enabled, e
         const int a0 = mode_at(N, i0), a1 = mode_at(N, i1), a2 = mode_at(N, i2);
         sig[(size_t)m] = s1[i0] * s1[i1] * s1[i2];
         const int64_t m2 = 4 * ((int64_t)a0 * a0 + (int64_t)a1 * a1 + (int64_t)a2 * a2);
-        bmm[(size_t)m] = sig[(size_t)m] * sig[(size_t)m] * tab[(size_t)(m2 * nn)];
+        // B_hat(m, m): |m + m|^2 = 4 |m|^2, |m - m|^2 = 0 (the table's row 4|m|^2, column 0)
+        bmm[(size_t)m] = sig[(size_t)m] * sig[(size_t)m] * 4.0 * kPiC * radial_integral(cc * std::sqrt((double)m2), 0.0, R);
     }
     e = cudaMalloc((void **)&c->d_tab, (size_t)(nn * nn) * sizeof(double));
+    if (e == cudaSuccess) {
+        classical_table_kernel<<<152 * 16, 256>>>(c->d_tab, nn, cc, R);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_sig, (size_t)M * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_bmm, (size_t)M * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_x, (size_t)M * sizeof(double2));
     if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_y, (size_t)M * sizeof(double2));
-    if (e == cudaSuccess) e = cudaMemcpy(c->d_tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_sig, sig.data(), sig.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_bmm, bmm.data(), bmm.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { cfree(c); return ccuda(e, "classical-form tables"); }

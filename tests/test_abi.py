@@ -50,7 +50,7 @@ def test_host_side_argument_checks():
     assert lib.ef_transport_step(None, None, None, 4, 0.1, 0.01, None) == ef.EF_ERR_INVALID_ARG
     c = ctypes.c_void_p()
     assert lib.ef_classical_create(7, 8.0, 0.0, 1, ctypes.byref(c)) == ef.EF_ERR_INVALID_ARG      # odd N
-    assert lib.ef_classical_create(64, 8.0, 0.0, 1, ctypes.byref(c)) == ef.EF_ERR_INVALID_ARG     # N > 32
+    assert lib.ef_classical_create(130, 8.0, 0.0, 1, ctypes.byref(c)) == ef.EF_ERR_INVALID_ARG    # N > 128
     assert lib.ef_classical_create(16, -1.0, 0.0, 1, ctypes.byref(c)) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_classical_create(16, 8.0, 0.0, 1, None) == ef.EF_ERR_INVALID_ARG
     assert lib.ef_classical_collide(None, None, None, 1, None) == ef.EF_ERR_INVALID_ARG
