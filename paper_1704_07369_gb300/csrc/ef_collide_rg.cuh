@@ -27,9 +27,22 @@
 
 namespace ef {
 
-// row stride (complex) of the slabs: N/2 + 2, an odd number of 16-byte pairs
+// Slab layout of one axis-0 plane: N rows (k_y) of N/2 stored k_x values (complex).  Where a row
+// holds a multiple of 4 16-byte pairs (N = 16, 32, 48, 64) the pairs of row y are stored in the
+// order pair ^ ((y >> 1) & 3) (an XOR swizzle inside aligned groups of four pairs); otherwise each
+// row is padded to N/2 + 2 values (an odd number of pairs).  Either way 16-byte accesses to pair j
+// of eight consecutive rows, and 8-byte accesses to a k_x range of one row, fall on distinct banks.
 template <int N>
-__host__ __device__ constexpr int rg_row_stride() { return N / 2 + 2; }
+__host__ __device__ constexpr bool rg_swizzled() { return (N / 4) % 4 == 0; }
+template <int N>
+__host__ __device__ constexpr int rg_row_stride() { return rg_swizzled<N>() ? N / 2 : N / 2 + 2; }
+// offset (complex values) of (k_y = y, k_x) inside a plane; the pair (k_x even, k_x + 1) stays adjacent
+template <int N>
+__device__ __forceinline__ int rg_at(int y, int kx)
+{
+    if constexpr (rg_swizzled<N>()) return y * (N / 2) + ((((kx >> 1) ^ ((y >> 1) & 3)) << 1) | (kx & 1));
+    else return y * rg_row_stride<N>() + kx;
+}
 // plane stride: N rows, padded to 8 mod 16 complex values
 template <int N>
 __host__ __device__ constexpr int rg_plane_stride()
@@ -37,16 +50,19 @@ __host__ __device__ constexpr int rg_plane_stride()
     constexpr int s = N * rg_row_stride<N>();
     return s + ((8 - s % 16) + 16) % 16;
 }
-// Instantiations ("variants", one CTA per SM each): 1 = one row per thread with the size's widest
-// launch bound, 2 = two rows per thread, 3 = one row per thread with at most 200 threads (N = 40,
-// 48: 7 warps keep 255 registers, where the widest bound leaves 168).  rg_bound is the launch bound
-// (0: not built).
+// Instantiations ("variants", one CTA per SM each): 1 = the gain accumulator G in registers, one
+// row per thread, the size's widest launch bound; 2 = G in registers, two rows per thread; 3 = G in
+// registers, one row per thread, at most 200 threads (N = 40, 48: 7 warps keep 255 registers where
+// the widest bound leaves 168); 4 = G in shared memory (any thread count up to the bound: for the
+// sizes where a row in registers besides a length-N transform would spill).  rg_bound is the
+// launch bound (0: not built).
 template <int N, int V>
 __host__ __device__ constexpr int rg_bound()
 {
     if (V == 1) return N == 40 ? 320 : (N == 32 || N == 64) ? 256 : 288;
     if (V == 2) return N == 16 ? 128 : N == 24 ? 288 : N == 32 ? 256 : N == 40 ? 200 : N == 48 ? 192 : 128;
     if (V == 3) return (N == 40 || N == 48) ? 200 : 0;
+    if (V == 4) return N == 40 ? 320 : (N == 48 || N == 24) ? 288 : 256;
     return 0;
 }
 template <int V>
@@ -62,15 +78,15 @@ __host__ __device__ inline int rg_npc(int N, int C)
 }
 
 template <int N>
-__host__ __device__ constexpr size_t rg_smem_bytes(int planes, int npc)
+__host__ __device__ constexpr size_t rg_smem_bytes(int planes, int npc, bool g_shared)
 {
-    return (size_t)2 * planes * rg_plane_stride<N>() * 8 + (size_t)N * npc * 8 + (32 + 1) * kDiag * sizeof(double) + 16 +
-           32 * sizeof(float);
+    return (size_t)2 * planes * rg_plane_stride<N>() * 8 + (size_t)N * npc * 8 + (g_shared ? (size_t)planes * N * N * 4 : 0) +
+           (32 + 1) * kDiag * sizeof(double) + 16 + 32 * sizeof(float);
 }
 
 // in-plane offset of the even pencil of a lane pair: pencil q (even) -> (k_y, k_x) = (q / (N/2), q % (N/2))
 template <int N>
-__device__ __forceinline__ int rg_poff(int q) { return (q / (N / 2)) * rg_row_stride<N>() + (q % (N / 2)); }
+__device__ __forceinline__ int rg_poff(int q) { return rg_at<N>(q / (N / 2), q % (N / 2)); }
 
 // stage-A scatter of one pencil (lane pairs hold pencils q, q + 1 of one slab row; one shuffle per
 // z pair so that each lane issues 16-byte stores; owner CTA of z by multiply-high)
@@ -114,15 +130,17 @@ __device__ __forceinline__ void rg_gather(C2<float> (&v)[N], uint32_t slab_base,
 }
 
 // two Hermitian half rows (k < N/2; the k = N/2 entry is zero for every op) -> z = IFFT(R0) + i
-// IFFT(R1), read as 16-byte pairs
+// IFFT(R1), read as 16-byte pairs; R0, R1 point at the start of rows y0, y1 of their planes
 template <int N>
-__device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, const C2<float> *R1, C2<float> (&z)[N])
+__device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, int y0, const C2<float> *R1, int y1, C2<float> (&z)[N])
 {
     const float4 *A = reinterpret_cast<const float4 *>(R0);
     const float4 *B = reinterpret_cast<const float4 *>(R1);
+    const int sw0 = rg_swizzled<N>() ? (y0 >> 1) & 3 : 0;
+    const int sw1 = rg_swizzled<N>() ? (y1 >> 1) & 3 : 0;
 #pragma unroll
     for (int k2 = 0; k2 < N / 2; k2 += 2) {
-        const float4 a = A[k2 / 2], b = B[k2 / 2];
+        const float4 a = A[(k2 / 2) ^ sw0], b = B[(k2 / 2) ^ sw1];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int k = k2 + h;
@@ -140,12 +158,13 @@ __device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, const C2<float>
     fft<N, 1, N>(z);
 }
 
-template <int D, int N, int RPT, int LB>
+// GS = false: G of this thread's RPT rows in registers (nt * RPT = rows); GS = true: G in shared
+// memory, column-major ([x][row], so consecutive threads touch consecutive banks), rows looped.
+template <int D, int N, int RPT, int LB, bool GS>
 __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
 {
     static_assert(D == 3, "3D only");
     using T = float;
-    constexpr int RS = rg_row_stride<N>();
     constexpr int NPP = rg_plane_stride<N>();
     constexpr int NH = N / 2;              // stored k_x values per row
     constexpr int64_t CELL = (int64_t)N * N * N;
@@ -154,13 +173,13 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
     const int C = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
     const int P = a.planes;
-    const int tid = threadIdx.x, nt = blockDim.x;          // nt * RPT = rows
+    const int tid = threadIdx.x, nt = blockDim.x;
     Sync bar{cl, C};
     const int rows = P * N;
     const int NPC = a.npc;                 // pencils per CTA = N^2 / (2 C), even
     // the launch shape this layout needs (the same for every CTA, so all return together):
-    // RPT rows per thread exactly, an even pencil split over the cluster
-    if (nt * RPT != rows || P * C != N || 2 * NPC * C != N * N || NPC % 2) {
+    // RPT rows per thread exactly (G in registers), an even pencil split over the cluster
+    if ((!GS && nt * RPT != rows) || P * C != N || 2 * NPC * C != N * N || NPC % 2) {
         if (tid == 0) record_status(a.status, 2);       // EF_ERR_UNSUPPORTED
         return;
     }
@@ -169,7 +188,8 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
     C2<T> *Is0 = reinterpret_cast<C2<T> *>(smem_raw);
     C2<T> *Is1 = Is0 + (size_t)P * NPP;
     C2<T> *Fs = Is1 + (size_t)P * NPP;                       // [z][local pencil] forward spectrum
-    double *part = reinterpret_cast<double *>(Fs + (size_t)N * NPC);     // [32 warps + 1][kDiag]
+    T *Gs = reinterpret_cast<T *>(Fs + (size_t)N * NPC);      // GS: [x][row]
+    double *part = reinterpret_cast<double *>(Gs + (GS ? (size_t)rows * N : 0));   // [32 warps + 1][kDiag]
     long long *s_cell = reinterpret_cast<long long *>(part + (32 + 1) * kDiag);
     int *s_nubig = reinterpret_cast<int *>(s_cell + 1);
     float *s_maxnu = reinterpret_cast<float *>(s_cell + 2);          // [32 warps] max nu of the loss op
@@ -209,24 +229,24 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
             load_row<T, N>(F + ((int64_t)rank * rows + r1) * N, x1);
             C2<T> X0[H], X1[H];
             r2c_pair<N, T>(x0, x1, X0, X1);
-            float4 *d0 = reinterpret_cast<float4 *>(Is0 + (r0 / N) * NPP + (r0 % N) * RS);
-            float4 *d1 = reinterpret_cast<float4 *>(Is0 + (r1 / N) * NPP + (r1 % N) * RS);
+            C2<T> *d0 = Is0 + (r0 / N) * NPP, *d1 = Is0 + (r1 / N) * NPP;
+            const int y0 = r0 % N, y1 = r1 % N;
 #pragma unroll
             for (int k = 0; k < NH; k += 2) {
-                d0[k / 2] = make_float4(X0[k].x, X0[k].y, X0[k + 1].x, X0[k + 1].y);
-                d1[k / 2] = make_float4(X1[k].x, X1[k].y, X1[k + 1].x, X1[k + 1].y);
+                *reinterpret_cast<float4 *>(d0 + rg_at<N>(y0, k)) = make_float4(X0[k].x, X0[k].y, X0[k + 1].x, X0[k + 1].y);
+                *reinterpret_cast<float4 *>(d1 + rg_at<N>(y1, k)) = make_float4(X1[k].x, X1[k].y, X1[k + 1].x, X1[k + 1].y);
             }
         }
         __syncthreads();
         for (int q = tid; q < P * NH; q += nt) {            // axis 1 forward, k_x < N/2
             const int zl = q / NH, lx = q % NH;
-            C2<T> *col = Is0 + (size_t)zl * NPP + lx;
+            C2<T> *pl = Is0 + (size_t)zl * NPP;
             C2<T> v[N];
 #pragma unroll
-            for (int y = 0; y < N; ++y) v[y] = col[y * RS];
+            for (int y = 0; y < N; ++y) v[y] = pl[rg_at<N>(y, lx)];
             fft<N, -1, N>(v);
 #pragma unroll
-            for (int y = 0; y < N; ++y) col[y * RS] = v[y];
+            for (int y = 0; y < N; ++y) pl[rg_at<N>(y, lx)] = v[y];
         }
         bar.full();
 
@@ -249,7 +269,7 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
         // the diagnostics accumulate only in the last op (reset there), so they hold no registers
         // through the earlier ops; the loss op's max nu goes to shared memory per warp
         Diag dg;
-        T g[RPT][N];                       // gain accumulator of this thread's rows tid + j nt
+        T g[GS ? 1 : RPT][N];              // G in registers: this thread's rows tid + j nt
 
         for (int o = 0; o < a.nops; ++o) {
             const Op op = a.ops[o];
@@ -282,77 +302,108 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
                 const int b = q >= P * NH;
                 const int rem = q - b * P * NH;
                 const int zl = rem / NH, lx = rem % NH;
-                C2<T> *col = (b ? Is1 : Is0) + (size_t)zl * NPP + lx;
+                C2<T> *pl = (b ? Is1 : Is0) + (size_t)zl * NPP;
                 C2<T> v[N];
 #pragma unroll
-                for (int y = 0; y < N; ++y) v[y] = col[y * RS];
+                for (int y = 0; y < N; ++y) v[y] = pl[rg_at<N>(y, lx)];
                 fft<N, 1, N>(v);
 #pragma unroll
-                for (int y = 0; y < N; ++y) col[y * RS] = v[y];
+                for (int y = 0; y < N; ++y) pl[rg_at<N>(y, lx)] = v[y];
             }
             __syncthreads();
 
-            // ---------------- rows: half complex -> real, accumulate in registers / output
+            // ---------------- rows: half complex -> real, accumulate / output
             if (pair) {
                 const bool last = op.kind == OP_PAIR_LAST;
                 const bool big = *s_nubig != 0;
                 if (last) dg.reset();
+                if constexpr (GS) {
+                    for (int r = tid; r < rows; r += nt) {
+                        const int rb = (r / N) * NPP + (r % N) * rg_row_stride<N>();
+                        C2<T> z[N];
+                        rg_c2r_rows<N>(Is0 + rb, r % N, Is1 + rb, r % N, z);
+                        T *Gr = Gs + r;
+                        if (!last) {
 #pragma unroll
-                for (int j = 0; j < RPT; ++j) {
-                    const int r = tid + j * nt;
-                    const int ro = (r / N) * NPP + (r % N) * RS;
-                    C2<T> z[N];
-                    rg_c2r_rows<N>(Is0 + ro, Is1 + ro, z);
-                    if (!last) {
+                            for (int n = 0; n < N; ++n) Gr[n * rows] += z[n].x * z[n].y;
+                        } else {
+                            T qv[N];
 #pragma unroll
-                        for (int n = 0; n < N; ++n) g[j][n] += z[n].x * z[n].y;
-                    } else {
-                        T qv[N];
-#pragma unroll
-                        for (int n = 0; n < N; ++n) qv[n] = g[j][n] + z[n].x * z[n].y;
-                        const int64_t grow = (int64_t)rank * rows + r;
-                        T fr[N];
-                        load_row<T, N>(F + grow * N, fr);
-                        emit_row<T, D, N>(a, fr, Out + grow * N, qv, nullptr, big, grow, dg);
-                    }
-                }
-            } else {
-                // the loss (first op): nu of this thread's rows, G = -F nu.  With two rows per
-                // thread they share one complex transform; with one, the second input is zero.
-                bool bigt = false;
-                T mxt = T(-3.0e38);
-                if constexpr (RPT == 2) {
-                    const int r0 = tid, r1 = tid + nt;
-                    C2<T> z[N];
-                    rg_c2r_rows<N>(Is0 + (r0 / N) * NPP + (r0 % N) * RS, Is0 + (r1 / N) * NPP + (r1 % N) * RS, z);
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int r = j ? r1 : r0;
-                        T fr[N];
-                        load_row<T, N>(F + ((int64_t)rank * rows + r) * N, fr);
-                        T mx = j ? z[0].y : z[0].x;
-#pragma unroll
-                        for (int n = 0; n < N; ++n) {
-                            const T nu = j ? z[n].y : z[n].x;
-                            g[j][n] = -fr[n] * nu;
-                            mx = nu > mx ? nu : mx;
-                            if (T(a.dt) * nu > T(1)) bigt = true;
+                            for (int n = 0; n < N; ++n) qv[n] = Gr[n * rows] + z[n].x * z[n].y;
+                            const int64_t grow = (int64_t)rank * rows + r;
+                            T fr[N];
+                            load_row<T, N>(F + grow * N, fr);
+                            emit_row<T, D, N>(a, fr, Out + grow * N, qv, nullptr, big, grow, dg);
                         }
-                        mxt = mx > mxt ? mx : mxt;
                     }
                 } else {
 #pragma unroll
                     for (int j = 0; j < RPT; ++j) {
                         const int r = tid + j * nt;
-                        const C2<T> *R0 = Is0 + (r / N) * NPP + (r % N) * RS;
+                        const int rb = (r / N) * NPP + (r % N) * rg_row_stride<N>();
+                        C2<T> z[N];
+                        rg_c2r_rows<N>(Is0 + rb, r % N, Is1 + rb, r % N, z);
+                        if (!last) {
+#pragma unroll
+                            for (int n = 0; n < N; ++n) g[j][n] += z[n].x * z[n].y;
+                        } else {
+                            T qv[N];
+#pragma unroll
+                            for (int n = 0; n < N; ++n) qv[n] = g[j][n] + z[n].x * z[n].y;
+                            const int64_t grow = (int64_t)rank * rows + r;
+                            T fr[N];
+                            load_row<T, N>(F + grow * N, fr);
+                            emit_row<T, D, N>(a, fr, Out + grow * N, qv, nullptr, big, grow, dg);
+                        }
+                    }
+                }
+            } else {
+                // the loss (first op): nu of the rows, G = -F nu; two rows share one complex
+                // transform (with G in registers and one row per thread, the second input is zero)
+                bool bigt = false;
+                T mxt = T(-3.0e38);
+                if constexpr (GS || RPT == 2) {
+                    // rows r0 and r1 = r0 + rows / 2 (G in shared memory: looped; two rows per
+                    // thread in registers: tid and tid + nt = tid + rows / 2)
+                    for (int q = tid; q < rows / 2; q += nt) {
+                        const int r0 = q, r1 = q + rows / 2;
+                        const int rb0 = (r0 / N) * NPP + (r0 % N) * rg_row_stride<N>();
+                        const int rb1 = (r1 / N) * NPP + (r1 % N) * rg_row_stride<N>();
+                        C2<T> z[N];
+                        rg_c2r_rows<N>(Is0 + rb0, r0 % N, Is0 + rb1, r1 % N, z);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int r = j ? r1 : r0;
+                            T fr[N];
+                            load_row<T, N>(F + ((int64_t)rank * rows + r) * N, fr);
+                            T mx = j ? z[0].y : z[0].x;
+#pragma unroll
+                            for (int n = 0; n < N; ++n) {
+                                const T nu = j ? z[n].y : z[n].x;
+                                const T gv = -fr[n] * nu;
+                                if constexpr (GS) Gs[n * rows + r] = gv;
+                                else g[j][n] = gv;
+                                mx = nu > mx ? nu : mx;
+                                if (T(a.dt) * nu > T(1)) bigt = true;
+                            }
+                            mxt = mx > mxt ? mx : mxt;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) {
+                        const int r = tid + j * nt;
+                        const C2<T> *R0 = Is0 + (r / N) * NPP;
+                        const int y = r % N;
                         // real row from one half spectrum: z = IFFT(R0) (the second input zero)
                         C2<T> z[N];
 #pragma unroll
                         for (int k = 1; k < NH; ++k) {
-                            z[k] = R0[k];
-                            z[N - k] = cconj(R0[k]);
+                            const C2<T> w = R0[rg_at<N>(y, k)];
+                            z[k] = w;
+                            z[N - k] = cconj(w);
                         }
-                        z[0] = C2<T>{R0[0].x, 0.f};
+                        z[0] = C2<T>{R0[rg_at<N>(y, 0)].x, 0.f};
                         z[NH] = C2<T>{0.f, 0.f};
                         fft<N, 1, N>(z);
                         T fr[N];

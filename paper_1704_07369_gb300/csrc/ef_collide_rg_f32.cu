@@ -10,7 +10,7 @@ namespace {
 template <int N, int V>
 constexpr auto rg_kernel()
 {
-    return collide_kernel_rg<3, N, rg_rpt<V>(), (rg_bound<N, V>() > 0 ? rg_bound<N, V>() : 32)>;
+    return collide_kernel_rg<3, N, rg_rpt<V>(), (rg_bound<N, V>() > 0 ? rg_bound<N, V>() : 32), V == 4>;
 }
 
 template <int N>
@@ -21,6 +21,7 @@ cudaError_t rg_setup_n(int v, size_t smem, int cluster, int tpb, int *max_cluste
     if constexpr (rg_bound<N, 3>() > 0) {
         if (v == 3) return setup_kernel(rg_kernel<N, 3>(), smem, cluster, tpb, max_clusters);
     }
+    if (v == 4) return setup_kernel(rg_kernel<N, 4>(), smem, cluster, tpb, max_clusters);
     return cudaErrorInvalidValue;
 }
 
@@ -32,6 +33,7 @@ cudaError_t rg_launch_n(int v, const CollideArgs &a, int grid_clusters, int tpb,
     if constexpr (rg_bound<N, 3>() > 0) {
         if (v == 3) return launch_kernel(rg_kernel<N, 3>(), a, grid_clusters, tpb, smem, s);
     }
+    if (v == 4) return launch_kernel(rg_kernel<N, 4>(), a, grid_clusters, tpb, smem, s);
     return cudaErrorInvalidValue;
 }
 
@@ -41,21 +43,21 @@ cudaError_t rg_launch_n(int v, const CollideArgs &a, int grid_clusters, int tpb,
 
 int rg_maxthreads_f32(int N, int v)
 {
-    if (v < 1 || v > 3) return 0;
+    if (v < 1 || v > 4) return 0;
     switch (N) {
-#define EF_CASE(n) case n: return v == 1 ? rg_bound<n, 1>() : v == 2 ? rg_bound<n, 2>() : rg_bound<n, 3>();
+#define EF_CASE(n) case n: return v == 1 ? rg_bound<n, 1>() : v == 2 ? rg_bound<n, 2>() : v == 3 ? rg_bound<n, 3>() : rg_bound<n, 4>();
         EF_RG_SIZES(EF_CASE)
 #undef EF_CASE
     default: return 0;
     }
 }
 
-int rg_rows_per_thread(int v) { return v == 2 ? 2 : 1; }
+int rg_rows_per_thread(int v) { return v == 2 ? 2 : v == 4 ? 0 : 1; }
 
-size_t rg_smem_f32(int N, int planes)
+size_t rg_smem_f32(int N, int planes, int v)
 {
     switch (N) {
-#define EF_CASE(n) case n: return rg_smem_bytes<n>(planes, rg_npc(n, n / planes));
+#define EF_CASE(n) case n: return rg_smem_bytes<n>(planes, rg_npc(n, n / planes), v == 4);
         EF_RG_SIZES(EF_CASE)
 #undef EF_CASE
     default: return 0;

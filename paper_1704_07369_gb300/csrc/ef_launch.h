@@ -19,12 +19,12 @@ namespace ef {
     cudaError_t collide_launch_##SUF(int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, \
                                      int occ, cudaStream_t s);
 
-// FP32 3D register-accumulator kernel (ef_collide_rg_f32.cu), instantiation v = 1, 2, 3 (kernel
+// FP32 3D register-accumulator kernel (ef_collide_rg_f32.cu), instantiation v = 1 .. 4 (kernel
 // variant occ = 2 + v): rg_maxthreads_f32 is its launch bound (0: not built for N),
-// rg_rows_per_thread its rows per thread.
+// rg_rows_per_thread its rows per thread (0: the gain accumulator in shared memory, rows looped).
 int rg_maxthreads_f32(int N, int v);
 int rg_rows_per_thread(int v);
-size_t rg_smem_f32(int N, int planes);
+size_t rg_smem_f32(int N, int planes, int v);
 cudaError_t rg_setup_f32(int N, int v, size_t smem, int cluster, int tpb, int *max_clusters);
 cudaError_t rg_launch_f32(int N, int v, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s);
 
@@ -69,9 +69,9 @@ inline size_t collide_fh_bytes(int prec, int d, int N)
 }
 size_t collide_smem(int prec, int d, int N, int planes, int sg_global, int paired, int occ);
 // Kernel variants ("occ"): 1 = one CTA per SM, 2 = two CTAs per SM (shared-memory accumulators);
-// 3 / 4 / 5 = FP32 3D register-accumulator kernel (one row per thread / two / one with at most 200
-// threads), which keeps the forward spectrum in shared memory and skips the Nyquist column
-// (pencils: N^2 / (2 C) per CTA).
+// 3 / 4 / 5 / 6 = FP32 3D kernel that keeps the forward spectrum in shared memory and skips the
+// Nyquist column (pencils: N^2 / (2 C) per CTA), with the gain accumulator in registers (one row
+// per thread / two / one with at most 200 threads) or (6) in shared memory.
 inline int collide_npc_v(int d, int N, int C, int occ)
 {
     if (occ >= 3) {

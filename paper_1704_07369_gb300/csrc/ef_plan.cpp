@@ -356,24 +356,28 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
         for (int C : cands) {
             if (N % C || ef::collide_npc_v(d, N, C, 3) == 0) continue;
             const int planes = N / C, rows = planes * N;
-            for (int v = 1; v <= 3; ++v) {
+            for (int v = 1; v <= 4; ++v) {
                 const int occ = 2 + v;
                 const int rpt = ef::rg_rows_per_thread(v);
                 const int tmax = maxthreads_for(ds.prec, d, N, occ);
-                if (tmax == 0 || rows % rpt) continue;
-                const int tpb = rows / rpt;
-                if (tpb > tmax || tpb < 32) continue;
-                const size_t smem = smem_for(ds.prec, d, N, planes, 0, 1, occ);
-                if ((long)smem > smem_max) continue;
-                int mc = 0;
-                cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, occ, &mc);
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    why = cudaGetErrorString(e);
-                    continue;
+                if (tmax == 0) continue;
+                // G in registers: exactly rows / rpt threads; in shared memory: one or two rows each
+                for (int per = (rpt ? rpt : 1); per <= (rpt ? rpt : 2); ++per) {
+                    if (rows % per) continue;
+                    const int tpb = rows / per;
+                    if (tpb > tmax || tpb < 32) continue;
+                    const size_t smem = smem_for(ds.prec, d, N, planes, 0, 1, occ);
+                    if ((long)smem > smem_max) continue;
+                    int mc = 0;
+                    cudaError_t e = setup_for(ds.prec, d, N, smem, C, tpb, occ, &mc);
+                    if (e != cudaSuccess) {
+                        cudaGetLastError();
+                        why = cudaGetErrorString(e);
+                        continue;
+                    }
+                    if (mc <= 0) continue;
+                    out.push_back(Shape{C, tpb, planes, 0, 1, occ, smem, mc});
                 }
-                if (mc <= 0) continue;
-                out.push_back(Shape{C, tpb, planes, 0, 1, occ, smem, mc});
             }
         }
     }

@@ -21,16 +21,20 @@ import paper_1704_07369_gb300 as ef  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 def rg_bound(N, v):
-    """Launch bound of instantiation v (1: one row per thread, 2: two rows, 3: one row, <= 200 threads)."""
+    """Launch bound of instantiation v (1: one row per thread, 2: two rows, 3: one row, <= 200
+    threads, 4: the gain accumulator in shared memory)."""
     if v == 1:
         return 320 if N == 40 else 256 if N in (32, 64) else 288
     if v == 2:
         return {16: 128, 24: 288, 32: 256, 40: 200, 48: 192, 64: 128}[N]
-    return 200 if N in (40, 48) else 0
+    if v == 3:
+        return 200 if N in (40, 48) else 0
+    return 320 if N == 40 else 288 if N in (24, 48) else 256
 
 
 def _npp(N):
-    s = N * (N // 2 + 2)
+    rs = N // 2 if (N // 4) % 4 == 0 else N // 2 + 2
+    s = N * rs
     return s + ((8 - s % 16) + 16) % 16
 
 
@@ -41,14 +45,14 @@ def rg_shapes(N):
             continue
         P = N // C
         npc = N * N // (2 * C)
-        smem = 2 * P * _npp(N) * 8 + N * npc * 8 + 33 * 10 * 8 + 16 + 128
-        if smem > 232448:
-            continue
-        for v in (1, 2, 3):
-            rpt = 2 if v == 2 else 1
-            t = N * P // rpt
-            if (N * P) % rpt == 0 and 32 <= t <= rg_bound(N, v):
-                out.append((C, t, 2 + v))
+        for v in (1, 2, 3, 4):
+            smem = 2 * P * _npp(N) * 8 + N * npc * 8 + (P * N * N * 4 if v == 4 else 0) + 33 * 10 * 8 + 16 + 128
+            if smem > 232448:
+                continue
+            for per in ((1, 2) if v == 4 else ((2,) if v == 2 else (1,))):
+                t = N * P // per
+                if (N * P) % per == 0 and 32 <= t <= rg_bound(N, v):
+                    out.append((C, t, 2 + v))
     return out
 
 
