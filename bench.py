@@ -609,11 +609,14 @@ def _quantiles(e):
 
 def surrogate_leg(args, device):
     """Surrogate vs plain on batches of 16384 BKW-family cells (3D, N = 32, L = 8), for the
-    hard-sphere and Maxwell kernels: the network (926 -> 512 x 3 -> 926, bf16 weights, FP32
-    accumulation) is trained on 204800 cells generated by the library, then plain-operator and
-    surrogate-with-fallback throughput are timed on the same resident batch, and the band of Q
-    the surrogate path delivers is compared cell by cell with the plain FP32 band (all cells) and
-    the FP64 band (first 1024 cells)."""
+    hard-sphere and Maxwell kernels: the network (928 -> 512 x 3 -> 926, bf16 weights, FP32
+    accumulation) and a checker network of the same shape are trained on 204800 cells generated by
+    the library; the checker threshold is calibrated on 16384 held-out cells; then plain-operator
+    and surrogate throughput are timed on a third batch.  The guarded policy ("checked_to_grid")
+    runs the checker gate and returns Q on the grid; its delivered band is compared cell by cell
+    with the plain FP32 band (all cells) and the FP64 band (first 1024 cells), its grid Q with the
+    plain Q, beside the band's truncation floor.  The other policies return the band only; the
+    unaudited one judges no cell and is an upper bound of the speed, not a guarded result."""
     import torch
 
     import paper_1704_07369_gb300 as ef
@@ -638,7 +641,15 @@ def surrogate_leg(args, device):
         hist = tr.fit(fF, fQ, fM, epochs=args.sur_epochs, lr0=SUR_LR, lr1=SUR_LR1, warmup=0.05)
         torch.cuda.synchronize()
         train_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        hist_c = tr.fit_checker(epochs=args.sur_epochs, lr0=SUR_LR, lr1=SUR_LR1, warmup=0.05)
+        torch.cuda.synchronize()
+        train_c_s = time.perf_counter() - t0
         del fF, fQ, fM
+        tr._train_set = None
+        # checker threshold from a held-out calibration batch (seeds disjoint from training and test)
+        inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 8_000_000, device=device, out=F)
+        thr, cal_flagged, cal_miss = tr.calibrate(F, SUR_CELLS, SUR_TOL, margin=0.8)
         inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 9_000_000, device=device, out=F)
         # references: plain FP32 band of every cell, FP64 band of the first 1024
         plan.collide(F, Q, ncells=SUR_CELLS)
@@ -667,10 +678,41 @@ def surrogate_leg(args, device):
         reps = max(3, min(args.steps, 10))
         plain_ms = timed(lambda i: plan.collide(F, Q, ncells=SUR_CELLS), reps)
         res = {"plain_ms": plain_ms, "plain_cells_per_s": SUR_CELLS / plain_ms * 1e3,
-               "train": {"data_s": data_s, "train_s": train_s, "final_loss": hist[-1]}, "policies": {}}
+               "train": {"data_s": data_s, "train_s": train_s, "final_loss": hist[-1],
+                         "checker_train_s": train_c_s, "checker_final_loss": hist_c[-1]},
+               "checker_calibration": {"threshold": thr, "flagged_fraction": cal_flagged, "misses_in_calibration_set": cal_miss,
+                                       "cells": SUR_CELLS, "margin": 0.8}, "policies": {}}
         q = torch.zeros(SUR_CELLS, ef.EF_FEATURE_STRIDE, device=device)
         flags = torch.zeros(SUR_CELLS, dtype=torch.int32, device=device)
-        for pname, audit, max_miss in (("no_audit", 0.0, 0.0), ("audit_strict", SUR_AUDIT, 0.0),
+        # the guarded path end to end: checker gate, Q on the grid (band reconstruction where the
+        # prediction is delivered, the plain operator's full Q where it is not), no audit
+        Qg = torch.empty_like(F)
+        ms = timed(lambda i: tr.sur.infer_ex(F, q, flags, SUR_CELLS, Q=Qg, audit_fraction=0.0, seed=i, tol=SUR_TOL), reps)
+        f = flags.cpu().numpy()
+        e = S.band_rel_l2(q, ref)
+        e64 = S.band_rel_l2(q[:n64], ref64)
+        # Q on the grid against the plain operator's full Q, and the band's own truncation floor
+        # (the plain Q against its projection on the band), per cell over the first 1024 cells
+        proj = torch.empty(n64, SUR_N, SUR_N, SUR_N, device=device)
+        ef.ef_features_inverse(plan.handle, ref[:n64], proj, n64)
+        Qd, Gd, Pd = Q[:n64].double(), Qg[:n64].double(), proj.double()
+        nrm = Qd.pow(2).sum(dim=(1, 2, 3)).sqrt()
+        full_err = (Gd - Qd).pow(2).sum(dim=(1, 2, 3)).sqrt() / nrm
+        floor = (Pd - Qd).pow(2).sum(dim=(1, 2, 3)).sqrt() / nrm
+        del proj, Qd, Gd, Pd
+        res["policies"]["checked_to_grid"] = {
+            "audit_fraction": 0.0, "checker_threshold": thr, "ms": ms, "cells_per_s": SUR_CELLS / ms * 1e3,
+            "speedup_vs_plain": plain_ms / ms, "output": "Q on the grid (N^3 per cell)",
+            "checker_flagged": int(((f & 32) != 0).sum()), "gated": int(((f & 1) != 0).sum()),
+            "plain_used": int(((f & 8) != 0).sum()),
+            "band_rel_l2_vs_fp32_plain": _quantiles(e), "band_rel_l2_vs_fp64_first1024": _quantiles(e64),
+            "full_Q_rel_l2_vs_plain_first1024": _quantiles(full_err),
+            "band_truncation_floor_first1024": {"p50": float(floor.median()),
+                                                "max": float(floor.max()), "mean": float(floor.mean())}}
+        del Qg
+        tr.sur.set_checker(None, 1.0)
+        # unguarded upper bound (nothing judges the cells) and the audit policies, band output only
+        for pname, audit, max_miss in (("no_audit_unjudged", 0.0, 0.0), ("audit_strict", SUR_AUDIT, 0.0),
                                        ("audit_tolerant", SUR_AUDIT, 0.05)):
             tr.sur.set_policy(max_miss_fraction=max_miss)
             ms = timed(lambda i: tr.sur.infer(F, q, flags, SUR_CELLS, audit, i, SUR_TOL), reps)

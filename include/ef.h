@@ -267,11 +267,38 @@ ef_status ef_surrogate_set_policy(ef_surrogate_t sur, float max_miss_fraction, f
  * +-xmax training standard deviations, or positive band entropy production sum Q ln F, which the
  * discrete H-theorem forbids), 2 = audited (a seeded fraction audit_fraction of cells, drawn from
  * seed), 4 = audited and the prediction missed the plain band by more than tol in relative L2,
- * 8 = plain result used, 16 = fell back because the audit failed: more than the policy's fraction
+ * 8 = plain result used, 32 = the checker network disagreed (ef_surrogate_set_checker), 16 = fell
+ * back because the audit failed: more than the policy's fraction
  * of the audited cells (by default none, ef_surrogate_set_policy) missed tol, and then the whole
  * batch uses the plain operator.  Everything stays on the device: no host synchronisation. */
 ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat, int *flags, int64_t ncells,
                              float audit_fraction, uint64_t seed, float tol, ef_stream_t stream);
+
+/* A second network (the checker: same input and output widths, max batch >= the surrogate's,
+ * trained like the first from another seed) whose disagreement with the surrogate's prediction
+ * gates every cell: with q and c the two decoded bands, the score ||q - c||_2 / ||q||_2 over the
+ * band (zero mode excluded) above tol (> 0) sends the cell to the plain operator (flags bit 32, with
+ * 8).  Two independently trained networks disagree most where each is least reliable, so a score
+ * threshold calibrated on held-out cells flags the cells whose prediction misses the tolerance.
+ * Allocates the checker's output rows for max_batch cells on the first call (a set-up call);
+ * checker = null switches the gate off.  The paper has no counterpart. */
+ef_status ef_surrogate_set_checker(ef_surrogate_t sur, ef_mlp_t checker, float tol);
+
+/* ef_surrogate_infer with two optional outputs: score (ncells floats, device; nullable) receives
+ * each cell's checker score (0 without a checker), and Q_dev (ncells cells of N^3 floats, layout as
+ * ef_collide, 16-byte aligned; nullable; FP32 3D plans) receives Q on the grid: the surrogate's band
+ * mapped back to the grid (ef_features_inverse) where the prediction is delivered, and the plain
+ * operator's full Q where flags has 8.  No allocation, no host synchronisation. */
+ef_status ef_surrogate_infer_ex(ef_surrogate_t sur, const void *F_dev, float *qfeat, int *flags, float *score,
+                                float *Q_dev, int64_t ncells, float audit_fraction, uint64_t seed, float tol,
+                                ef_stream_t stream);
+
+/* The inverse of ef_features on its band: Q_dev[c][i] = sum over the band modes k (both halves:
+ * each stored mode and its conjugate) of feat[c][k] exp(2 pi i k.i / N), i the array index; so a
+ * band-limited function is returned exactly and a general one is projected on the band (its
+ * truncation to |k| <= EF_FEATURE_K).  FP32 3D uniform plans with a band; Q_dev 16-byte aligned,
+ * ncells cells of N^3 floats.  No allocation. */
+ef_status ef_features_inverse(ef_plan_t plan, const float *feat, float *Q_dev, int64_t ncells, ef_stream_t stream);
 
 /* Moments and entropy of each cell (layout EF_DIAG_STRIDE, entries [0..7] and [9]).  Here [8] is
  * the positivity error of Sec. 4.2, Example 1: (sum |F| - sum F) / sum |F| (0 for F >= 0), in place

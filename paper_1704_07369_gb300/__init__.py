@@ -40,7 +40,8 @@ SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_
            "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_status", "ef_mlp_params",
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
-           "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer",
+           "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer", "ef_surrogate_set_checker",
+           "ef_surrogate_infer_ex", "ef_features_inverse",
            "ef_stream_plan_create", "ef_stream_plan_destroy", "ef_stream_plan_info", "ef_stream_euler_step",
            "ef_stream_plan_status", "ef_transport_step", "ef_classical_create", "ef_classical_collide",
            "ef_classical_destroy", "ef_status_string", "ef_last_error")
@@ -106,6 +107,9 @@ def lib():
         L.ef_surrogate_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_surrogate_set_policy.argtypes = [vp, ctypes.c_float, ctypes.c_float]
         L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
+        L.ef_surrogate_set_checker.argtypes = [vp, vp, ctypes.c_float]
+        L.ef_surrogate_infer_ex.argtypes = [vp, vp, vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
+        L.ef_features_inverse.argtypes = [vp, vp, vp, i64, vp]
         L.ef_euler_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
         L.ef_rk3_step.argtypes = [vp, vp, dbl, i32, vp, i64, vp]
         L.ef_stream_plan_create.argtypes = [i32, i64, vp, dbl, i32, i32, i32, i32, ctypes.POINTER(vp)]
@@ -188,6 +192,11 @@ def ef_collide(plan, F, Q, ncells, stream=None):
 def ef_collide_noalloc(plan, F, Q, ncells, stream=None):
     """ef_collide without any device allocation (scratch in the library's static device array)."""
     _check(lib().ef_collide_noalloc(plan, _ptr(F), _ptr(Q), int(ncells), _stream(stream)))
+
+
+def ef_features_inverse(plan, feat, Q, ncells, stream=None):
+    """Q on the grid from band modes (the inverse of ef_features on its band)."""
+    _check(lib().ef_features_inverse(plan, _ptr(feat), _ptr(Q), int(ncells), _stream(stream)))
 
 
 def ef_kernel_G(plan, z_index, G, stream=None):
@@ -291,6 +300,15 @@ class Surrogate:
     def infer(self, F, qfeat, flags, ncells, audit_fraction=0.05, seed=0, tol=1e-3, stream=None):
         _check(lib().ef_surrogate_infer(self.handle, _ptr(F), _ptr(qfeat), _ptr(flags), int(ncells),
                                         float(audit_fraction), int(seed), float(tol), _stream(stream)))
+
+    def set_checker(self, mlp, tol):
+        """Gate every cell on the disagreement of a second network (None switches it off)."""
+        self.checker = mlp
+        _check(lib().ef_surrogate_set_checker(self.handle, None if mlp is None else mlp.handle, float(tol)))
+
+    def infer_ex(self, F, qfeat, flags, ncells, score=None, Q=None, audit_fraction=0.0, seed=0, tol=1e-3, stream=None):
+        _check(lib().ef_surrogate_infer_ex(self.handle, _ptr(F), _ptr(qfeat), _ptr(flags), _ptr(score), _ptr(Q),
+                                           int(ncells), float(audit_fraction), int(seed), float(tol), _stream(stream)))
 
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:

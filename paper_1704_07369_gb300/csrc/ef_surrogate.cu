@@ -207,7 +207,8 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
                                    const int *kvec, float pi_over_L, int64_t n, int nf, int nin, int idx0, const float *nu,
                                    const float *td, const float *Xn, float xmax, float N3, float audit_frac, uint64_t seed,
                                    float *qfeat, int *flags, unsigned long long *count, int64_t *list_off,
-                                   int64_t *list_id, int64_t cell, unsigned *audit)
+                                   int64_t *list_id, int64_t cell, unsigned *audit, const float *Ycheck, float check_tol,
+                                   float *score)
 {
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -216,11 +217,19 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
     const double *mi = mom + i * EF_DIAG_STRIDE;
     float ux, uy, uz;
     cell_velocity(mi, ux, uy, uz);
-    float prod = 0.f;
+    float prod = 0.f, dnum = 0.f, dden = 0.f;
     bool bad = false;
     for (int jm = lane; jm < nf / 2; jm += 32) {
         const float yr = (Ypred[i * ldy + 2 * jm] * td[2 * jm] + nu[2 * jm]) * m * m;
         const float yi = (Ypred[i * ldy + 2 * jm + 1] * td[2 * jm + 1] + nu[2 * jm + 1]) * m * m;
+        if (Ycheck && jm != idx0) {
+            // disagreement of the checker network, in the band's own units (the decoded modes
+            // differ by the same per-cell phase and scale, which the norms do not see)
+            const float cr = (Ycheck[i * ldy + 2 * jm] * td[2 * jm] + nu[2 * jm]) * m * m;
+            const float ci = (Ycheck[i * ldy + 2 * jm + 1] * td[2 * jm + 1] + nu[2 * jm + 1]) * m * m;
+            dnum += (yr - cr) * (yr - cr) + (yi - ci) * (yi - ci);
+            dden += yr * yr + yi * yi;
+        }
         const float ph = pi_over_L * (kvec[3 * jm] * ux + kvec[3 * jm + 1] * uy + kvec[3 * jm + 2] * uz);
         float sn, cs;
         sincosf(ph, &sn, &cs);
@@ -237,12 +246,17 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
             if (fabsf(Xn[i * kStride + j]) > xmax) bad = true;
     for (int o = 16; o > 0; o >>= 1) {
         prod += __shfl_xor_sync(0xffffffffu, prod, o);
+        dnum += __shfl_xor_sync(0xffffffffu, dnum, o);
+        dden += __shfl_xor_sync(0xffffffffu, dden, o);
         bad |= __shfl_xor_sync(0xffffffffu, (int)bad, o) != 0;
     }
     if (lane == 0) {
         prod *= 2.f * N3;
         int f = 0;
         if (bad || !(prod <= 0.f)) f |= 1;
+        const float dis = Ycheck ? sqrtf(dnum / fmaxf(dden, 1e-30f)) : 0.f;
+        if (score) score[i] = dis;
+        if (Ycheck && !(dis <= check_tol)) f |= 32;          // the checker disagrees: plain operator
         if (hash_unit(seed, i) < audit_frac) {
             f |= 2;
             atomicAdd(&audit[0], 1u);
@@ -303,6 +317,125 @@ __global__ void relist_kernel(const unsigned *audit, float max_miss, int64_t n, 
     list_id[k] = i;
 }
 
+// Q on the grid from the band: Q[i] = sum over the band (both halves) of q_k exp(2 pi i k.i / N), the
+// inverse of ef_features' transform on the band (index-origin convention), evaluated separably:
+//   S1[k0][k1][x] = sum_k2 c_k exp(2 pi i k2 x / N),  then per plane z
+//   T[k1][x] = sum_k0 S1[k0][k1][x] exp(2 pi i k0 z / N),  Q[z][y][x] = Re sum_k1 T[k1][x] exp(2 pi i k1 y / N).
+// One CTA of 256 threads per cell, 3D; cells whose flags carry 8 (plain operator used) take the
+// plain operator's full Q instead (the collide output of the fallback launch).
+constexpr int kBandK = EF_FEATURE_K, kBandW = 2 * EF_FEATURE_K + 1;
+
+template <int N>
+constexpr size_t band_grid_smem() { return (size_t)(kBandW * kBandW * kBandW + kBandW * kBandW * N + kBandW * N + N) * 8; }
+
+template <int N>
+__global__ void __launch_bounds__(256) band_to_grid_kernel(const float *qfeat, const int *kvec, int nmodes, const int *flags,
+                                                           const float *Qplain, float *Q, int64_t n)
+{
+    extern __shared__ float2 bsm[];
+    auto cf = reinterpret_cast<float2 (*)[kBandW][kBandW]>(bsm);                                    // [k0][k1][k2]
+    auto S1 = reinterpret_cast<float2 (*)[kBandW][N]>(bsm + kBandW * kBandW * kBandW);               // [k0][k1][x]
+    auto Tz = reinterpret_cast<float2 (*)[N]>(bsm + kBandW * kBandW * kBandW + kBandW * kBandW * N);   // [k1][x]
+    float2 *ex = bsm + kBandW * kBandW * kBandW + kBandW * kBandW * N + kBandW * N;                   // exp(2 pi i m / N)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int m = tid; m < N; m += nt) {
+        float s, c;
+        sincospif(2.0f * (float)m / (float)N, &s, &c);
+        ex[m] = make_float2(c, s);
+    }
+    constexpr int64_t CELL = (int64_t)N * N * N;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        float *Qi = Q + i * CELL;
+        if (flags && (flags[i] & 8)) {                     // the plain operator's full Q
+            const float4 *src = reinterpret_cast<const float4 *>(Qplain + i * CELL);
+            float4 *dst = reinterpret_cast<float4 *>(Qi);
+            for (int64_t t = tid; t < CELL / 4; t += nt) dst[t] = src[t];
+            continue;
+        }
+        __syncthreads();
+        for (int t = tid; t < kBandW * kBandW * kBandW; t += nt) (&cf[0][0][0])[t] = make_float2(0.f, 0.f);
+        __syncthreads();
+        for (int j = tid; j < nmodes; j += nt) {
+            const int k0 = kvec[3 * j], k1 = kvec[3 * j + 1], k2 = kvec[3 * j + 2];
+            const float re = qfeat[i * kStride + 2 * j], im = qfeat[i * kStride + 2 * j + 1];
+            cf[k0 + kBandK][k1 + kBandK][k2 + kBandK] = make_float2(re, im);
+            if (k0 || k1 || k2) cf[kBandK - k0][kBandK - k1][kBandK - k2] = make_float2(re, -im);
+        }
+        __syncthreads();
+        for (int t = tid; t < kBandW * kBandW * N; t += nt) {
+            const int x = t % N, k1 = (t / N) % kBandW, k0 = t / (N * kBandW);
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k2 = 0; k2 < kBandW; ++k2) {
+                const float2 c = cf[k0][k1][k2];
+                const float2 e = ex[(((k2 - kBandK) * x) % N + N) % N];
+                acc.x += c.x * e.x - c.y * e.y;
+                acc.y += c.x * e.y + c.y * e.x;
+            }
+            S1[k0][k1][x] = acc;
+        }
+        for (int z = 0; z < N; ++z) {
+            __syncthreads();
+            for (int t = tid; t < kBandW * N; t += nt) {
+                const int x = t % N, k1 = t / N;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k0 = 0; k0 < kBandW; ++k0) {
+                    const float2 c = S1[k0][k1][x];
+                    const float2 e = ex[(((k0 - kBandK) * z) % N + N) % N];
+                    acc.x += c.x * e.x - c.y * e.y;
+                    acc.y += c.x * e.y + c.y * e.x;
+                }
+                Tz[k1][x] = acc;
+            }
+            __syncthreads();
+            for (int t = tid; t < N * N; t += nt) {
+                const int x = t % N, y = t / N;
+                float acc = 0.f;
+#pragma unroll
+                for (int k1 = 0; k1 < kBandW; ++k1) {
+                    const float2 c = Tz[k1][x];
+                    const float2 e = ex[(((k1 - kBandK) * y) % N + N) % N];
+                    acc += c.x * e.x - c.y * e.y;
+                }
+                Qi[(int64_t)z * N * N + t] = acc;
+            }
+        }
+    }
+}
+
+template <int N>
+cudaError_t band_to_grid_n(const float *qfeat, const int *kvec, int nmodes, const int *flags, const float *Qplain, float *Q,
+                           int64_t n, cudaStream_t st)
+{
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(band_to_grid_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)band_grid_smem<N>());
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    const int grid = (int)std::min<int64_t>(n, 152 * 4);
+    band_to_grid_kernel<N><<<grid, 256, band_grid_smem<N>(), st>>>(qfeat, kvec, nmodes, flags, Qplain, Q, n);
+    return cudaGetLastError();
+}
+
+cudaError_t band_to_grid(int N, const float *qfeat, const int *kvec, int nmodes, const int *flags, const float *Qplain,
+                         float *Q, int64_t n, cudaStream_t st)
+{
+    switch (N) {
+    case 16: return band_to_grid_n<16>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
+    case 24: return band_to_grid_n<24>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
+    case 32: return band_to_grid_n<32>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
+    case 40: return band_to_grid_n<40>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
+    case 48: return band_to_grid_n<48>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
+    case 64: return band_to_grid_n<64>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 struct ef_surrogate_s {
@@ -322,6 +455,9 @@ struct ef_surrogate_s {
     int64_t *list_off = nullptr, *list_id = nullptr;
     float xmax = 8.f;
     float max_miss = 0.f;
+    ef_mlp_t checker = nullptr;           // second network; its disagreement gates cells (nullable)
+    float check_tol = 0.f;
+    float *Yc = nullptr;                  // checker outputs (max_batch rows)
 };
 
 namespace {
@@ -342,6 +478,7 @@ void sur_free(ef_surrogate_s *s)
     cudaFree(s->Y);
     cudaFree(s->qplain);
     cudaFree(s->Qs);
+    cudaFree(s->Yc);
     cudaFree(s->fh);
     cudaFree(s->audit);
     cudaFree(s->count);
@@ -506,8 +643,47 @@ ef_status ef_surrogate_set_policy(ef_surrogate_t s, float max_miss_fraction, flo
     return EF_OK;
 }
 
+ef_status ef_features_inverse(ef_plan_t plan, const float *feat, float *Q_dev, int64_t ncells, ef_stream_t stream)
+{
+    ef::PlanView v;
+    if (!ef::plan_view(plan, &v)) return sfail(EF_ERR_INVALID_ARG, "ef_features_inverse: needs a uniform plan");
+    if (v.prec != EF_PREC_F32 || v.d != 3 || v.nfeat == 0) return sfail(EF_ERR_UNSUPPORTED, "ef_features_inverse: FP32 3D plans with a band");
+    if (ncells < 0) return sfail(EF_ERR_INVALID_ARG, "ncells < 0");
+    if (ncells == 0) return EF_OK;
+    if (!feat || !Q_dev || (uintptr_t)Q_dev % 16) return sfail(EF_ERR_INVALID_ARG, "null feat or Q, or Q not 16-byte aligned");
+    const cudaError_t e = band_to_grid(v.N, feat, v.modes, v.nfeat, nullptr, nullptr, Q_dev, ncells, (cudaStream_t)stream);
+    return e == cudaSuccess ? EF_OK : scuda(e, "ef_features_inverse");
+}
+
+ef_status ef_surrogate_set_checker(ef_surrogate_t s, ef_mlp_t checker, float tol)
+{
+    if (!s) return sfail(EF_ERR_INVALID_ARG, "null surrogate");
+    if (checker) {
+        int64_t a[8], b[8];
+        ef_status st = ef_mlp_info(s->mlp, a);
+        if (st == EF_OK) st = ef_mlp_info(checker, b);
+        if (st != EF_OK) return st;
+        if (a[0] != b[0] || a[3] != b[3] || b[7] < s->max_batch)
+            return sfail(EF_ERR_INVALID_ARG, "checker: same inputs and outputs as the surrogate's network, max batch >= the surrogate's");
+        if (!(tol > 0.f)) return sfail(EF_ERR_INVALID_ARG, "checker tolerance must be > 0");
+        if (!s->Yc) {
+            cudaError_t e = cudaMalloc((void **)&s->Yc, (size_t)s->max_batch * s->noutp * 4);
+            if (e != cudaSuccess) { s->Yc = nullptr; return scuda(e, "checker outputs"); }
+        }
+    }
+    s->checker = checker;
+    s->check_tol = tol;
+    return EF_OK;
+}
+
 ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int *flags, int64_t ncells, float audit_fraction,
                              uint64_t seed, float tol, ef_stream_t stream)
+{
+    return ef_surrogate_infer_ex(s, F, qfeat, flags, nullptr, nullptr, ncells, audit_fraction, seed, tol, stream);
+}
+
+ef_status ef_surrogate_infer_ex(ef_surrogate_t s, const void *F, float *qfeat, int *flags, float *score, float *Q,
+                                int64_t ncells, float audit_fraction, uint64_t seed, float tol, ef_stream_t stream)
 {
     if (!s || !F || !qfeat || !flags) return sfail(EF_ERR_INVALID_ARG, "null argument");
     if (ncells < 0 || ncells > s->max_batch || ncells % 64) return sfail(EF_ERR_INVALID_ARG, "ncells: multiple of 64, <= max_batch");
@@ -535,13 +711,19 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
     if (r != EF_OK) return r;
     r = ef_mlp_forward(s->mlp, s->X, kStride, s->Y, s->noutp, ncells, stream);
     if (r != EF_OK) return r;
+    if (s->checker) {
+        r = ef_mlp_forward(s->checker, s->X, kStride, s->Yc, s->noutp, ncells, stream);
+        if (r != EF_OK) return r;
+    }
+    if (Q && (v.prec != EF_PREC_F32 || v.d != 3 || (uintptr_t)Q % 16)) return sfail(EF_ERR_UNSUPPORTED, "Q on the grid: FP32 3D plans, 16-byte aligned Q");
     e = cudaMemsetAsync(s->count, 0, 8, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->audit, 0, 8, st);
     if (e != cudaSuccess) return scuda(e, "surrogate reset");
     decode_gate_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(
         s->Y, s->noutp, s->featF, s->featL, s->mom, s->kvec, s->pi_over_L, ncells, s->nf, s->nin, s->idx0, s->nu, s->td, s->X,
         s->xmax, (float)cell,
-        audit_fraction, seed, qfeat, flags, s->count, s->list_off, s->list_id, cell, s->audit);
+        audit_fraction, seed, qfeat, flags, s->count, s->list_off, s->list_id, cell, s->audit,
+        s->checker ? s->Yc : nullptr, s->check_tol, score);
     for (int round = 0; round < 2; ++round) {
         // plain operator on the listed cells (count read on the device), then their band
         ef::CollideArgs a{};
@@ -586,6 +768,10 @@ ef_status ef_surrogate_infer(ef_surrogate_t s, const void *F, float *qfeat, int 
             relist_kernel<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(s->audit, s->max_miss, ncells, flags,
                                                                             s->count, s->list_off, s->list_id, cell);
         }
+    }
+    if (Q) {
+        e = band_to_grid(v.N, qfeat, s->kvec, s->nf / 2, flags, static_cast<const float *>(s->Qs), Q, ncells, st);
+        if (e != cudaSuccess) return scuda(e, "band to grid");
     }
     e = cudaGetLastError();
     return e == cudaSuccess ? EF_OK : scuda(e, "surrogate infer");

@@ -80,33 +80,74 @@ class Trainer:
         self.wmask = loss_mask(self.nf, zero_slot())
 
     def fit(self, featF, featQ, mom, epochs=20, lr0=1e-3, lr1=1e-5, seed=0, log=None, warmup=0.02):
-        n = featF.shape[0] // self.batch * self.batch
+        """Fits the normalisation on the training set, then trains the surrogate's network.  The
+        normalised training set is kept for fit_checker."""
         X = torch.zeros(featF.shape[0], EF_FEATURE_STRIDE, device=featF.device)
         Y = torch.zeros_like(X)
         rw = torch.zeros(featF.shape[0], device=featF.device)
         self.sur.fit_stats(featF, featQ, mom, X, Y, featF.shape[0], rowweight=rw)
         self.sur.normalize(featF, featQ, mom, X, Y, featF.shape[0])
-        loss = torch.zeros(1, device=featF.device)
+        self._train_set = (X, Y, rw)
+        return self._train(self.mlp, epochs, lr0, lr1, seed, log, warmup)
+
+    def _train(self, net, epochs, lr0, lr1, seed, log, warmup):
+        X, Y, rw = self._train_set
+        n = X.shape[0] // self.batch * self.batch
+        loss = torch.zeros(1, device=X.device)
         g = torch.Generator(device="cpu")
         g.manual_seed(seed)
         steps = epochs * (n // self.batch)
         hist = []
         step = 0
         for ep in range(epochs):
-            perm = torch.randperm(featF.shape[0], generator=g)[:n].to(featF.device)
+            perm = torch.randperm(X.shape[0], generator=g)[:n].to(X.device)
             Xs, Ys, Rs = X[perm], Y[perm], rw[perm]
-            tot = torch.zeros(1, device=featF.device)
+            tot = torch.zeros(1, device=X.device)
             for b0 in range(0, n, self.batch):
                 lr = lr1 + 0.5 * (lr0 - lr1) * (1 + math.cos(math.pi * step / max(1, steps)))
                 lr *= min(1.0, (step + 1) / max(1.0, warmup * steps))
-                self.mlp.train_step(Xs[b0:b0 + self.batch], Ys[b0:b0 + self.batch], self.batch, lr, loss,
-                                    wmask=self.wmask, rowweight=Rs[b0:b0 + self.batch])
+                net.train_step(Xs[b0:b0 + self.batch], Ys[b0:b0 + self.batch], self.batch, lr, loss,
+                               wmask=self.wmask, rowweight=Rs[b0:b0 + self.batch])
                 tot += loss
                 step += 1
             hist.append(float(tot.item()) / (n // self.batch))
             if log:
                 log(ep, hist[-1])
         return hist
+
+    def fit_checker(self, epochs=20, lr0=1e-3, lr1=1e-5, seed=1, init_seed=101, log=None, warmup=0.02):
+        """Trains the checker network (same widths, another initialisation and sample order) on the
+        training set of fit(); ef_surrogate_set_checker then gates cells on the two networks'
+        disagreement (calibrate chooses the threshold)."""
+        nin = self.mlp.nin
+        self.checker = MLP(nin, self.mlp.nhidden, self.mlp.nlayers, self.nf, self.mlp.max_batch, seed=init_seed)
+        return self._train(self.checker, epochs, lr0, lr1, seed, log, warmup)
+
+    def calibrate(self, F, ncells, tol=1e-3, margin=0.8, seed=0):
+        """Chooses the checker threshold on held-out cells F (resident, ncells a multiple of 64): with
+        the checker's scores s_i and the surrogate's band errors e_i against the plain operator,
+        the threshold is margin * min{s_i : e_i > tol} (every miss of the calibration set is
+        flagged, with room to spare), or the largest score / margin if nothing misses.  Returns
+        (threshold, fraction of calibration cells flagged, misses)."""
+        from . import ef_features
+        q = torch.zeros(ncells, EF_FEATURE_STRIDE, device=F.device)
+        flags = torch.zeros(ncells, dtype=torch.int32, device=F.device)
+        score = torch.zeros(ncells, device=F.device)
+        self.sur.set_checker(self.checker, 3.0e38)
+        self.sur.infer_ex(F, q, flags, ncells, score=score, audit_fraction=0.0, seed=seed, tol=tol)
+        Q = torch.empty_like(F)
+        self.plan.collide(F, Q, ncells=ncells)
+        ref = torch.zeros_like(q)
+        ef_features(self.plan.handle, Q, ref, ncells)
+        e = band_rel_l2(q, ref)
+        sc = score.double()
+        miss = e > tol
+        if bool(miss.any()):
+            thr = float(margin * sc[miss].min())
+        else:
+            thr = float(sc.max() / margin)
+        self.sur.set_checker(self.checker, thr)
+        return thr, float((sc > thr).double().mean()), int(miss.sum())
 
     def predict(self, F, ncells, audit_fraction=0.0, seed=0, tol=1e-3):
         q = torch.zeros(ncells, EF_FEATURE_STRIDE, device=F.device)

@@ -66,7 +66,7 @@ def test_no_operation_allocates_or_synchronises():
     source of the operation bodies: every cudaMalloc / cudaFree / cudaDeviceSynchronize sits in a
     create, reserve, destroy, status, autotune or table-building function."""
     allowed = re.compile(r"^(ef_plan_create\w*|ef_plan_reserve|ef_plan_destroy|ef_plan_status|ef_mlp_status|"
-                         r"ef_mlp_create|ef_mlp_destroy|ef_mlp_params|ef_surrogate_create|ef_surrogate_destroy|"
+                         r"ef_mlp_create|ef_mlp_destroy|ef_mlp_params|ef_surrogate_create|ef_surrogate_destroy|ef_surrogate_set_checker|"
                          r"ef_surrogate_stats|ef_stream_plan_create|ef_stream_plan_destroy|ef_classical_create|"
                          r"ef_classical_destroy|ef_galerkin_create|gfree|choose_shape|upload_table|build_class|alloc_workspaces|"
                          r"destroy_plan|finish_plan|cfree|\w*_free)$")

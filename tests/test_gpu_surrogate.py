@@ -330,3 +330,82 @@ def test_surrogate_audit_and_fallback_paths():
     assert torch.equal(q[:, :926], ref[:, :926])
     with pytest.raises(ef.EfError):
         sur.set_policy(max_miss_fraction=1.5)
+
+
+def test_features_inverse_projects_on_the_band():
+    """ef_features_inverse returns a band-limited field exactly (features -> grid -> features is the
+    identity on the band) and maps a general cell to its truncation to |k| <= 6, against the
+    oracle's DFT with the modes outside the band zeroed."""
+    N, L, n = 32, 8.0, 3
+    plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F32)
+    cells = [inputs.mixture_cell(3, N, L, 90 + i) for i in range(n)]
+    F = torch.tensor(np.stack(cells), dtype=torch.float32, device="cuda")
+    feat = torch.zeros(n, ef.EF_FEATURE_STRIDE, device="cuda")
+    ef.ef_features(plan.handle, F, feat, n)
+    P = torch.empty_like(F)
+    ef.ef_features_inverse(plan.handle, feat, P, n)
+    feat2 = torch.zeros_like(feat)
+    ef.ef_features(plan.handle, P, feat2, n)
+    torch.cuda.synchronize()
+    a, b = feat2[:, :926].cpu().numpy(), feat[:, :926].cpu().numpy()
+    assert np.abs(a - b).max() <= 2e-6 * np.abs(b).max()
+    k = np.fft.fftfreq(N, 1.0 / N)
+    K0, K1, K2 = np.meshgrid(k, k, k, indexing="ij")
+    band = K0 ** 2 + K1 ** 2 + K2 ** 2 <= 36
+    for i in range(n):
+        c = F[i].double().cpu().numpy()
+        ref = np.real(np.fft.ifftn(np.fft.fftn(c) * band))   # index-origin DFT, truncated, inverted
+        got = P[i].double().cpu().numpy()
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_checker_gate_and_q_on_the_grid():
+    """The checker gate: with the surrogate's own network as checker every score is zero and no
+    cell is flagged; with a different network and a threshold below every score, every cell goes
+    to the plain operator (flags 32 and 8) and Q on the grid is the plain operator's Q bit for bit;
+    cells that keep the prediction get its band mapped to the grid."""
+    N, L, n = 16, 8.0, 128
+    plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F32)
+    net = ef.MLP(926, 64, 3, 926, n, seed=1)
+    other = ef.MLP(926, 64, 3, 926, n, seed=2)
+    sur = ef.Surrogate(plan, net, n)
+    F = inputs.bkw_family_torch(N, L, n, seed=78)
+    Q = torch.empty_like(F)
+    plan.collide(F, Q, ncells=n)
+    ref = torch.zeros(n, ef.EF_FEATURE_STRIDE, device="cuda")
+    ef.ef_features(plan.handle, Q, ref, n)
+    fF = torch.zeros_like(ref)
+    ef.ef_features(plan.handle, F, fF, n)
+    mom = torch.zeros(n, ef.EF_DIAG_STRIDE, dtype=torch.float64, device="cuda")
+    ef.ef_moments_entropy(plan.handle, F, None, mom, n)
+    Xt, Yt = torch.zeros_like(ref), torch.zeros_like(ref)
+    sur.fit_stats(fF, ref, mom, Xt, Yt, n)
+    sur.set_policy(max_miss_fraction=0.0, xmax=1e30)        # no input-envelope gate here
+    q = torch.zeros_like(ref)
+    flags = torch.zeros(n, dtype=torch.int32, device="cuda")
+    score = torch.full((n,), -1.0, device="cuda")
+    G = torch.empty_like(F)
+    sur.set_checker(net, 1e-6)
+    sur.infer_ex(F, q, flags, n, score=score, Q=G, audit_fraction=0.0, seed=3)
+    torch.cuda.synchronize()
+    assert float(score.abs().max()) == 0.0
+    f = flags.cpu().numpy()
+    assert ((f & 32) == 0).all()
+    keep = torch.tensor((f & 8) == 0, device="cuda")
+    if bool(keep.any()):                                    # delivered cells: Q on the grid = the band's inverse
+        P = torch.empty_like(F)
+        ef.ef_features_inverse(plan.handle, q, P, n)
+        torch.cuda.synchronize()
+        d = (G[keep] - P[keep]).abs().max() / P[keep].abs().max()
+        assert float(d) <= 1e-6
+    sur.set_checker(other, 1e-12)
+    sur.infer_ex(F, q, flags, n, score=score, Q=G, audit_fraction=0.0, seed=3)
+    torch.cuda.synchronize()
+    f = flags.cpu().numpy()
+    assert ((f & 40) == 40).all()
+    assert float(score.min()) > 0.0
+    assert torch.equal(G, Q)
+    assert torch.equal(q[:, :926], ref[:, :926])
+    sur.set_checker(None, 1.0)
+    with pytest.raises(ef.EfError):
+        sur.set_checker(other, 0.0)
