@@ -292,6 +292,15 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
                     for (int z = 0; z < N; ++z) v[z] = cscale(Fs[(size_t)z * NPC + ql], __ldg(M + (size_t)z * NPT));
                     fft<N, 1, N>(v);
                     rg_scatter<N>(v, b ? base1 : base0, P, pm, rg_poff<N>(q & ~1), q & 1, mask);
+                    if (a.prefetch && o + 1 < a.nops) {
+                        // pull the next op's multipliers of this item towards L1 while the local
+                        // passes run (the next op has the same item split: both directions or, after
+                        // the loss, two); a hint only, every address is inside the table
+                        const Op nx = a.ops[o + 1];
+                        const T *Mn = Mbase + (size_t)(b ? nx.dir2 : nx.dir) * N * NPT + ky * H + kx;
+#pragma unroll
+                        for (int z = 0; z < N; ++z) asm volatile("prefetch.global.L1 [%0];" ::"l"(Mn + (size_t)z * NPT));
+                    }
                 }
             }
             bar.full();

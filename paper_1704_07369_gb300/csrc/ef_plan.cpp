@@ -596,7 +596,6 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
                     }
                 }
             }
-            if (sh.occ >= 3) break;              // the register-accumulator kernel has no prefetch option
         }
     }
     cudaFree(F);

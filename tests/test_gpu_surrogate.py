@@ -360,8 +360,9 @@ def test_features_inverse_projects_on_the_band():
 
 
 def test_checker_gate_and_q_on_the_grid():
-    """The checker gate: with the surrogate's own network as checker every score is zero and no
-    cell is flagged; with a different network and a threshold below every score, every cell goes
+    """The checker gate: with the surrogate's own network as checker every score is at FP32
+    round-off (the two forward passes need not agree bit for bit) and no cell is flagged at a
+    threshold above it; with a different network and a threshold below every score, every cell goes
     to the plain operator (flags 32 and 8) and Q on the grid is the plain operator's Q bit for bit;
     cells that keep the prediction get its band mapped to the grid."""
     N, L, n = 16, 8.0, 128
@@ -385,10 +386,10 @@ def test_checker_gate_and_q_on_the_grid():
     flags = torch.zeros(n, dtype=torch.int32, device="cuda")
     score = torch.full((n,), -1.0, device="cuda")
     G = torch.empty_like(F)
-    sur.set_checker(net, 1e-6)
+    sur.set_checker(net, 1e-4)
     sur.infer_ex(F, q, flags, n, score=score, Q=G, audit_fraction=0.0, seed=3)
     torch.cuda.synchronize()
-    assert float(score.abs().max()) == 0.0
+    assert 0.0 <= float(score.min()) and float(score.max()) <= 1e-6
     f = flags.cpu().numpy()
     assert ((f & 32) == 0).all()
     keep = torch.tensor((f & 8) == 0, device="cuda")
