@@ -767,7 +767,7 @@ def main():
     ap.add_argument("--no-kernels", action="store_true", help="skip the HBM-bound kernels' timings")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the precision study (N = 64) and the small configurations' timings")
-    ap.add_argument("--chunks", type=int, default=8, help="chunks of the streamed end-to-end leg")
+    ap.add_argument("--chunks", type=int, default=32, help="chunks of the streamed end-to-end leg")
     ap.add_argument("--strong", action="store_true",
                     help="split one --cells batch over the ranks (default: a batch per rank)")
     ap.add_argument("--sur-epochs", type=int, default=300)

@@ -220,15 +220,20 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
     float prod = 0.f, dnum = 0.f, dden = 0.f;
     bool bad = false;
     for (int jm = lane; jm < nf / 2; jm += 32) {
-        const float yr = (Ypred[i * ldy + 2 * jm] * td[2 * jm] + nu[2 * jm]) * m * m;
-        const float yi = (Ypred[i * ldy + 2 * jm + 1] * td[2 * jm + 1] + nu[2 * jm + 1]) * m * m;
-        if (Ycheck && jm != idx0) {
-            // disagreement of the checker network, in the band's own units (the decoded modes
-            // differ by the same per-cell phase and scale, which the norms do not see)
+        float yr = (Ypred[i * ldy + 2 * jm] * td[2 * jm] + nu[2 * jm]) * m * m;
+        float yi = (Ypred[i * ldy + 2 * jm + 1] * td[2 * jm + 1] + nu[2 * jm + 1]) * m * m;
+        if (Ycheck) {
+            // the two networks: their disagreement in the band's own units (the decoded modes
+            // differ by the same per-cell phase and scale, which the norms do not see), and their
+            // mean as the prediction (an ensemble of two, more accurate than either)
             const float cr = (Ycheck[i * ldy + 2 * jm] * td[2 * jm] + nu[2 * jm]) * m * m;
             const float ci = (Ycheck[i * ldy + 2 * jm + 1] * td[2 * jm + 1] + nu[2 * jm + 1]) * m * m;
-            dnum += (yr - cr) * (yr - cr) + (yi - ci) * (yi - ci);
-            dden += yr * yr + yi * yi;
+            yr = 0.5f * (yr + cr);
+            yi = 0.5f * (yi + ci);
+            if (jm != idx0) {
+                dnum += 4.f * ((yr - cr) * (yr - cr) + (yi - ci) * (yi - ci));
+                dden += yr * yr + yi * yi;
+            }
         }
         const float ph = pi_over_L * (kvec[3 * jm] * ux + kvec[3 * jm + 1] * uy + kvec[3 * jm + 2] * uz);
         float sn, cs;
