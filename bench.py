@@ -597,6 +597,7 @@ SUR_AUDIT = 0.02
 SUR_BATCH = 512
 SUR_LR = 7e-4
 SUR_LR1 = 1e-6
+SUR_BUDGET = 0.08           # fraction of cells the budgeted checker threshold sends to the plain operator
 
 
 def _quantiles(e):
@@ -649,7 +650,8 @@ def surrogate_leg(args, device):
         tr._train_set = None
         # checker threshold from a held-out calibration batch (seeds disjoint from training and test)
         inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 8_000_000, device=device, out=F)
-        thr, cal_flagged, cal_miss = tr.calibrate(F, SUR_CELLS, SUR_TOL, margin=0.8)
+        thr, cal_flagged, cal_miss, _ = tr.calibrate(F, SUR_CELLS, SUR_TOL, margin=0.8)
+        thr_b, cal_flagged_b, _, cal_left_b = tr.calibrate(F, SUR_CELLS, SUR_TOL, budget=SUR_BUDGET)
         inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 9_000_000, device=device, out=F)
         # references: plain FP32 band of every cell, FP64 band of the first 1024
         plan.collide(F, Q, ncells=SUR_CELLS)
@@ -680,35 +682,42 @@ def surrogate_leg(args, device):
         res = {"plain_ms": plain_ms, "plain_cells_per_s": SUR_CELLS / plain_ms * 1e3,
                "train": {"data_s": data_s, "train_s": train_s, "final_loss": hist[-1],
                          "checker_train_s": train_c_s, "checker_final_loss": hist_c[-1]},
-               "checker_calibration": {"threshold": thr, "flagged_fraction": cal_flagged, "misses_in_calibration_set": cal_miss,
-                                       "cells": SUR_CELLS, "margin": 0.8}, "policies": {}}
+               "checker_calibration": {"cells": SUR_CELLS, "misses_in_calibration_set": cal_miss,
+                                       "catch_all": {"threshold": thr, "flagged_fraction": cal_flagged, "margin": 0.8},
+                                       "budget": {"threshold": thr_b, "flagged_fraction": cal_flagged_b,
+                                                  "misses_left_unflagged": cal_left_b}},
+               "policies": {}}
         q = torch.zeros(SUR_CELLS, ef.EF_FEATURE_STRIDE, device=device)
         flags = torch.zeros(SUR_CELLS, dtype=torch.int32, device=device)
         # the guarded path end to end: checker gate, Q on the grid (band reconstruction where the
-        # prediction is delivered, the plain operator's full Q where it is not), no audit
+        # prediction is delivered, the plain operator's full Q where it is not), no audit; with the
+        # threshold that flagged every calibration miss, and with the one that flags a fixed budget
         Qg = torch.empty_like(F)
-        ms = timed(lambda i: tr.sur.infer_ex(F, q, flags, SUR_CELLS, Q=Qg, audit_fraction=0.0, seed=i, tol=SUR_TOL), reps)
-        f = flags.cpu().numpy()
-        e = S.band_rel_l2(q, ref)
-        e64 = S.band_rel_l2(q[:n64], ref64)
-        # Q on the grid against the plain operator's full Q, and the band's own truncation floor
-        # (the plain Q against its projection on the band), per cell over the first 1024 cells
         proj = torch.empty(n64, SUR_N, SUR_N, SUR_N, device=device)
         ef.ef_features_inverse(plan.handle, ref[:n64], proj, n64)
-        Qd, Gd, Pd = Q[:n64].double(), Qg[:n64].double(), proj.double()
-        nrm = Qd.pow(2).sum(dim=(1, 2, 3)).sqrt()
-        full_err = (Gd - Qd).pow(2).sum(dim=(1, 2, 3)).sqrt() / nrm
-        floor = (Pd - Qd).pow(2).sum(dim=(1, 2, 3)).sqrt() / nrm
-        del proj, Qd, Gd, Pd
-        res["policies"]["checked_to_grid"] = {
-            "audit_fraction": 0.0, "checker_threshold": thr, "ms": ms, "cells_per_s": SUR_CELLS / ms * 1e3,
-            "speedup_vs_plain": plain_ms / ms, "output": "Q on the grid (N^3 per cell)",
-            "checker_flagged": int(((f & 32) != 0).sum()), "gated": int(((f & 1) != 0).sum()),
-            "plain_used": int(((f & 8) != 0).sum()),
-            "band_rel_l2_vs_fp32_plain": _quantiles(e), "band_rel_l2_vs_fp64_first1024": _quantiles(e64),
-            "full_Q_rel_l2_vs_plain_first1024": _quantiles(full_err),
-            "band_truncation_floor_first1024": {"p50": float(floor.median()),
-                                                "max": float(floor.max()), "mean": float(floor.mean())}}
+        for pname, th in (("checked_catch_all_to_grid", thr), ("checked_budget_to_grid", thr_b)):
+            tr.sur.set_checker(tr.checker, th)
+            ms = timed(lambda i: tr.sur.infer_ex(F, q, flags, SUR_CELLS, Q=Qg, audit_fraction=0.0, seed=i, tol=SUR_TOL), reps)
+            f = flags.cpu().numpy()
+            e = S.band_rel_l2(q, ref)
+            e64 = S.band_rel_l2(q[:n64], ref64)
+            # Q on the grid against the plain operator's full Q, and the band's own truncation floor
+            # (the plain Q against its projection on the band), per cell over the first 1024 cells
+            Qd, Gd, Pd = Q[:n64].double(), Qg[:n64].double(), proj.double()
+            nrm = Qd.pow(2).sum(dim=(1, 2, 3)).sqrt()
+            full_err = (Gd - Qd).pow(2).sum(dim=(1, 2, 3)).sqrt() / nrm
+            floor = (Pd - Qd).pow(2).sum(dim=(1, 2, 3)).sqrt() / nrm
+            del Qd, Gd, Pd
+            res["policies"][pname] = {
+                "audit_fraction": 0.0, "checker_threshold": th, "ms": ms, "cells_per_s": SUR_CELLS / ms * 1e3,
+                "speedup_vs_plain": plain_ms / ms, "output": "Q on the grid (N^3 per cell)",
+                "checker_flagged": int(((f & 32) != 0).sum()), "gated": int(((f & 1) != 0).sum()),
+                "plain_used": int(((f & 8) != 0).sum()),
+                "band_rel_l2_vs_fp32_plain": _quantiles(e), "band_rel_l2_vs_fp64_first1024": _quantiles(e64),
+                "full_Q_rel_l2_vs_plain_first1024": _quantiles(full_err),
+                "band_truncation_floor_first1024": {"p50": float(floor.median()), "max": float(floor.max()),
+                                                    "mean": float(floor.mean())}}
+        del proj
         del Qg
         tr.sur.set_checker(None, 1.0)
         # unguarded upper bound (nothing judges the cells) and the audit policies, band output only

@@ -123,12 +123,13 @@ class Trainer:
         self.checker = MLP(nin, self.mlp.nhidden, self.mlp.nlayers, self.nf, self.mlp.max_batch, seed=init_seed)
         return self._train(self.checker, epochs, lr0, lr1, seed, log, warmup)
 
-    def calibrate(self, F, ncells, tol=1e-3, margin=0.8, seed=0):
+    def calibrate(self, F, ncells, tol=1e-3, margin=0.8, seed=0, budget=None):
         """Chooses the checker threshold on held-out cells F (resident, ncells a multiple of 64): with
-        the checker's scores s_i and the surrogate's band errors e_i against the plain operator,
-        the threshold is margin * min{s_i : e_i > tol} (every miss of the calibration set is
-        flagged, with room to spare), or the largest score / margin if nothing misses.  Returns
-        (threshold, fraction of calibration cells flagged, misses)."""
+        the checker's scores s_i and the delivered band errors e_i against the plain operator, the
+        threshold is margin * min{s_i : e_i > tol} (every miss of the calibration set is flagged,
+        with room to spare), or the largest score / margin if nothing misses.  With a budget
+        (fraction of cells), the threshold is instead the score quantile that flags that fraction.
+        Returns (threshold, fraction of calibration cells flagged, misses, misses left unflagged)."""
         from . import ef_features
         q = torch.zeros(ncells, EF_FEATURE_STRIDE, device=F.device)
         flags = torch.zeros(ncells, dtype=torch.int32, device=F.device)
@@ -142,12 +143,14 @@ class Trainer:
         e = band_rel_l2(q, ref)
         sc = score.double()
         miss = e > tol
-        if bool(miss.any()):
+        if budget is not None:
+            thr = float(torch.quantile(sc, 1.0 - float(budget)))
+        elif bool(miss.any()):
             thr = float(margin * sc[miss].min())
         else:
             thr = float(sc.max() / margin)
         self.sur.set_checker(self.checker, thr)
-        return thr, float((sc > thr).double().mean()), int(miss.sum())
+        return thr, float((sc > thr).double().mean()), int(miss.sum()), int((miss & (sc <= thr)).sum())
 
     def predict(self, F, ncells, audit_fraction=0.0, seed=0, tol=1e-3):
         q = torch.zeros(ncells, EF_FEATURE_STRIDE, device=F.device)
