@@ -29,26 +29,40 @@ namespace ef {
 
 // Slab layout of one axis-0 plane: N rows (k_y) of N/2 stored k_x values (complex).  Where a row
 // holds a multiple of 4 16-byte pairs (N = 16, 32, 48, 64) the pairs of row y are stored in the
-// order pair ^ ((y >> 1) & 3) (an XOR swizzle inside aligned groups of four pairs); otherwise each
-// row is padded to N/2 + 2 values (an odd number of pairs).  Either way 16-byte accesses to pair j
-// of eight consecutive rows, and 8-byte accesses to a k_x range of one row, fall on distinct banks.
+// order pair ^ s(y), an XOR swizzle inside aligned groups of pairs: s(y) = y & 7 when a row holds a
+// multiple of 8 pairs (its rows all start on the same bank), (y >> 1) & 3 when it holds 4 mod 8
+// (consecutive rows start 64 bytes apart).  Otherwise each row is padded to N/2 + 2 values (an odd
+// number of pairs).  Either way 16-byte accesses to pair j of eight consecutive rows, and 8-byte
+// accesses to a k_x range of one row, fall on distinct banks.
 template <int N>
 __host__ __device__ constexpr bool rg_swizzled() { return (N / 4) % 4 == 0; }
 template <int N>
 __host__ __device__ constexpr int rg_row_stride() { return rg_swizzled<N>() ? N / 2 : N / 2 + 2; }
+template <int N>
+__device__ __forceinline__ int rg_swz(int y)
+{
+    if constexpr (!rg_swizzled<N>()) return 0;
+    else if constexpr ((N / 4) % 8 == 0) return y & 7;
+    else return (y >> 1) & 3;
+}
 // offset (complex values) of (k_y = y, k_x) inside a plane; the pair (k_x even, k_x + 1) stays adjacent
 template <int N>
 __device__ __forceinline__ int rg_at(int y, int kx)
 {
-    if constexpr (rg_swizzled<N>()) return y * (N / 2) + ((((kx >> 1) ^ ((y >> 1) & 3)) << 1) | (kx & 1));
+    if constexpr (rg_swizzled<N>()) return y * (N / 2) + ((((kx >> 1) ^ rg_swz<N>(y)) << 1) | (kx & 1));
     else return y * rg_row_stride<N>() + kx;
 }
-// plane stride: N rows, padded to 8 mod 16 complex values
+// plane stride: N rows, padded to r mod 16 complex values (16 values = 128 bytes, one bank line).
+// Swizzled rows: r = 8, so that the two lanes of a scatter pair (planes z and z + 1, same pencil
+// offset) store to opposite halves of a line.  Padded rows: r = N/2 mod 16, so that column q =
+// plane * N/2 + k_x of a column pass sits at bank slot q + const (mod 16) and the warps of the
+// axis-1 passes, which straddle planes, touch every 8-byte slot exactly twice.
 template <int N>
 __host__ __device__ constexpr int rg_plane_stride()
 {
     constexpr int s = N * rg_row_stride<N>();
-    return s + ((8 - s % 16) + 16) % 16;
+    constexpr int r = rg_swizzled<N>() ? 8 : (N / 2) % 16;
+    return s + ((r - s % 16) % 16 + 16) % 16;
 }
 // Instantiations ("variants", one CTA per SM each): 1 = the gain accumulator G in registers, one
 // row per thread, the size's widest launch bound; 2 = G in registers, two rows per thread; 3 = G in
@@ -136,8 +150,8 @@ __device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, int y0, const C
 {
     const float4 *A = reinterpret_cast<const float4 *>(R0);
     const float4 *B = reinterpret_cast<const float4 *>(R1);
-    const int sw0 = rg_swizzled<N>() ? (y0 >> 1) & 3 : 0;
-    const int sw1 = rg_swizzled<N>() ? (y1 >> 1) & 3 : 0;
+    const int sw0 = rg_swz<N>(y0);
+    const int sw1 = rg_swz<N>(y1);
 #pragma unroll
     for (int k2 = 0; k2 < N / 2; k2 += 2) {
         const float4 a = A[(k2 / 2) ^ sw0], b = B[(k2 / 2) ^ sw1];

@@ -33,9 +33,11 @@ def rg_bound(N, v):
 
 
 def _npp(N):
-    rs = N // 2 if (N // 4) % 4 == 0 else N // 2 + 2
+    swz = (N // 4) % 4 == 0
+    rs = N // 2 if swz else N // 2 + 2
     s = N * rs
-    return s + ((8 - s % 16) + 16) % 16
+    r = 8 if swz else (N // 2) % 16
+    return s + ((r - s % 16) % 16 + 16) % 16
 
 
 def rg_shapes(N):
