@@ -595,9 +595,12 @@ SUR_TRAIN = 204800
 SUR_TOL = 1e-3
 SUR_AUDIT = 0.02
 SUR_BATCH = 512
-SUR_LR = 7e-4
+SUR_HIDDEN = 768            # network width and depth (4 hidden layers)
+SUR_LAYERS = 5
+SUR_LR = 5e-4
 SUR_LR1 = 1e-6
-SUR_BUDGET = 0.08           # fraction of cells the budgeted checker threshold sends to the plain operator
+SUR_TARGET = 5.0            # speed-up over the plain operator the budgeted checker threshold is sized for
+SUR_BUDGETS = (0.02, 0.04, 0.08)   # fixed budgets reported beside it
 
 
 def _quantiles(e):
@@ -610,14 +613,20 @@ def _quantiles(e):
 
 def surrogate_leg(args, device):
     """Surrogate vs plain on batches of 16384 BKW-family cells (3D, N = 32, L = 8), for the
-    hard-sphere and Maxwell kernels: the network (928 -> 512 x 3 -> 926, bf16 weights, FP32
+    hard-sphere and Maxwell kernels: the network (928 -> 768 x 4 -> 926, bf16 weights, FP32
     accumulation) and a checker network of the same shape are trained on 204800 cells generated by
     the library; the checker threshold is calibrated on 16384 held-out cells; then plain-operator
-    and surrogate throughput are timed on a third batch.  The guarded policy ("checked_to_grid")
-    runs the checker gate and returns Q on the grid; its delivered band is compared cell by cell
-    with the plain FP32 band (all cells) and the FP64 band (first 1024 cells), its grid Q with the
-    plain Q, beside the band's truncation floor.  The other policies return the band only; the
-    unaudited one judges no cell and is an upper bound of the speed, not a guarded result."""
+    and surrogate throughput are timed on a third batch.  The guarded policies ("checked_*_to_grid")
+    deliver the mean of the two networks, send the cells where they disagree most to the plain
+    operator and return Q on the grid; they run without the entropy-production gate (the checker
+    gate replaces it, and the band of ln F is half of the feature pass).  The budgeted threshold
+    flags a fixed fraction of cells: the largest one that the measured cost of the guarded path
+    (its time with no cell flagged, plus the plain operator's time per flagged cell) keeps at
+    SUR_TARGET times the plain operator, and fixed fractions beside it.  Every delivered band is
+    compared cell by cell with the plain FP32 band (all cells) and the FP64 band (first 1024 cells),
+    the grid Q with the plain Q, beside the band's truncation floor.  The other policies return the
+    band only; the unaudited one judges no cell and is an upper bound of the speed, not a guarded
+    result."""
     import torch
 
     import paper_1704_07369_gb300 as ef
@@ -627,6 +636,7 @@ def surrogate_leg(args, device):
     out = {"workload": "3D BKW family (t0~U[0.5,10], rho~U[0.5,2], theta~U[0.5,2], |u|<=1), N=32, L=8, R=32, "
                        "FP32 plain operator vs bf16 MLP surrogate with gates, audit and fallback",
            "cells": SUR_CELLS, "train_cells": SUR_TRAIN, "epochs": args.sur_epochs, "batch": SUR_BATCH,
+           "network": "928 -> %d x %d -> 926, ReLU, bf16 weights" % (SUR_HIDDEN, SUR_LAYERS - 1),
            "lr": SUR_LR, "lr_final": SUR_LR1, "tol": SUR_TOL, "inputs": "926 band floats + theta + relative entropy",
            "audit_fraction": SUR_AUDIT, "metric": "band rel-L2 per cell, modes |k|<=6", "kernels": {}}
     F = torch.empty(SUR_CELLS, SUR_N, SUR_N, SUR_N, device=device)
@@ -637,7 +647,7 @@ def surrogate_leg(args, device):
         t0 = time.perf_counter()
         fF, fQ, fM = S.features_of_family(plan, SUR_TRAIN, seed=1000)
         data_s = time.perf_counter() - t0
-        tr = S.Trainer(plan, batch=SUR_BATCH, max_infer_batch=SUR_CELLS, seed=0)
+        tr = S.Trainer(plan, nhidden=SUR_HIDDEN, nlayers=SUR_LAYERS, batch=SUR_BATCH, max_infer_batch=SUR_CELLS, seed=0)
         t0 = time.perf_counter()
         hist = tr.fit(fF, fQ, fM, epochs=args.sur_epochs, lr0=SUR_LR, lr1=SUR_LR1, warmup=0.05)
         torch.cuda.synchronize()
@@ -648,10 +658,8 @@ def surrogate_leg(args, device):
         train_c_s = time.perf_counter() - t0
         del fF, fQ, fM
         tr._train_set = None
-        # checker threshold from a held-out calibration batch (seeds disjoint from training and test)
-        inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 8_000_000, device=device, out=F)
-        thr, cal_flagged, cal_miss, _ = tr.calibrate(F, SUR_CELLS, SUR_TOL, margin=0.8)
-        thr_b, cal_flagged_b, _, cal_left_b = tr.calibrate(F, SUR_CELLS, SUR_TOL, budget=SUR_BUDGET)
+        # the checked policies run without the entropy-production gate (calibration included)
+        tr.sur.set_entropy_gate(False)
         inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 9_000_000, device=device, out=F)
         # references: plain FP32 band of every cell, FP64 band of the first 1024
         plan.collide(F, Q, ncells=SUR_CELLS)
@@ -679,23 +687,38 @@ def surrogate_leg(args, device):
 
         reps = max(3, min(args.steps, 10))
         plain_ms = timed(lambda i: plan.collide(F, Q, ncells=SUR_CELLS), reps)
+        q = torch.zeros(SUR_CELLS, ef.EF_FEATURE_STRIDE, device=device)
+        flags = torch.zeros(SUR_CELLS, dtype=torch.int32, device=device)
+        Qg = torch.empty_like(F)
+        # the guarded path's cost: its time with no cell flagged, and the plain operator's per cell;
+        # the budget that keeps it at SUR_TARGET times the plain operator
+        tr.sur.set_checker(tr.checker, 3.0e38)
+        noflag_ms = timed(lambda i: tr.sur.infer_ex(F, q, flags, SUR_CELLS, Q=Qg, audit_fraction=0.0, seed=i, tol=SUR_TOL), reps)
+        budget_t = max(0.0, (plain_ms / SUR_TARGET - noflag_ms) / plain_ms)
+        # checker thresholds from a held-out calibration batch (seeds disjoint from training and test)
+        inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 8_000_000, device=device, out=F)
+        thr, cal_flagged, cal_miss, _ = tr.calibrate(F, SUR_CELLS, SUR_TOL, margin=0.8)
+        budgets = [("checked_budget_to_grid", budget_t)] + [("checked_budget%g_to_grid" % b, b) for b in SUR_BUDGETS]
+        cal_b = {}
+        for pname, b in budgets:
+            thr_b, fl_b, _, left_b = tr.calibrate(F, SUR_CELLS, SUR_TOL, budget=max(b, 1.0 / SUR_CELLS))
+            cal_b[pname] = {"budget": b, "threshold": thr_b, "flagged_fraction": fl_b, "misses_left_unflagged": left_b}
+        inputs.bkw_family_torch(SUR_N, L_BOX, SUR_CELLS, 9_000_000, device=device, out=F)
         res = {"plain_ms": plain_ms, "plain_cells_per_s": SUR_CELLS / plain_ms * 1e3,
                "train": {"data_s": data_s, "train_s": train_s, "final_loss": hist[-1],
                          "checker_train_s": train_c_s, "checker_final_loss": hist_c[-1]},
+               "guarded_cost": {"no_cell_flagged_ms": noflag_ms, "plain_ms_per_cell": plain_ms / SUR_CELLS,
+                                "target_speedup": SUR_TARGET, "budget_for_target": budget_t},
                "checker_calibration": {"cells": SUR_CELLS, "misses_in_calibration_set": cal_miss,
                                        "catch_all": {"threshold": thr, "flagged_fraction": cal_flagged, "margin": 0.8},
-                                       "budget": {"threshold": thr_b, "flagged_fraction": cal_flagged_b,
-                                                  "misses_left_unflagged": cal_left_b}},
+                                       "budgets": cal_b},
                "policies": {}}
-        q = torch.zeros(SUR_CELLS, ef.EF_FEATURE_STRIDE, device=device)
-        flags = torch.zeros(SUR_CELLS, dtype=torch.int32, device=device)
         # the guarded path end to end: checker gate, Q on the grid (band reconstruction where the
         # prediction is delivered, the plain operator's full Q where it is not), no audit; with the
-        # threshold that flagged every calibration miss, and with the one that flags a fixed budget
-        Qg = torch.empty_like(F)
+        # threshold that flagged every calibration miss, and with the ones that flag fixed budgets
         proj = torch.empty(n64, SUR_N, SUR_N, SUR_N, device=device)
         ef.ef_features_inverse(plan.handle, ref[:n64], proj, n64)
-        for pname, th in (("checked_catch_all_to_grid", thr), ("checked_budget_to_grid", thr_b)):
+        for pname, th in [("checked_catch_all_to_grid", thr)] + [(k, v["threshold"]) for k, v in cal_b.items()]:
             tr.sur.set_checker(tr.checker, th)
             ms = timed(lambda i: tr.sur.infer_ex(F, q, flags, SUR_CELLS, Q=Qg, audit_fraction=0.0, seed=i, tol=SUR_TOL), reps)
             f = flags.cpu().numpy()
@@ -720,6 +743,7 @@ def surrogate_leg(args, device):
         del proj
         del Qg
         tr.sur.set_checker(None, 1.0)
+        tr.sur.set_entropy_gate(True)
         # unguarded upper bound (nothing judges the cells) and the audit policies, band output only
         for pname, audit, max_miss in (("no_audit_unjudged", 0.0, 0.0), ("audit_strict", SUR_AUDIT, 0.0),
                                        ("audit_tolerant", SUR_AUDIT, 0.05)):

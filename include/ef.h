@@ -261,6 +261,11 @@ ef_status ef_surrogate_stats(ef_surrogate_t sur, float *host, int set);
  * to later ef_surrogate_infer calls; not to be changed while one is in flight on a stream. */
 ef_status ef_surrogate_set_policy(ef_surrogate_t sur, float max_miss_fraction, float xmax);
 
+/* Switches the entropy-production gate (flags bit 1 for a positive band sum Q ln F) on (default)
+ * or off.  With it off the inference skips the band of ln F, about half of its feature pass; the
+ * other gates stay.  Applies to later ef_surrogate_infer calls. */
+ef_status ef_surrogate_set_entropy_gate(ef_surrogate_t sur, int on);
+
 /* Band of Q^sigma for ncells cells (multiple of 64, <= max_batch): qfeat (EF_FEATURE_STRIDE per
  * cell, ef_features layout) receives the prediction, or the plain operator's band where the
  * prediction is not trusted.  flags (int per cell): 1 = a gate failed (non-finite, input outside

@@ -40,7 +40,8 @@ SYMBOLS = ("ef_plan_create", "ef_plan_create_ex", "ef_plan_create_batched", "ef_
            "ef_features", "ef_mlp_create", "ef_mlp_destroy", "ef_mlp_info", "ef_mlp_status", "ef_mlp_params",
            "ef_mlp_forward", "ef_mlp_grad", "ef_mlp_train_step",
            "ef_surrogate_create", "ef_surrogate_destroy", "ef_surrogate_fit_stats", "ef_surrogate_normalize",
-           "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_infer", "ef_surrogate_set_checker",
+           "ef_surrogate_stats", "ef_surrogate_set_policy", "ef_surrogate_set_entropy_gate", "ef_surrogate_infer",
+           "ef_surrogate_set_checker",
            "ef_surrogate_infer_ex", "ef_features_inverse",
            "ef_stream_plan_create", "ef_stream_plan_destroy", "ef_stream_plan_info", "ef_stream_euler_step",
            "ef_stream_plan_status", "ef_transport_step", "ef_classical_create", "ef_classical_collide",
@@ -106,6 +107,7 @@ def lib():
         L.ef_surrogate_normalize.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         L.ef_surrogate_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.ef_surrogate_set_policy.argtypes = [vp, ctypes.c_float, ctypes.c_float]
+        L.ef_surrogate_set_entropy_gate.argtypes = [vp, ctypes.c_int]
         L.ef_surrogate_infer.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
         L.ef_surrogate_set_checker.argtypes = [vp, vp, ctypes.c_float]
         L.ef_surrogate_infer_ex.argtypes = [vp, vp, vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_uint64, ctypes.c_float, vp]
@@ -296,6 +298,10 @@ class Surrogate:
 
     def set_policy(self, max_miss_fraction=0.0, xmax=8.0):
         _check(lib().ef_surrogate_set_policy(self.handle, float(max_miss_fraction), float(xmax)))
+
+    def set_entropy_gate(self, on):
+        """The band entropy-production gate on or off (off skips the band of ln F)."""
+        _check(lib().ef_surrogate_set_entropy_gate(self.handle, int(bool(on))))
 
     def infer(self, F, qfeat, flags, ncells, audit_fraction=0.05, seed=0, tol=1e-3, stream=None):
         _check(lib().ef_surrogate_infer(self.handle, _ptr(F), _ptr(qfeat), _ptr(flags), int(ncells),

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "ef.h"
+#include "ef_fft.cuh"
 #include "ef_launch.h"
 
 namespace {
@@ -244,7 +245,7 @@ __global__ void decode_gate_kernel(const float *Ypred, int ldy, const float *fea
         if (fabsf(Xn[i * kStride + 2 * jm]) > xmax || fabsf(Xn[i * kStride + 2 * jm + 1]) > xmax) bad = true;
         qfeat[i * kStride + 2 * jm] = qr;
         qfeat[i * kStride + 2 * jm + 1] = qi;
-        prod += qr * featL[i * kStride + 2 * jm] + qi * featL[i * kStride + 2 * jm + 1];   // Re(q conj(l))
+        if (featL) prod += qr * featL[i * kStride + 2 * jm] + qi * featL[i * kStride + 2 * jm + 1];   // Re(q conj(l))
     }
     if (lane == 0)
         for (int j = nf; j < nin; ++j)
@@ -323,120 +324,225 @@ __global__ void relist_kernel(const unsigned *audit, float max_miss, int64_t n, 
 }
 
 // Q on the grid from the band: Q[i] = sum over the band (both halves) of q_k exp(2 pi i k.i / N), the
-// inverse of ef_features' transform on the band (index-origin convention), evaluated separably:
-//   S1[k0][k1][x] = sum_k2 c_k exp(2 pi i k2 x / N),  then per plane z
-//   T[k1][x] = sum_k0 S1[k0][k1][x] exp(2 pi i k0 z / N),  Q[z][y][x] = Re sum_k1 T[k1][x] exp(2 pi i k1 y / N).
-// One CTA of 256 threads per cell, 3D; cells whose flags carry 8 (plain operator used) take the
-// plain operator's full Q instead (the collide output of the fallback launch).
-constexpr int kBandK = EF_FEATURE_K, kBandW = 2 * EF_FEATURE_K + 1;
+// inverse of ef_features' transform on the band (index-origin convention).  Q is real and
+// q_{-k} = conj(q_k), so only the half k2 >= 0 of the band enters (the k2 = 0 plane with both of its
+// halves), evaluated separably:
+//   A[z][k1][k2] = sum_k0 c[k0][k1][k2] exp(2 pi i k0 z / N)          (one shared-memory pass)
+//   B_k2(z, y)   = sum_k1 A[z][k1][k2] exp(2 pi i k1 y / N)           (per row, in registers)
+//   Q[z][y][x]   = Re B_0 + 2 Re sum_{k2 >= 1} B_k2 exp(2 pi i k2 x / N)  (compile-time twiddles)
+// Rows y and N - y share their sums (with P = sum_k1 A cos, R = sum_k1 A sin: B(y) = P + iR,
+// B(N - y) = P - iR), and so do the columns x and N - x of a row; one thread takes such a pair of
+// rows (y = 0 with y = N/2).  The rows of a chunk of planes are staged in shared memory and written
+// out with coalesced 16-byte stores.  One CTA of 256 threads per cell at a time (persistent over
+// cells).  Cells whose flags carry 8 (plain operator used) are skipped: the fallback launch wrote
+// their Q on the grid itself.  (A three-pass FFT of the zero-padded band has a third of the
+// instructions and measured slower: the pass is bound by latency, not by arithmetic.)
+constexpr int kBandK = EF_FEATURE_K, kBandW = 2 * EF_FEATURE_K + 1, kBandH = EF_FEATURE_K + 1;
 
+// output planes staged per pass: the largest divisor of N up to 512 / N (about 256 row pairs)
 template <int N>
-constexpr size_t band_grid_smem() { return (size_t)(kBandW * kBandW * kBandW + kBandW * kBandW * N + kBandW * N + N) * 8; }
+__host__ __device__ constexpr int band_pz()
+{
+    int p = 512 / N < N ? 512 / N : N;
+    while (N % p) --p;
+    return p;
+}
+template <int N>
+constexpr size_t band_grid_smem()
+{
+    return (size_t)band_pz<N>() * N * N * 4 + (size_t)(kBandW * kBandW * kBandH + N * kBandW * kBandH + N) * 8;
+}
+// position of 16-byte piece j of staged row y: rows of one warp's stores (consecutive y) start on
+// different banks (XOR for a power-of-two count of pieces, else a rotation)
+template <int N>
+__device__ __forceinline__ int band_swz(int j, int y)
+{
+    constexpr int NC = N / 4;
+    if constexpr ((NC & (NC - 1)) == 0) return j ^ (y & (NC < 8 ? NC - 1 : 7));
+    else return (j + y) % NC;
+}
+
+// one output row from its B_k2, k2 = 0 .. K: out[x] = Re B_0 + 2 Re sum_k2 B_k2 exp(2 pi i k2 x / N),
+// into staged row y (float4 pieces, swizzled)
+template <int N>
+__device__ __forceinline__ void band_row_out(const float2 (&B)[kBandH], float4 *rowbuf, int y)
+{
+    float out[N];
+    float c0 = 0.f, ch = 0.f;                               // x = 0 and x = N/2
+#pragma unroll
+    for (int k2 = 1; k2 < kBandH; ++k2) {
+        c0 += B[k2].x;
+        ch += (k2 & 1) ? -B[k2].x : B[k2].x;
+    }
+    out[0] = B[0].x + 2.f * c0;
+    out[N / 2] = B[0].x + 2.f * ch;
+#pragma unroll
+    for (int x = 1; x < N / 2; ++x) {
+        float cs = 0.f, sn = 0.f;
+#pragma unroll
+        for (int k2 = 1; k2 < kBandH; ++k2) {
+            const ef::C2<float> t = ef::tw_value<N, float>((k2 * x) % N);   // (cos, -sin) of 2 pi k2 x / N
+            cs += B[k2].x * t.x;
+            sn += B[k2].y * t.y;                                             // -b sin
+        }
+        out[x] = B[0].x + 2.f * (cs + sn);                  // Re(B w) = a cos - b sin
+        out[N - x] = B[0].x + 2.f * (cs - sn);
+    }
+#pragma unroll
+    for (int x = 0; x < N; x += 4) rowbuf[band_swz<N>(x / 4, y)] = make_float4(out[x], out[x + 1], out[x + 2], out[x + 3]);
+}
 
 template <int N>
 __global__ void __launch_bounds__(256) band_to_grid_kernel(const float *qfeat, const int *kvec, int nmodes, const int *flags,
-                                                           const float *Qplain, float *Q, int64_t n)
+                                                           float *Q, int64_t n)
 {
-    extern __shared__ float2 bsm[];
-    auto cf = reinterpret_cast<float2 (*)[kBandW][kBandW]>(bsm);                                    // [k0][k1][k2]
-    auto S1 = reinterpret_cast<float2 (*)[kBandW][N]>(bsm + kBandW * kBandW * kBandW);               // [k0][k1][x]
-    auto Tz = reinterpret_cast<float2 (*)[N]>(bsm + kBandW * kBandW * kBandW + kBandW * kBandW * N);   // [k1][x]
-    float2 *ex = bsm + kBandW * kBandW * kBandW + kBandW * kBandW * N + kBandW * N;                   // exp(2 pi i m / N)
+    constexpr int PZ = band_pz<N>(), NC = N / 4;
+    extern __shared__ __align__(16) float4 bsm4[];
+    float4 *ob = bsm4;                                                                             // [PZ][N rows][N/4]
+    float2 *bsm = reinterpret_cast<float2 *>(bsm4 + PZ * N * NC);
+    auto cf = reinterpret_cast<float2 (*)[kBandW][kBandH]>(bsm);                                   // [k0][k1][k2 >= 0]
+    auto A = reinterpret_cast<float2 (*)[kBandW][kBandH]>(bsm + kBandW * kBandW * kBandH);          // [z][k1][k2]
+    float2 *ex = bsm + kBandW * kBandW * kBandH + N * kBandW * kBandH;                             // exp(2 pi i m / N)
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int m = tid; m < N; m += nt) {
-        float s, c;
-        sincospif(2.0f * (float)m / (float)N, &s, &c);
-        ex[m] = make_float2(c, s);
+        float sn, cs;
+        sincospif(2.0f * (float)m / (float)N, &sn, &cs);
+        ex[m] = make_float2(cs, sn);
     }
     constexpr int64_t CELL = (int64_t)N * N * N;
+    constexpr int NA = N * kBandW * kBandH;
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-        float *Qi = Q + i * CELL;
-        if (flags && (flags[i] & 8)) {                     // the plain operator's full Q
-            const float4 *src = reinterpret_cast<const float4 *>(Qplain + i * CELL);
-            float4 *dst = reinterpret_cast<float4 *>(Qi);
-            for (int64_t t = tid; t < CELL / 4; t += nt) dst[t] = src[t];
-            continue;
-        }
-        __syncthreads();
-        for (int t = tid; t < kBandW * kBandW * kBandW; t += nt) (&cf[0][0][0])[t] = make_float2(0.f, 0.f);
+        if (flags && (flags[i] & 8)) continue;             // uniform over the CTA
+        __syncthreads();                                    // the previous cell's A and cf reads are done
+        for (int t = tid; t < kBandW * kBandW * kBandH; t += nt) (&cf[0][0][0])[t] = make_float2(0.f, 0.f);
         __syncthreads();
         for (int j = tid; j < nmodes; j += nt) {
             const int k0 = kvec[3 * j], k1 = kvec[3 * j + 1], k2 = kvec[3 * j + 2];
             const float re = qfeat[i * kStride + 2 * j], im = qfeat[i * kStride + 2 * j + 1];
-            cf[k0 + kBandK][k1 + kBandK][k2 + kBandK] = make_float2(re, im);
-            if (k0 || k1 || k2) cf[kBandK - k0][kBandK - k1][kBandK - k2] = make_float2(re, -im);
+            if (k2 > 0) {
+                cf[k0 + kBandK][k1 + kBandK][k2] = make_float2(re, im);
+            } else if (k2 == 0) {                           // both halves of the k2 = 0 plane
+                cf[k0 + kBandK][k1 + kBandK][0] = make_float2(re, im);
+                if (k0 || k1) cf[kBandK - k0][kBandK - k1][0] = make_float2(re, -im);
+            } else {                                        // a stored mode of the other half: its conjugate
+                cf[kBandK - k0][kBandK - k1][-k2] = make_float2(re, -im);
+            }
         }
         __syncthreads();
-        for (int t = tid; t < kBandW * kBandW * N; t += nt) {
-            const int x = t % N, k1 = (t / N) % kBandW, k0 = t / (N * kBandW);
+        for (int o = tid; o < NA; o += nt) {
+            const int z = o / (kBandW * kBandH), r = o % (kBandW * kBandH);
+            const int k1 = r / kBandH, k2 = r % kBandH;
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k2 = 0; k2 < kBandW; ++k2) {
+            for (int k0 = 0; k0 < kBandW; ++k0) {
                 const float2 c = cf[k0][k1][k2];
-                const float2 e = ex[(((k2 - kBandK) * x) % N + N) % N];
+                const float2 e = ex[(((k0 - kBandK) * z) % N + N) % N];
                 acc.x += c.x * e.x - c.y * e.y;
                 acc.y += c.x * e.y + c.y * e.x;
             }
-            S1[k0][k1][x] = acc;
+            A[z][k1][k2] = acc;
         }
-        for (int z = 0; z < N; ++z) {
-            __syncthreads();
-            for (int t = tid; t < kBandW * N; t += nt) {
-                const int x = t % N, k1 = t / N;
-                float2 acc = make_float2(0.f, 0.f);
+        __syncthreads();
+        float4 *Qi = reinterpret_cast<float4 *>(Q + i * CELL);
+        for (int z0 = 0; z0 < N; z0 += PZ) {
+            for (int item = tid; item < PZ * (N / 2); item += nt) {
+                const int zl = item / (N / 2), p = item % (N / 2), z = z0 + zl;
+                float4 *pl = ob + zl * N * NC;
+                float2 P[kBandH], R[kBandH];
 #pragma unroll
-                for (int k0 = 0; k0 < kBandW; ++k0) {
-                    const float2 c = S1[k0][k1][x];
-                    const float2 e = ex[(((k0 - kBandK) * z) % N + N) % N];
-                    acc.x += c.x * e.x - c.y * e.y;
-                    acc.y += c.x * e.y + c.y * e.x;
+                for (int k2 = 0; k2 < kBandH; ++k2) {
+                    P[k2] = A[z][kBandK][k2];
+                    R[k2] = make_float2(0.f, 0.f);
                 }
-                Tz[k1][x] = acc;
+                if (p == 0) {
+                    // rows y = 0 (every exp = 1) and y = N/2 (exp = (-1)^k1): R = 0 for both
+                    float2 Ph[kBandH];
+#pragma unroll
+                    for (int k2 = 0; k2 < kBandH; ++k2) Ph[k2] = P[k2];
+#pragma unroll
+                    for (int m = 1; m <= kBandK; ++m) {
+#pragma unroll
+                        for (int k2 = 0; k2 < kBandH; ++k2) {
+                            const float2 u = A[z][kBandK + m][k2], v = A[z][kBandK - m][k2];
+                            const float sx = u.x + v.x, sy = u.y + v.y;
+                            P[k2].x += sx;
+                            P[k2].y += sy;
+                            Ph[k2].x += (m & 1) ? -sx : sx;
+                            Ph[k2].y += (m & 1) ? -sy : sy;
+                        }
+                    }
+                    band_row_out<N>(P, pl, 0);
+                    band_row_out<N>(Ph, pl + (N / 2) * NC, N / 2);
+                } else {
+                    const float2 w = ex[p];
+                    float2 e = w;                           // exp(2 pi i m p / N), m = 1 .. K
+#pragma unroll
+                    for (int m = 1; m <= kBandK; ++m) {
+#pragma unroll
+                        for (int k2 = 0; k2 < kBandH; ++k2) {
+                            const float2 u = A[z][kBandK + m][k2], v = A[z][kBandK - m][k2];
+                            P[k2].x += (u.x + v.x) * e.x;
+                            P[k2].y += (u.y + v.y) * e.x;
+                            R[k2].x += (u.x - v.x) * e.y;
+                            R[k2].y += (u.y - v.y) * e.y;
+                        }
+                        e = make_float2(e.x * w.x - e.y * w.y, e.x * w.y + e.y * w.x);
+                    }
+                    float2 B[kBandH];
+#pragma unroll
+                    for (int k2 = 0; k2 < kBandH; ++k2) B[k2] = make_float2(P[k2].x - R[k2].y, P[k2].y + R[k2].x);   // P + iR
+                    band_row_out<N>(B, pl + p * NC, p);
+#pragma unroll
+                    for (int k2 = 0; k2 < kBandH; ++k2) B[k2] = make_float2(P[k2].x + R[k2].y, P[k2].y - R[k2].x);   // P - iR
+                    band_row_out<N>(B, pl + (N - p) * NC, N - p);
+                }
             }
             __syncthreads();
-            for (int t = tid; t < N * N; t += nt) {
-                const int x = t % N, y = t / N;
-                float acc = 0.f;
-#pragma unroll
-                for (int k1 = 0; k1 < kBandW; ++k1) {
-                    const float2 c = Tz[k1][x];
-                    const float2 e = ex[(((k1 - kBandK) * y) % N + N) % N];
-                    acc += c.x * e.x - c.y * e.y;
-                }
-                Qi[(int64_t)z * N * N + t] = acc;
+            // the chunk's planes, contiguous in Q: coalesced 16-byte stores
+            for (int c = tid; c < PZ * N * NC; c += nt) {
+                const int row = c / NC, j = c % NC;
+                Qi[(int64_t)z0 * N * NC + c] = ob[row * NC + band_swz<N>(j, row % N)];
             }
+            __syncthreads();
         }
     }
 }
 
 template <int N>
-cudaError_t band_to_grid_n(const float *qfeat, const int *kvec, int nmodes, const int *flags, const float *Qplain, float *Q,
-                           int64_t n, cudaStream_t st)
+cudaError_t band_to_grid_n(const float *qfeat, const int *kvec, int nmodes, const int *flags, float *Q, int64_t n,
+                           cudaStream_t st)
 {
-    static bool attr_set[64] = {};
+    // per device: the shared-memory attribute and the persistent grid (resident CTAs on every SM)
+    static int grid_of[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !attr_set[dev]) {
+    int full = dev < 64 ? grid_of[dev] : 0;
+    if (full == 0) {
         cudaError_t e = cudaFuncSetAttribute(band_to_grid_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)band_grid_smem<N>());
+        int per_sm = 0, sms = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_to_grid_kernel<N>, 256, band_grid_smem<N>());
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
+        full = std::max(1, per_sm) * sms;
+        if (dev < 64) grid_of[dev] = full;
     }
-    const int grid = (int)std::min<int64_t>(n, 152 * 4);
-    band_to_grid_kernel<N><<<grid, 256, band_grid_smem<N>(), st>>>(qfeat, kvec, nmodes, flags, Qplain, Q, n);
+    const int grid = (int)std::min<int64_t>(n, full);
+    band_to_grid_kernel<N><<<grid, 256, band_grid_smem<N>(), st>>>(qfeat, kvec, nmodes, flags, Q, n);
     return cudaGetLastError();
 }
 
-cudaError_t band_to_grid(int N, const float *qfeat, const int *kvec, int nmodes, const int *flags, const float *Qplain,
-                         float *Q, int64_t n, cudaStream_t st)
+cudaError_t band_to_grid(int N, const float *qfeat, const int *kvec, int nmodes, const int *flags, float *Q, int64_t n,
+                         cudaStream_t st)
 {
     switch (N) {
-    case 16: return band_to_grid_n<16>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
-    case 24: return band_to_grid_n<24>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
-    case 32: return band_to_grid_n<32>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
-    case 40: return band_to_grid_n<40>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
-    case 48: return band_to_grid_n<48>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
-    case 64: return band_to_grid_n<64>(qfeat, kvec, nmodes, flags, Qplain, Q, n, st);
+    case 16: return band_to_grid_n<16>(qfeat, kvec, nmodes, flags, Q, n, st);
+    case 24: return band_to_grid_n<24>(qfeat, kvec, nmodes, flags, Q, n, st);
+    case 32: return band_to_grid_n<32>(qfeat, kvec, nmodes, flags, Q, n, st);
+    case 40: return band_to_grid_n<40>(qfeat, kvec, nmodes, flags, Q, n, st);
+    case 48: return band_to_grid_n<48>(qfeat, kvec, nmodes, flags, Q, n, st);
+    case 64: return band_to_grid_n<64>(qfeat, kvec, nmodes, flags, Q, n, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -463,6 +569,7 @@ struct ef_surrogate_s {
     ef_mlp_t checker = nullptr;           // second network; its disagreement gates cells (nullable)
     float check_tol = 0.f;
     float *Yc = nullptr;                  // checker outputs (max_batch rows)
+    bool entropy_gate = true;             // the band entropy-production gate (needs the band of ln F)
 };
 
 namespace {
@@ -648,6 +755,13 @@ ef_status ef_surrogate_set_policy(ef_surrogate_t s, float max_miss_fraction, flo
     return EF_OK;
 }
 
+ef_status ef_surrogate_set_entropy_gate(ef_surrogate_t s, int on)
+{
+    if (!s) return sfail(EF_ERR_INVALID_ARG, "null surrogate");
+    s->entropy_gate = on != 0;
+    return EF_OK;
+}
+
 ef_status ef_features_inverse(ef_plan_t plan, const float *feat, float *Q_dev, int64_t ncells, ef_stream_t stream)
 {
     ef::PlanView v;
@@ -656,7 +770,7 @@ ef_status ef_features_inverse(ef_plan_t plan, const float *feat, float *Q_dev, i
     if (ncells < 0) return sfail(EF_ERR_INVALID_ARG, "ncells < 0");
     if (ncells == 0) return EF_OK;
     if (!feat || !Q_dev || (uintptr_t)Q_dev % 16) return sfail(EF_ERR_INVALID_ARG, "null feat or Q, or Q not 16-byte aligned");
-    const cudaError_t e = band_to_grid(v.N, feat, v.modes, v.nfeat, nullptr, nullptr, Q_dev, ncells, (cudaStream_t)stream);
+    const cudaError_t e = band_to_grid(v.N, feat, v.modes, v.nfeat, nullptr, Q_dev, ncells, (cudaStream_t)stream);
     return e == cudaSuccess ? EF_OK : scuda(e, "ef_features_inverse");
 }
 
@@ -699,12 +813,12 @@ ef_status ef_surrogate_infer_ex(ef_surrogate_t s, const void *F, float *qfeat, i
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t cell = v.d == 3 ? (int64_t)v.N * v.N * v.N : (int64_t)v.N * v.N;
     if ((uintptr_t)F % 16) return sfail(EF_ERR_INVALID_ARG, "F must be 16-byte aligned");
-    // one pass over the cells: band modes of F and of ln F, and the moments of F
+    // one pass over the cells: band modes of F (and of ln F for the entropy gate), and the moments of F
     ef::FeatArgs fa{};
     fa.F = F;
     fa.ncells = ncells;
     fa.feat = s->featF;
-    fa.featL = s->featL;
+    fa.featL = s->entropy_gate ? s->featL : nullptr;
     fa.fstride = kStride;
     fa.mom = s->mom;
     fa.h = 2.0 * v.L / v.N;
@@ -725,15 +839,16 @@ ef_status ef_surrogate_infer_ex(ef_surrogate_t s, const void *F, float *qfeat, i
     if (e == cudaSuccess) e = cudaMemsetAsync(s->audit, 0, 8, st);
     if (e != cudaSuccess) return scuda(e, "surrogate reset");
     decode_gate_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(
-        s->Y, s->noutp, s->featF, s->featL, s->mom, s->kvec, s->pi_over_L, ncells, s->nf, s->nin, s->idx0, s->nu, s->td, s->X,
+        s->Y, s->noutp, s->featF, s->entropy_gate ? s->featL : nullptr, s->mom, s->kvec, s->pi_over_L, ncells, s->nf, s->nin, s->idx0, s->nu, s->td, s->X,
         s->xmax, (float)cell,
         audit_fraction, seed, qfeat, flags, s->count, s->list_off, s->list_id, cell, s->audit,
         s->checker ? s->Yc : nullptr, s->check_tol, score);
     for (int round = 0; round < 2; ++round) {
-        // plain operator on the listed cells (count read on the device), then their band
+        // plain operator on the listed cells (count read on the device), then their band; with Q on
+        // the grid requested the plain operator writes the listed cells' Q there directly
         ef::CollideArgs a{};
         a.F = F;
-        a.Q = s->Qs;
+        a.Q = Q ? static_cast<void *>(Q) : s->Qs;
         a.cell_off = s->list_off;
         a.cell_id = s->list_id;
         a.ncells = ncells;
@@ -753,7 +868,7 @@ ef_status ef_surrogate_infer_ex(ef_surrogate_t s, const void *F, float *qfeat, i
         e = ef::collide_launch(v.prec, v.d, v.N, a, grid, v.tpb, v.smem, v.occ, st);
         if (e != cudaSuccess) return scuda(e, "fallback collide");
         ef::FeatArgs qa{};
-        qa.F = s->Qs;
+        qa.F = a.Q;
         qa.cell_off = s->list_off;
         qa.cell_id = s->list_id;
         qa.ncells = ncells;
@@ -775,7 +890,7 @@ ef_status ef_surrogate_infer_ex(ef_surrogate_t s, const void *F, float *qfeat, i
         }
     }
     if (Q) {
-        e = band_to_grid(v.N, qfeat, s->kvec, s->nf / 2, flags, static_cast<const float *>(s->Qs), Q, ncells, st);
+        e = band_to_grid(v.N, qfeat, s->kvec, s->nf / 2, flags, Q, ncells, st);
         if (e != cudaSuccess) return scuda(e, "band to grid");
     }
     e = cudaGetLastError();

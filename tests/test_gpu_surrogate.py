@@ -332,6 +332,41 @@ def test_surrogate_audit_and_fallback_paths():
         sur.set_policy(max_miss_fraction=1.5)
 
 
+def test_entropy_gate_switch():
+    """With the entropy-production gate off the inference skips the band of ln F: cells the gate
+    did not flag keep the same prediction bit for bit, and no cell is flagged for a positive band
+    production (an untrained network on a wide input envelope trips that gate on some cells)."""
+    N, L, n = 16, 8.0, 256
+    plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F32)
+    net = ef.MLP(926, 64, 3, 926, n, seed=4)
+    sur = ef.Surrogate(plan, net, n)
+    F = inputs.bkw_family_torch(N, L, n, seed=79)
+    Q = torch.empty_like(F)
+    plan.collide(F, Q, ncells=n)
+    ref = torch.zeros(n, ef.EF_FEATURE_STRIDE, device="cuda")
+    ef.ef_features(plan.handle, Q, ref, n)
+    fF = torch.zeros_like(ref)
+    ef.ef_features(plan.handle, F, fF, n)
+    mom = torch.zeros(n, ef.EF_DIAG_STRIDE, dtype=torch.float64, device="cuda")
+    ef.ef_moments_entropy(plan.handle, F, None, mom, n)
+    Xt, Yt = torch.zeros_like(ref), torch.zeros_like(ref)
+    sur.fit_stats(fF, ref, mom, Xt, Yt, n)
+    sur.set_policy(max_miss_fraction=0.0, xmax=1e30)
+    q1, q0 = torch.zeros_like(ref), torch.zeros_like(ref)
+    f1 = torch.zeros(n, dtype=torch.int32, device="cuda")
+    f0 = torch.zeros_like(f1)
+    sur.infer(F, q1, f1, n, audit_fraction=0.0, seed=1, tol=1e-3)
+    sur.set_entropy_gate(False)
+    sur.infer(F, q0, f0, n, audit_fraction=0.0, seed=1, tol=1e-3)
+    sur.set_entropy_gate(True)
+    torch.cuda.synchronize()
+    g1, g0 = f1.cpu().numpy(), f0.cpu().numpy()
+    assert (g1 & 1).sum() > 0, "the untrained network should trip the entropy gate somewhere"
+    assert (g0 == 0).all()
+    keep = torch.tensor(g1 == 0, device="cuda")
+    assert torch.equal(q0[keep], q1[keep])
+
+
 def test_features_inverse_projects_on_the_band():
     """ef_features_inverse returns a band-limited field exactly (features -> grid -> features is the
     identity on the band) and maps a general cell to its truncation to |k| <= 6, against the
