@@ -771,8 +771,9 @@ def surrogate_leg(args, device):
     return out
 
 
-COLLIDE_SOURCES = ("ef_collide_impl.cuh", "ef_collide_rg.cuh", "ef_fft.cuh", "ef_internal.h", "ef_collide_variant.inc",
-                   "ef_collide_f32_3d.cu", "ef_collide_rg_f32.cu", "ef_cluster_launch.h")
+COLLIDE_SOURCES = ("ef_collide_impl.cuh", "ef_collide_rg.cuh", "ef_collide_tm.cuh", "ef_fft.cuh", "ef_internal.h",
+                   "ef_collide_variant.inc", "ef_collide_f32_3d.cu", "ef_collide_rg_f32.cu", "ef_collide_tm_f32.cu",
+                   "ef_cluster_launch.h")
 
 
 def ef_kernel_hash():

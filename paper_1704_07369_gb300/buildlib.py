@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC] + ARCH
-UNITS = ["ef_plan.cpp", "ef_moments.cu", "ef_noalloc.cu", "ef_mlp.cu", "ef_surrogate.cu", "ef_collide_f32_3d.cu", "ef_collide_rg_f32.cu", "ef_collide_f64_3d.cu",
+UNITS = ["ef_plan.cpp", "ef_moments.cu", "ef_noalloc.cu", "ef_mlp.cu", "ef_surrogate.cu", "ef_collide_f32_3d.cu", "ef_collide_rg_f32.cu", "ef_collide_tm_f32.cu", "ef_collide_f64_3d.cu",
          "ef_collide_f32_2d.cu", "ef_collide_f64_2d.cu", "ef_features_f32.cu", "ef_features_f64.cu", "ef_step.cu", "ef_stream.cpp",
          "ef_transport.cu", "ef_classical.cu", "ef_kernelg.cu", "ef_galerkin.cu"]
 

@@ -98,6 +98,14 @@ __host__ __device__ constexpr size_t rg_smem_bytes(int planes, int npc, bool g_s
            (32 + 1) * kDiag * sizeof(double) + 16 + 32 * sizeof(float);
 }
 
+// lanes of the calling thread's warp that exist: a block whose size is not a multiple of 32 has a
+// partial last warp, and warp-synchronous operations name only these lanes
+__device__ __forceinline__ unsigned warp_lanes(int nt, int tid)
+{
+    const int n = nt - (tid & ~31);
+    return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+}
+
 // in-plane offset of the even pencil of a lane pair: pencil q (even) -> (k_y, k_x) = (q / (N/2), q % (N/2))
 template <int N>
 __device__ __forceinline__ int rg_poff(int q) { return rg_at<N>(q / (N / 2), q % (N / 2)); }
@@ -213,6 +221,7 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
     const int64_t nclusters = gridDim.x / C;
     const int64_t cid = blockIdx.x / C;
     const int lane = tid & 31;
+    const unsigned wmask = warp_lanes(nt, tid);
     const T scale = T(1) / T(CELL);
     const T *Mbase = reinterpret_cast<const T *>(a.mult);
     constexpr int H = N / 2 + 1;
@@ -268,7 +277,7 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
         for (int q0 = tid - lane; q0 < NPC; q0 += nt) {
             const int ql = q0 + lane;
             const bool has = ql < NPC;
-            const unsigned mask = __ballot_sync(0xffffffffu, has);
+            const unsigned mask = __ballot_sync(wmask, has);
             if (has) {
                 const int q = rank * NPC + ql;
                 C2<T> v[N];
@@ -294,7 +303,7 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
             for (int q0 = tid - lane; q0 < nitems; q0 += nt) {
                 const int qi = q0 + lane;
                 const bool has = qi < nitems;
-                const unsigned mask = __ballot_sync(0xffffffffu, has);
+                const unsigned mask = __ballot_sync(wmask, has);
                 if (has) {
                     const int b = qi >= NPC;
                     const int ql = qi - b * NPC;
@@ -445,8 +454,8 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
                 if (bigt && a.out_mode == OUT_EULER) *s_nubig = 1;
 #pragma unroll
                 for (int o2 = 16; o2 > 0; o2 >>= 1) {
-                    const T u = __shfl_xor_sync(0xffffffffu, mxt, o2);
-                    mxt = u > mxt ? u : mxt;
+                    const T u = __shfl_xor_sync(wmask, mxt, o2);
+                    if ((wmask >> (lane ^ o2)) & 1u) mxt = u > mxt ? u : mxt;
                 }
                 if (lane == 0) s_maxnu[tid >> 5] = mxt;
             }
@@ -464,8 +473,8 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
                 double v = dg.sum[k];
 #pragma unroll
                 for (int s = 16; s > 0; s >>= 1) {
-                    const double u = __shfl_xor_sync(0xffffffffu, v, s);
-                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                    const double u = __shfl_xor_sync(wmask, v, s);
+                    if ((wmask >> (lane ^ s)) & 1u) v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
                 }
                 if (lane == 0) part[warp * kDiag + k] = v;
             }

@@ -19,11 +19,18 @@ namespace ef {
     cudaError_t collide_launch_##SUF(int N, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, \
                                      int occ, cudaStream_t s);
 
-// FP32 3D register-accumulator kernel (ef_collide_rg_f32.cu), instantiation v = 1 .. 4 (kernel
-// variant occ = 2 + v): rg_maxthreads_f32 is its launch bound (0: not built for N),
-// rg_rows_per_thread its rows per thread (0: the gain accumulator in shared memory, rows looped).
+// FP32 3D register-accumulator kernels (ef_collide_rg_f32.cu), instantiation v = 1 .. 6 (kernel
+// variant occ = 2 + v; 5, 6: two lanes per line): rg_maxthreads_f32 is its launch bound (0: not
+// built for N), rg_rows_per_thread its rows per thread or team (0: the gain accumulator in shared
+// memory, rows looped).
 int rg_maxthreads_f32(int N, int v);
 int rg_rows_per_thread(int v);
+// lanes per line transform of variant v (2: the team kernel, threads = 2 rows / RPT)
+int rg_team(int v);
+// the team kernel (ef_collide_tm_f32.cu, variants 5 and 6): launch bound (0: not built for N)
+int tm_maxthreads_f32(int N);
+cudaError_t tm_setup_f32(int N, int v, size_t smem, int cluster, int tpb, int *max_clusters);
+cudaError_t tm_launch_f32(int N, int v, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s);
 size_t rg_smem_f32(int N, int planes, int v);
 cudaError_t rg_setup_f32(int N, int v, size_t smem, int cluster, int tpb, int *max_clusters);
 cudaError_t rg_launch_f32(int N, int v, const CollideArgs &a, int grid_clusters, int tpb, size_t smem, cudaStream_t s);

@@ -89,7 +89,7 @@ extern "C" ef_status ef_collide_noalloc(ef_plan_t plan, const void *F_dev, void 
 
     // per cluster: S and G of each CTA in global memory (2 * rows * N values per CTA) and the
     // forward-spectrum workspace; layout [counter][S/G of grid * C CTAs][spectra of grid clusters].
-    // The register-accumulator variants (occ 3, 4) keep both on chip and need only the counter.
+    // The register-accumulator variants (occ >= 3) keep both on chip and need only the counter.
     const bool onchip = v.occ >= 3;
     const int64_t rows = (int64_t)v.planes * (v.d == 3 ? v.N : 1);
     const size_t el = v.prec == EF_PREC_F32 ? 4 : 8;

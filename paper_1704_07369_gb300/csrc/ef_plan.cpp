@@ -356,15 +356,16 @@ std::vector<Shape> candidate_shapes(const Desc &ds, int N, std::string &why)
         for (int C : cands) {
             if (N % C || ef::collide_npc_v(d, N, C, 3) == 0) continue;
             const int planes = N / C, rows = planes * N;
-            for (int v = 1; v <= 4; ++v) {
+            for (int v = 1; v <= 6; ++v) {
                 const int occ = 2 + v;
                 const int rpt = ef::rg_rows_per_thread(v);
+                const int team = ef::rg_team(v);
                 const int tmax = maxthreads_for(ds.prec, d, N, occ);
                 if (tmax == 0) continue;
                 // G in registers: exactly rows / rpt threads; in shared memory: one or two rows each
                 for (int per = (rpt ? rpt : 1); per <= (rpt ? rpt : 2); ++per) {
                     if (rows % per) continue;
-                    const int tpb = rows / per;
+                    const int tpb = rows * team / per;
                     if (tpb > tmax || tpb < 32) continue;
                     const size_t smem = smem_for(ds.prec, d, N, planes, 0, 1, occ);
                     if ((long)smem > smem_max) continue;
@@ -447,8 +448,8 @@ std::string device_key()
 std::string tune_key(const Desc &ds, int N)
 {
     char buf[256];
-    // "v4": kernel layout generation (variants 3 / 4: register-accumulator kernel)
-    std::snprintf(buf, sizeof(buf), "v4 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
+    // "v5": kernel layout generation (variants 3 - 8: register-accumulator kernels, 7 / 8 the team ones)
+    std::snprintf(buf, sizeof(buf), "v5 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
                   ds.d, N, (int)ds.kernel, ds.R, ds.J, ds.nmu, ds.nphi, ds.nc, ds.sigma);
     return buf;
 }

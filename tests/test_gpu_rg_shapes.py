@@ -1,11 +1,12 @@
 """The FP32 3D register-accumulator collide kernel (gain accumulator in registers, forward spectrum
 in shared memory, Nyquist column skipped) on every launch shape the autotuner can pick: cluster
-sizes 1 to 16 and one or two real rows per thread, pinned through EF_SHAPE.  Each shape is checked
+sizes 1 to 16, one or two real rows per thread, and the two-lanes-per-line variants, pinned through
+EF_SHAPE.  Each shape is checked
 against the FP64 oracle (whole cells at N = 16, sampled points above) on a ragged two-cell batch,
 with the dynamic cell queue and the Euler diagnostics (mass against the oracle's).
 
 The shapes are those the kernel's layout admits: C | N, an even split of the N^2 / 2 pencils,
-threads = N^2 / (C RPT) within the instantiation's launch bound, shared memory within the 227 KB
+threads = N^2 / (C RPT) (twice that for the team variants) within the instantiation's launch bound, shared memory within the 227 KB
 limit."""
 import os
 
@@ -29,6 +30,8 @@ def rg_bound(N, v):
         return {16: 128, 24: 288, 32: 256, 40: 200, 48: 192, 64: 128}[N]
     if v == 3:
         return 200 if N in (40, 48) else 0
+    if v in (5, 6):          # two lanes per line (collide_kernel_tm), one or two rows per team
+        return {24: 288, 32: 256, 40: 400, 48: 384}.get(N, 0)
     return 320 if N == 40 else 288 if N in (24, 48) else 256
 
 
@@ -47,12 +50,13 @@ def rg_shapes(N):
             continue
         P = N // C
         npc = N * N // (2 * C)
-        for v in (1, 2, 3, 4):
+        for v in (1, 2, 3, 4, 5, 6):
             smem = 2 * P * _npp(N) * 8 + N * npc * 8 + (P * N * N * 4 if v == 4 else 0) + 33 * 10 * 8 + 16 + 128
             if smem > 232448:
                 continue
-            for per in ((1, 2) if v == 4 else ((2,) if v == 2 else (1,))):
-                t = N * P // per
+            team = 2 if v >= 5 else 1
+            for per in ((1, 2) if v == 4 else ((2,) if v in (2, 6) else (1,))):
+                t = team * N * P // per
                 if (N * P) % per == 0 and 32 <= t <= rg_bound(N, v):
                     out.append((C, t, 2 + v))
     return out
