@@ -45,10 +45,14 @@ __host__ __device__ constexpr bool occ2_built()
     return sizeof(T) == 4 && D == 3 && (N == 24 || N == 32 || N == 40 || N == 48);
 }
 
+// ln f of the diagnostic sums (entropy F ln F and production Q ln F, f > 0).  FP32: the hardware
+// log2 approximation times ln 2 (__logf, a few instructions), whose error (about 2e-7 absolute on
+// ln f) is far below the FP32 path's parity bar of 2e-5 max|Q| sum |ln F| on the production sum;
+// the accurate logf cost as much per element as a length-N transform in the output pass.
 template <typename T>
 __device__ __forceinline__ T log_t(T x);
 template <>
-__device__ __forceinline__ float log_t<float>(float x) { return logf(x); }
+__device__ __forceinline__ float log_t<float>(float x) { return __logf(x); }
 template <>
 __device__ __forceinline__ double log_t<double>(double x) { return log(x); }
 
@@ -133,6 +137,96 @@ struct Diag {
         max_nu = -1e300;
         min_out = 1e300;
     }
+    // one row's partial sums (row index jz along axis 0, jy along axis 1); moments in array-axis
+    // order: [1] axis 0, [2] axis 1, [3] axis 2 (2D: [1] axis 0, [2] axis 1)
+    template <int D, typename T>
+    __device__ __forceinline__ void add_row(T s_m, T s_mx, T s_e2, T s_eta, T s_prod, int jz, int jy, T mn_f, T mn_out)
+    {
+        const double m = (double)s_m;
+        sum[0] += m;
+        if (D == 3) {
+            sum[1] += m * jz;
+            sum[2] += m * jy;
+            sum[3] += (double)s_mx;
+        } else {
+            sum[1] += m * jz;
+            sum[2] += (double)s_mx;
+        }
+        sum[4] += (double)s_e2 + m * ((double)jy * jy + (double)jz * jz);
+        sum[5] += (double)s_eta;
+        sum[6] += (double)s_prod;
+        min_f = fmin(min_f, (double)mn_f);
+        min_out = fmin(min_out, (double)mn_out);
+    }
+};
+
+// Float-float accumulation (an unevaluated sum hi + lo of two FP32 values): Knuth's TwoSum gives
+// the exact rounding error of an FP32 addition, an FMA the exact error of a product (Dekker's
+// TwoProduct), so a running sum keeps about 48 significant bits in FP32 arithmetic.  The FP32 3D
+// kernels accumulate their per-cell diagnostics this way and convert to FP64 once per warp: on
+// GB300 the FP64 pipe runs at a small fraction of the FP32 rate, and FP64 sums over every row
+// cost more than the output pass itself.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void ff_add(FF &x, float b)
+{
+    float s, e;
+    two_sum(x.hi, b, s, e);
+    x.hi = s;
+    x.lo += e;
+}
+// x += a b with the product's rounding error kept
+__device__ __forceinline__ void ff_add_prod(FF &x, float a, float b)
+{
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    ff_add(x, p);
+    x.lo += pe;
+}
+__device__ __forceinline__ FF ff_merge(FF a, FF b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    const float h = s + e;                  // renormalise (|s| >= |e|)
+    return FF{h, e - (h - s)};
+}
+__device__ __forceinline__ double ff_value(FF x) { return (double)x.hi + (double)x.lo; }
+
+struct DiagF {
+    FF sum[7];                              // the seven sums of Diag (slots 0 - 6)
+    float min_f, max_nu, min_out;
+    __device__ __forceinline__ void reset()
+    {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) sum[k] = FF{0.f, 0.f};
+        min_f = 3.0e38f;
+        max_nu = -3.0e38f;
+        min_out = 3.0e38f;
+    }
+    template <int D, typename T>
+    __device__ __forceinline__ void add_row(float s_m, float s_mx, float s_e2, float s_eta, float s_prod, int jz, int jy,
+                                            float mn_f, float mn_out)
+    {
+        static_assert(D == 3, "the float-float diagnostics serve the 3D kernels");
+        ff_add(sum[0], s_m);
+        ff_add_prod(sum[1], s_m, (float)jz);
+        ff_add_prod(sum[2], s_m, (float)jy);
+        ff_add(sum[3], s_mx);
+        ff_add(sum[4], s_e2);
+        ff_add_prod(sum[4], s_m, (float)(jy * jy + jz * jz));
+        ff_add(sum[5], s_eta);
+        ff_add(sum[6], s_prod);
+        min_f = fminf(min_f, mn_f);
+        min_out = fminf(min_out, mn_out);
+    }
 };
 
 // Global row I/O: a row is N contiguous values starting on a 16-byte boundary (the caller's
@@ -182,9 +276,9 @@ __device__ __forceinline__ void store_row(T *dst, const T (&x)[N])
 // non-finite / positivity status checks and the diagnostic sums of the row.  nu (nullable) gives
 // the point-wise collision frequency for the positivity test; otherwise nu_big says whether
 // dt nu > 1 anywhere in this CTA's rows.
-template <typename T, int D, int N>
+template <typename T, int D, int N, typename DG>
 __device__ __forceinline__ void emit_row(const CollideArgs &a, const T (&fr)[N], T *Orow, T (&q)[N], const T *nu,
-                                         bool nu_big, int64_t grow, Diag &dg)
+                                         bool nu_big, int64_t grow, DG &dg)
 {
     constexpr int N1 = (D == 3) ? N : 1;
     const int jz = (int)(grow / N1) - N / 2;
@@ -223,24 +317,7 @@ __device__ __forceinline__ void emit_row(const CollideArgs &a, const T (&fr)[N],
     store_row<T, N>(Orow, q);
     if (bad) record_status(a.status, 7);     // EF_ERR_NOT_FINITE
     if (neg) record_status(a.status, 6);     // EF_ERR_POSITIVITY
-    if (a.diag) {
-        // moments in array-axis order: [1] axis 0, [2] axis 1, [3] axis 2
-        const double m = (double)s_m;
-        dg.sum[0] += m;
-        if (D == 3) {
-            dg.sum[1] += m * jz;
-            dg.sum[2] += m * jy;
-            dg.sum[3] += (double)s_mx;
-        } else {
-            dg.sum[1] += m * jz;
-            dg.sum[2] += (double)s_mx;
-        }
-        dg.sum[4] += (double)s_e2 + m * ((double)jy * jy + (double)jz * jz);
-        dg.sum[5] += (double)s_eta;
-        dg.sum[6] += (double)s_prod;
-        dg.min_f = fmin(dg.min_f, (double)mn_f);
-        dg.min_out = fmin(dg.min_out, (double)mn_out);
-    }
+    if (a.diag) dg.template add_row<D, T>(s_m, s_mx, s_e2, s_eta, s_prod, jz, jy, mn_f, mn_out);
 }
 
 // Distributed shared memory through explicit shared::cluster addresses: mapa turns this CTA's

@@ -103,7 +103,7 @@ __device__ __forceinline__ void tm_c2r_load(const C2<float> *R0, int y0, const C
 // the status checks and the half row's share of the diagnostic sums (the same sums as emit_row).
 template <int N>
 __device__ __forceinline__ void tm_emit_half(const CollideArgs &a, const float (&fr)[N / 2], float *Ohalf, float (&q)[N / 2],
-                                             bool nu_big, int64_t grow, int x0, Diag &dg)
+                                             bool nu_big, int64_t grow, int x0, DiagF &dg)
 {
     constexpr int NH = N / 2;
     const int jz = (int)(grow / N) - N / 2;
@@ -141,18 +141,7 @@ __device__ __forceinline__ void tm_emit_half(const CollideArgs &a, const float (
     store_row<float, NH>(Ohalf, q);
     if (bad) record_status(a.status, 7);     // EF_ERR_NOT_FINITE
     if (neg) record_status(a.status, 6);     // EF_ERR_POSITIVITY
-    if (a.diag) {
-        const double m = (double)s_m;
-        dg.sum[0] += m;
-        dg.sum[1] += m * jz;
-        dg.sum[2] += m * jy;
-        dg.sum[3] += (double)s_mx;
-        dg.sum[4] += (double)s_e2 + m * ((double)jy * jy + (double)jz * jz);
-        dg.sum[5] += (double)s_eta;
-        dg.sum[6] += (double)s_prod;
-        dg.min_f = fmin(dg.min_f, (double)mn_f);
-        dg.min_out = fmin(dg.min_out, (double)mn_out);
-    }
+    if (a.diag) dg.template add_row<3, float>(s_m, s_mx, s_e2, s_eta, s_prod, jz, jy, mn_f, mn_out);
 }
 
 // RPT: rows per team (G of RPT half rows per lane in registers; teams = rows / RPT, threads = 2
@@ -300,7 +289,7 @@ __global__ void __launch_bounds__(LB, MINB) collide_kernel_tm(const CollideArgs 
         }
         bar.full();                        // Fs complete; every slab free again
 
-        Diag dg;
+        DiagF dg;
         T g[RPT][NH];                      // G of this lane's half of rows tm + j teams
 
         for (int o = 0; o < a.nops; ++o) {
@@ -422,18 +411,32 @@ __global__ void __launch_bounds__(LB, MINB) collide_kernel_tm(const CollideArgs 
         // ---------------- per-cell FP64 reduction of the diagnostics
         if (a.diag) {
             const int warp = tid >> 5, nw = (nt + 31) >> 5;
-            dg.sum[7] = dg.min_f;
-            dg.sum[8] = lane == 0 ? (double)s_maxnu[warp] : -1e300;
-            dg.sum[9] = dg.min_out;
+            // float-float sums and FP32 minima across the warp, one FP64 value per warp
 #pragma unroll
-            for (int k = 0; k < kDiag; ++k) {
-                double v = dg.sum[k];
+            for (int k = 0; k < 7; ++k) {
+                FF v = dg.sum[k];
 #pragma unroll
-                for (int sh = 16; sh > 0; sh >>= 1) {
-                    const double u = __shfl_xor_sync(wmask, v, sh);
-                    if ((wmask >> (lane ^ sh)) & 1u) v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
+                for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
+                    FF u;
+                    u.hi = __shfl_xor_sync(wmask, v.hi, sh2);
+                    u.lo = __shfl_xor_sync(wmask, v.lo, sh2);
+                    if ((wmask >> (lane ^ sh2)) & 1u) v = ff_merge(v, u);
                 }
-                if (lane == 0) part[warp * kDiag + k] = v;
+                if (lane == 0) part[warp * kDiag + k] = ff_value(v);
+            }
+            float mnf = dg.min_f, mno = dg.min_out;
+#pragma unroll
+            for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
+                const float u1 = __shfl_xor_sync(wmask, mnf, sh2), u2 = __shfl_xor_sync(wmask, mno, sh2);
+                if ((wmask >> (lane ^ sh2)) & 1u) {
+                    mnf = fminf(mnf, u1);
+                    mno = fminf(mno, u2);
+                }
+            }
+            if (lane == 0) {
+                part[warp * kDiag + 7] = (double)mnf;
+                part[warp * kDiag + 8] = (double)s_maxnu[warp];
+                part[warp * kDiag + 9] = (double)mno;
             }
             __syncthreads();
             if (tid < kDiag) {
@@ -447,20 +450,25 @@ __global__ void __launch_bounds__(LB, MINB) collide_kernel_tm(const CollideArgs 
             }
             bar.full();
             if (rank == 0 && tid < kDiag) {
+                // the other CTAs' values, all loads issued before the first use
                 const int k = tid;
+                double u[16];
+#pragma unroll
+                for (int r = 1; r < 16; ++r)
+                    if (r < C) u[r] = cl.map_shared_rank(part, r)[32 * kDiag + k];
                 double v = part[32 * kDiag + k];
-                for (int r = 1; r < C; ++r) {
-                    const double *rp = cl.map_shared_rank(part, r);
-                    const double u = rp[32 * kDiag + k];
-                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
-                }
+#pragma unroll
+                for (int r = 1; r < 16; ++r)
+                    if (r < C) v = (k == 7 || k == 9) ? fmin(v, u[r]) : (k == 8 ? fmax(v, u[r]) : v + u[r]);
                 const double hd = a.h * a.h * a.h;
                 if (k == 0 || k == 5) v *= hd;
                 else if (k >= 1 && k <= 3) v *= hd * a.h;
                 else if (k == 4) v *= 0.5 * hd * a.h * a.h;
                 a.diag[cglob * kDiag + k] = v;
             }
-            bar.war();
+            // no barrier here: part[] is written again only in the next cell's reduction, after
+            // cluster barriers that rank 0 reaches only once these reads are done (the kernel's
+            // closing barrier covers the last cell)
         }
     }
     bar.war();   // no CTA leaves while a peer may still read its shared memory

@@ -445,12 +445,17 @@ std::string device_key()
     return k + "_sm" + std::to_string(prop.major) + std::to_string(prop.minor) + "_" + std::to_string(prop.multiProcessorCount);
 }
 
-std::string tune_key(const Desc &ds, int N)
+// The cache key: device, discretisation and a bucket of the class's cell count (64, 256, 1024 or
+// more: the best shape for a few dozen cells, as in the chunks of a stream plan, is not the best for
+// a thousand).
+std::string tune_key(const Desc &ds, int N, int64_t ncells)
 {
     char buf[256];
+    int bucket = 64;
+    while (bucket < 4096 && bucket < ncells) bucket *= 4;
     // "v5": kernel layout generation (variants 3 - 8: register-accumulator kernels, 7 / 8 the team ones)
-    std::snprintf(buf, sizeof(buf), "v5 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d", device_key().c_str(), (int)ds.prec,
-                  ds.d, N, (int)ds.kernel, ds.R, ds.J, ds.nmu, ds.nphi, ds.nc, ds.sigma);
+    std::snprintf(buf, sizeof(buf), "v5 %s p%d d%d N%d k%d R%d J%d a%d.%d.%d s%d b%d", device_key().c_str(), (int)ds.prec,
+                  ds.d, N, (int)ds.kernel, ds.R, ds.J, ds.nmu, ds.nphi, ds.nc, ds.sigma, bucket);
     return buf;
 }
 
@@ -482,8 +487,10 @@ void cache_store(const std::string &key, int C, int tpb, int sg, int pf, int pr,
     std::fclose(f);
 }
 
-// Plan-time autotuner: time every candidate shape (and the L1 prefetch on / off) on a scratch
-// batch of ncells_tune cells and keep the fastest.  Results are cached per device and
+// Plan-time autotuner: time every candidate shape (and the L1 prefetch on / off), as an Euler step
+// with the diagnostics, on a scratch batch of up to 512 cells, then the three fastest again on a batch of ncells_tune cells (the size
+// class's own count, up to 2048: the tail of the last round of clusters and the packing of clusters
+// on the SMs depend on it), and keep the fastest of those.  Results are cached per device and
 // discretisation in the file named by EF_AUTOTUNE_CACHE when it is set; EF_AUTOTUNE=0 skips the
 // timing and takes the smallest cluster.
 ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
@@ -516,7 +523,7 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     const char *env = std::getenv("EF_AUTOTUNE");
     const bool tune = ncells_tune > 0 && !(env && env[0] == '0') && shapes.size() > 1;
     if (!tune) return EF_OK;
-    const std::string key = tune_key(ds, cp.N);
+    const std::string key = tune_key(ds, cp.N, ncells_tune);
     int C = 0, tpb = 0, sg = 0, pf = 1, pr = 0, occ = 1;
     if (cache_lookup(key, C, tpb, sg, pf, pr, occ)) {
         for (const Shape &sh : shapes)
@@ -530,11 +537,13 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     const int64_t cell = d == 3 ? (int64_t)cp.N * cp.N * cp.N : (int64_t)cp.N * cp.N;
     const size_t el = ds.prec == EF_PREC_F32 ? 4 : 8;
     void *F = nullptr, *Q = nullptr, *sgws = nullptr, *fhws = nullptr;
+    double *dgws = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaMalloc(&F, ncells_tune * cell * el);
     if (e == cudaSuccess) e = cudaMalloc(&Q, ncells_tune * cell * el);
     if (e == cudaSuccess) e = cudaMemset(F, 0, ncells_tune * cell * el);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&dgws, (size_t)ncells_tune * ef::kDiag * sizeof(double));
     int64_t fh_need = 0;
     for (const Shape &sh : shapes) fh_need = std::max<int64_t>(fh_need, std::min<int64_t>(ncells_tune, sh.max_clusters));
     if (e == cudaSuccess) e = cudaMalloc(&fhws, (size_t)fh_need * ef::collide_fh_bytes(ds.prec, d, cp.N));
@@ -544,6 +553,50 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
     double best = 1e30;
     Shape best_sh = shapes[0];
     int best_pf = 0;
+    struct Timed {
+        double ms;
+        size_t shape;
+        int pf;
+    };
+    std::vector<Timed> sweep;
+    auto time_one = [&](const Shape &sh, int pfv, int64_t nc, double &tmin) -> cudaError_t {
+        const int grid = (int)std::min<int64_t>(nc, sh.max_clusters);
+        ef::CollideArgs a{};
+        a.F = F;
+        a.Q = Q;
+        a.ncells = nc;
+        a.mult = cp.d_mult;
+        a.ops = sh.paired ? cp.d_ops_paired : cp.d_ops_single;
+        a.nops = sh.paired ? cp.nops_paired : cp.nops_single;
+        a.paired = sh.paired;
+        a.cluster = sh.cluster;
+        a.planes = sh.planes;
+        a.sg_global = sh.sg_global;
+        a.sg_ws = sgws;
+        a.fh_ws = fhws;
+        a.npc = ef::collide_npc_v(d, cp.N, sh.cluster, sh.occ);
+        // timed as the step runs it: the Euler output in place (dt = 0 leaves F unchanged) with the
+        // per-cell diagnostics, which cost some shapes more than others
+        a.Q = F;
+        a.out_mode = ef::OUT_EULER;
+        a.dt = 0.0;
+        a.diag = dgws;
+        a.h = 1.0;
+        a.prefetch = pfv;
+        tmin = 1e30;
+        cudaError_t r = cudaSuccess;
+        for (int rep = 0; rep < 4 && r == cudaSuccess; ++rep) {
+            r = cudaEventRecord(e0, st);
+            if (r == cudaSuccess) r = launch_for(ds.prec, d, cp.N, a, grid, sh.tpb, sh.smem, sh.occ, st);
+            if (r == cudaSuccess) r = cudaEventRecord(e1, st);
+            if (r == cudaSuccess) r = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (r == cudaSuccess) r = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, (double)ms);
+        }
+        return r;
+    };
+    const int64_t n1 = std::min<int64_t>(ncells_tune, 512);
     for (size_t i = 0; e == cudaSuccess && i < shapes.size(); ++i) {
         const Shape &sh = shapes[i];
         const int grid = (int)std::min<int64_t>(ncells_tune, sh.max_clusters);
@@ -554,55 +607,51 @@ ef_status choose_shape(const Desc &ds, ClassPlan &cp, int64_t ncells_tune)
             e = cudaMalloc(&sgws, (size_t)grid * sh.cluster * 2 * rows * cp.N * el);
             if (e != cudaSuccess) break;
         }
-        for (int pfv = 0; pfv <= 1; ++pfv) {
-            ef::CollideArgs a{};
-            a.F = F;
-            a.Q = Q;
-            a.ncells = ncells_tune;
-            a.mult = cp.d_mult;
-            a.ops = sh.paired ? cp.d_ops_paired : cp.d_ops_single;
-            a.nops = sh.paired ? cp.nops_paired : cp.nops_single;
-            a.paired = sh.paired;
-            a.cluster = sh.cluster;
-            a.planes = sh.planes;
-            a.sg_global = sh.sg_global;
-            a.sg_ws = sgws;
-            a.fh_ws = fhws;
-            a.npc = ef::collide_npc_v(d, cp.N, sh.cluster, sh.occ);
-            a.out_mode = ef::OUT_COLLIDE;
-            a.h = 1.0;
-            a.prefetch = pfv;
+        for (int pfv = 0; pfv <= 1 && e == cudaSuccess; ++pfv) {
             double tmin = 1e30;
-            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-                e = cudaEventRecord(e0, st);
-                if (e == cudaSuccess) e = launch_for(ds.prec, d, cp.N, a, grid, sh.tpb, sh.smem, sh.occ, st);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) tmin = std::min(tmin, (double)ms);
-            }
-            if (e == cudaSuccess && tmin < best) {
-                best = tmin;
-                best_sh = sh;
-                best_pf = pfv;
-            }
-            if (e == cudaSuccess) {
-                // EF_AUTOTUNE_LOG names a file that receives every timed candidate (tuning records)
-                if (const char *lp = std::getenv("EF_AUTOTUNE_LOG")) {
-                    if (FILE *lf = std::fopen(lp, "a")) {
-                        std::fprintf(lf, "N=%d cells=%lld cluster=%d threads=%d variant=%d sg=%d paired=%d prefetch=%d ms=%.4f\n",
-                                     cp.N, (long long)ncells_tune, sh.cluster, sh.tpb, sh.occ, sh.sg_global, sh.paired, pfv, tmin);
-                        std::fclose(lf);
-                    }
+            e = time_one(sh, pfv, n1, tmin);
+            if (e != cudaSuccess) break;
+            sweep.push_back(Timed{tmin, i, pfv});
+            // EF_AUTOTUNE_LOG names a file that receives every timed candidate (tuning records)
+            if (const char *lp = std::getenv("EF_AUTOTUNE_LOG")) {
+                if (FILE *lf = std::fopen(lp, "a")) {
+                    std::fprintf(lf, "N=%d cells=%lld cluster=%d threads=%d variant=%d sg=%d paired=%d prefetch=%d ms=%.4f\n",
+                                 cp.N, (long long)n1, sh.cluster, sh.tpb, sh.occ, sh.sg_global, sh.paired, pfv, tmin);
+                    std::fclose(lf);
                 }
             }
+        }
+        if (e != cudaSuccess) break;
+    }
+    // the three fastest of the sweep, again on the class's own count (global S/G shapes keep their
+    // sweep time: their workspace is sized for the last swept shape only)
+    std::sort(sweep.begin(), sweep.end(), [](const Timed &x, const Timed &y) { return x.ms < y.ms; });
+    for (size_t j = 0; e == cudaSuccess && j < sweep.size() && j < 3; ++j) {
+        const Shape &sh = shapes[sweep[j].shape];
+        double tmin = sweep[j].ms * (double)ncells_tune / (double)n1;
+        if (ncells_tune > n1 && !sh.sg_global) {
+            e = time_one(sh, sweep[j].pf, ncells_tune, tmin);
+            if (e != cudaSuccess) break;
+            if (const char *lp = std::getenv("EF_AUTOTUNE_LOG")) {
+                if (FILE *lf = std::fopen(lp, "a")) {
+                    std::fprintf(lf, "N=%d cells=%lld cluster=%d threads=%d variant=%d sg=%d paired=%d prefetch=%d ms=%.4f\n",
+                                 cp.N, (long long)ncells_tune, sh.cluster, sh.tpb, sh.occ, sh.sg_global, sh.paired,
+                                 sweep[j].pf, tmin);
+                    std::fclose(lf);
+                }
+            }
+        }
+        if (tmin < best) {
+            best = tmin;
+            best_sh = sh;
+            best_pf = sweep[j].pf;
         }
     }
     cudaFree(F);
     cudaFree(Q);
     cudaFree(sgws);
     cudaFree(fhws);
+    cudaFree(dgws);
     if (st) cudaStreamDestroy(st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -742,7 +791,7 @@ ef_status build_class(const Desc &ds, ClassPlan &cp)
         if (e != cudaSuccess) return cuda_fail(e, "feature table");
         cp.nfeat = (int)modes.size() / 3;
     }
-    return choose_shape(ds, cp, cp.ncells > 0 ? std::min<int64_t>(cp.ncells, 512) : 0);
+    return choose_shape(ds, cp, cp.ncells > 0 ? std::min<int64_t>(cp.ncells, 2048) : 0);
 }
 
 // Workspaces of one class for every cluster that can be resident at once (max_clusters, fixed by
