@@ -169,7 +169,7 @@ struct Diag {
 struct FF {
     float hi, lo;
 };
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+__device__ __forceinline__ void ff_two_sum(float a, float b, float &s, float &e)
 {
     s = a + b;
     const float bb = s - a;
@@ -178,7 +178,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 __device__ __forceinline__ void ff_add(FF &x, float b)
 {
     float s, e;
-    two_sum(x.hi, b, s, e);
+    ff_two_sum(x.hi, b, s, e);
     x.hi = s;
     x.lo += e;
 }
@@ -193,7 +193,7 @@ __device__ __forceinline__ void ff_add_prod(FF &x, float a, float b)
 __device__ __forceinline__ FF ff_merge(FF a, FF b)
 {
     float s, e;
-    two_sum(a.hi, b.hi, s, e);
+    ff_two_sum(a.hi, b.hi, s, e);
     e += a.lo + b.lo;
     const float h = s + e;                  // renormalise (|s| >= |e|)
     return FF{h, e - (h - s)};

@@ -10,21 +10,22 @@ cudaError_t moments_launch(int prec, int d, const void *F, const void *Q, const 
 {
     if (ncells <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)(ncells < 65535 * 16 ? ncells : 65535 * 16);
+    const bool q = Q != nullptr;
+#define EF_MOM(T, D)                                                                                     \
+    do {                                                                                                 \
+        if (q) moments_kernel<T, D, true><<<grid, 256, 0, s>>>((const T *)F, (const T *)Q, cell_off, cell_N, \
+                                                               ncells, N_uniform, twoL, out);            \
+        else moments_kernel<T, D, false><<<grid, 256, 0, s>>>((const T *)F, nullptr, cell_off, cell_N,   \
+                                                              ncells, N_uniform, twoL, out);             \
+    } while (0)
     if (prec == 0) {
-        if (d == 3)
-            moments_kernel<float, 3><<<grid, 256, 0, s>>>((const float *)F, (const float *)Q, cell_off, cell_N,
-                                                          ncells, N_uniform, twoL, out);
-        else
-            moments_kernel<float, 2><<<grid, 256, 0, s>>>((const float *)F, (const float *)Q, cell_off, cell_N,
-                                                          ncells, N_uniform, twoL, out);
+        if (d == 3) EF_MOM(float, 3);
+        else EF_MOM(float, 2);
     } else {
-        if (d == 3)
-            moments_kernel<double, 3><<<grid, 256, 0, s>>>((const double *)F, (const double *)Q, cell_off, cell_N,
-                                                           ncells, N_uniform, twoL, out);
-        else
-            moments_kernel<double, 2><<<grid, 256, 0, s>>>((const double *)F, (const double *)Q, cell_off, cell_N,
-                                                           ncells, N_uniform, twoL, out);
+        if (d == 3) EF_MOM(double, 3);
+        else EF_MOM(double, 2);
     }
+#undef EF_MOM
     return cudaGetLastError();
 }
 

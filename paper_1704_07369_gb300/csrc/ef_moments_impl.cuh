@@ -36,7 +36,9 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 // the FP32 one.  FP32 error: at most about (3 + 32 + 8) * 2^-24 of the sum of |terms| (a float4's
 // four terms, a run of 32 float4 partials, the pair, the warp); the logarithm is the fast one
 // (a few ulp), in the same budget.
-template <typename T, int D>
+// HASQ: Q is given (the FP32 vector path then keeps four float4 of F and four of Q in flight per
+// thread; with F alone, eight of F: one cell per CTA leaves few loads in flight otherwise).
+template <typename T, int D, bool HASQ>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) moments_kernel(const T *F, const T *Q, const int64_t *cell_off,
                                                       const int64_t *cell_N, int64_t ncells, int N_uniform,
                                                       double h_uniform_times_N, double *out)
@@ -67,19 +69,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) moments_kernel(co
             if (vec) {
                 const int nv = (int)((int64_t)nrows * N / 4);
                 const float4 *F4 = reinterpret_cast<const float4 *>(F + coff);
-                const float4 *Q4 = Q ? reinterpret_cast<const float4 *>(Q + coff) : nullptr;
-                constexpr int UV = 4;
+                const float4 *Q4 = HASQ ? reinterpret_cast<const float4 *>(Q + coff) : nullptr;
+                constexpr int UV = HASQ ? 4 : 8;
                 const int bd = blockDim.x;
                 const float half = float(N / 2);
                 int run = 0;
                 for (int v0 = threadIdx.x; v0 < nv; v0 += UV * bd) {
-                    float4 fv[UV], qv[UV];
+                    float4 fv[UV], qv[HASQ ? UV : 1];
 #pragma unroll
                     for (int u = 0; u < UV; ++u) {
                         const int v = v0 + u * bd;
                         const bool ok = v < nv;
                         fv[u] = ok ? F4[v] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        qv[u] = (ok && Q4) ? Q4[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if constexpr (HASQ) qv[u] = ok ? Q4[v] : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < UV; ++u) {
@@ -98,7 +100,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) moments_kernel(co
                         const float jz = (D == 3) ? float(zz) - half : 0.f, jy = float(yy) - half;
                         const float jx0 = float(x0) - half;
                         const float fa[4] = {fv[u].x, fv[u].y, fv[u].z, fv[u].w};
-                        const float qa[4] = {qv[u].x, qv[u].y, qv[u].z, qv[u].w};
+                        float qa[4] = {0.f, 0.f, 0.f, 0.f};
+                        if constexpr (HASQ) {
+                            qa[0] = qv[u].x; qa[1] = qv[u].y; qa[2] = qv[u].z; qa[3] = qv[u].w;
+                        }
                         float sf = 0.f, sfx = 0.f, sfxx = 0.f, seta = 0.f, sprod = 0.f, sneg = 0.f;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
@@ -109,10 +114,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) moments_kernel(co
                             sfxx = fmaf(fx, jx, sfxx);
                             const float lf = __logf(f > 1e-30f ? f : 1e-30f);
                             seta += f > 0.f ? f * lf : 0.f;
-                            if (Q4) sprod += f > 0.f ? qa[j] * lf : 0.f;
+                            if constexpr (HASQ) sprod += f > 0.f ? qa[j] * lf : 0.f;
                             mn = fminf(mn, f);
                             sneg += f < 0.f ? -f : 0.f;
-                            if (Q4) mq = fminf(mq, qa[j]);
+                            if constexpr (HASQ) mq = fminf(mq, qa[j]);
                         }
                         p0 += sf;
                         if (D == 3) {
