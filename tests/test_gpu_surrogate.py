@@ -367,11 +367,13 @@ def test_entropy_gate_switch():
     assert torch.equal(q0[keep], q1[keep])
 
 
-def test_features_inverse_projects_on_the_band():
+@pytest.mark.parametrize("N", [16, 24, 32, 40, 48, 64])
+def test_features_inverse_projects_on_the_band(N):
     """ef_features_inverse returns a band-limited field exactly (features -> grid -> features is the
     identity on the band) and maps a general cell to its truncation to |k| <= 6, against the
-    oracle's DFT with the modes outside the band zeroed."""
-    N, L, n = 32, 8.0, 3
+    oracle's DFT with the modes outside the band zeroed; every grid size of the band pass (its
+    planes per chunk and row swizzle depend on N)."""
+    L, n = 8.0, 3
     plan = ef.Plan(3, N, L, ef.EF_KERNEL_HARD_SPHERE, 32, ef.EF_PREC_F32)
     cells = [inputs.mixture_cell(3, N, L, 90 + i) for i in range(n)]
     F = torch.tensor(np.stack(cells), dtype=torch.float32, device="cuda")
