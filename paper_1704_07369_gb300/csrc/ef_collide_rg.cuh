@@ -180,6 +180,90 @@ __device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, int y0, const C
     fft<N, 1, N>(z);
 }
 
+// Per-cell reduction of the FP32 3D kernels' diagnostics, FP32 until the last step: float-float
+// sums and FP32 minima / maxima across each warp (shuffles), across the CTA's warps (kDiag threads)
+// and across the cluster's CTAs (rank 0, distributed shared memory), then one conversion to FP64
+// and the cell's scale factors.  part (33 * kDiag doubles of shared memory) holds float-float
+// pairs here: [warp][k][hi, lo], [32][k][hi, lo] the CTA's.  Slot 8 (max nu) comes from the loss
+// op's per-warp maxima.  (GB300's FP64 pipe runs at a small fraction of the FP32 rate: FP64 sums
+// over the warps took about as long as a cell's output pass.)
+template <typename SYNC>
+__device__ __forceinline__ void diag_reduce_cell(const CollideArgs &a, const DiagF &dg, const float *s_maxnu, double *part,
+                                                 unsigned wmask, int lane, int tid, int nt, int rank, int C, SYNC &bar,
+                                                 cg::cluster_group &cl, int64_t cglob)
+{
+    float *pf = reinterpret_cast<float *>(part);
+    const int warp = tid >> 5, nw = (nt + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        FF v = dg.sum[k];
+#pragma unroll
+        for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
+            FF u;
+            u.hi = __shfl_xor_sync(wmask, v.hi, sh2);
+            u.lo = __shfl_xor_sync(wmask, v.lo, sh2);
+            if ((wmask >> (lane ^ sh2)) & 1u) v = ff_merge(v, u);
+        }
+        if (lane == 0) {
+            pf[(warp * kDiag + k) * 2] = v.hi;
+            pf[(warp * kDiag + k) * 2 + 1] = v.lo;
+        }
+    }
+    float mnf = dg.min_f, mno = dg.min_out;
+#pragma unroll
+    for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
+        const float u1 = __shfl_xor_sync(wmask, mnf, sh2), u2 = __shfl_xor_sync(wmask, mno, sh2);
+        if ((wmask >> (lane ^ sh2)) & 1u) {
+            mnf = fminf(mnf, u1);
+            mno = fminf(mno, u2);
+        }
+    }
+    if (lane == 0) {
+        pf[(warp * kDiag + 7) * 2] = mnf;
+        pf[(warp * kDiag + 8) * 2] = s_maxnu[warp];
+        pf[(warp * kDiag + 9) * 2] = mno;
+    }
+    __syncthreads();
+    if (tid < kDiag) {
+        const int k = tid;
+        FF v{pf[k * 2], pf[k * 2 + 1]};
+        for (int w2 = 1; w2 < nw; ++w2) {
+            const FF u{pf[(w2 * kDiag + k) * 2], pf[(w2 * kDiag + k) * 2 + 1]};
+            if (k == 7 || k == 9) v.hi = fminf(v.hi, u.hi);
+            else if (k == 8) v.hi = fmaxf(v.hi, u.hi);
+            else v = ff_merge(v, u);
+        }
+        pf[(32 * kDiag + k) * 2] = v.hi;
+        pf[(32 * kDiag + k) * 2 + 1] = (k >= 7) ? 0.f : v.lo;
+    }
+    bar.full();
+    if (rank == 0 && tid < kDiag) {
+        // the other CTAs' values, all loads issued before the first use
+        const int k = tid;
+        float2 u[16];
+#pragma unroll
+        for (int r = 1; r < 16; ++r)
+            if (r < C) u[r] = *reinterpret_cast<const float2 *>(cl.map_shared_rank(pf, r) + (32 * kDiag + k) * 2);
+        FF v{pf[(32 * kDiag + k) * 2], pf[(32 * kDiag + k) * 2 + 1]};
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+            if (r >= C) continue;
+            if (k == 7 || k == 9) v.hi = fminf(v.hi, u[r].x);
+            else if (k == 8) v.hi = fmaxf(v.hi, u[r].x);
+            else v = ff_merge(v, FF{u[r].x, u[r].y});
+        }
+        double d = ff_value(v);
+        const double hd = a.h * a.h * a.h;
+        if (k == 0 || k == 5) d *= hd;
+        else if (k >= 1 && k <= 3) d *= hd * a.h;
+        else if (k == 4) d *= 0.5 * hd * a.h * a.h;
+        a.diag[cglob * kDiag + k] = d;
+    }
+    // no barrier here: part[] is written again only in the next cell's reduction, after cluster
+    // barriers that rank 0 reaches only once these reads are done (the kernel's closing barrier
+    // covers the last cell)
+}
+
 // GS = false: G of this thread's RPT rows in registers (nt * RPT = rows); GS = true: G in shared
 // memory, column-major ([x][row], so consecutive threads touch consecutive banks), rows looped.
 template <int D, int N, int RPT, int LB, bool GS>
@@ -462,68 +546,8 @@ __global__ void __launch_bounds__(LB, 1) collide_kernel_rg(const CollideArgs a)
             bar.war();
         }
 
-        // ---------------- per-cell FP64 reduction of the diagnostics
-        if (a.diag) {
-            const int warp = tid >> 5, nw = (nt + 31) >> 5;
-            // float-float sums and FP32 minima across the warp, one FP64 value per warp
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                FF v = dg.sum[k];
-#pragma unroll
-                for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
-                    FF u;
-                    u.hi = __shfl_xor_sync(wmask, v.hi, sh2);
-                    u.lo = __shfl_xor_sync(wmask, v.lo, sh2);
-                    if ((wmask >> (lane ^ sh2)) & 1u) v = ff_merge(v, u);
-                }
-                if (lane == 0) part[warp * kDiag + k] = ff_value(v);
-            }
-            float mnf = dg.min_f, mno = dg.min_out;
-#pragma unroll
-            for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
-                const float u1 = __shfl_xor_sync(wmask, mnf, sh2), u2 = __shfl_xor_sync(wmask, mno, sh2);
-                if ((wmask >> (lane ^ sh2)) & 1u) {
-                    mnf = fminf(mnf, u1);
-                    mno = fminf(mno, u2);
-                }
-            }
-            if (lane == 0) {
-                part[warp * kDiag + 7] = (double)mnf;
-                part[warp * kDiag + 8] = (double)s_maxnu[warp];
-                part[warp * kDiag + 9] = (double)mno;
-            }
-            __syncthreads();
-            if (tid < kDiag) {
-                const int k = tid;
-                double v = part[k];
-                for (int w2 = 1; w2 < nw; ++w2) {
-                    const double u = part[w2 * kDiag + k];
-                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
-                }
-                part[32 * kDiag + k] = v;
-            }
-            bar.full();
-            if (rank == 0 && tid < kDiag) {
-                // the other CTAs' values, all loads issued before the first use
-                const int k = tid;
-                double u[16];
-#pragma unroll
-                for (int r = 1; r < 16; ++r)
-                    if (r < C) u[r] = cl.map_shared_rank(part, r)[32 * kDiag + k];
-                double v = part[32 * kDiag + k];
-#pragma unroll
-                for (int r = 1; r < 16; ++r)
-                    if (r < C) v = (k == 7 || k == 9) ? fmin(v, u[r]) : (k == 8 ? fmax(v, u[r]) : v + u[r]);
-                const double hd = a.h * a.h * a.h;
-                if (k == 0 || k == 5) v *= hd;
-                else if (k >= 1 && k <= 3) v *= hd * a.h;
-                else if (k == 4) v *= 0.5 * hd * a.h * a.h;
-                a.diag[cglob * kDiag + k] = v;
-            }
-            // no barrier here: part[] is written again only in the next cell's reduction, after
-            // cluster barriers that rank 0 reaches only once these reads are done (the kernel's
-            // closing barrier covers the last cell)
-        }
+        // ---------------- per-cell reduction of the diagnostics
+        if (a.diag) diag_reduce_cell(a, dg, s_maxnu, part, wmask, lane, tid, nt, rank, C, bar, cl, cglob);
     }
     bar.war();   // no CTA leaves while a peer may still read its shared memory
 }

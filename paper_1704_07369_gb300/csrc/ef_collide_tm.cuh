@@ -408,68 +408,8 @@ __global__ void __launch_bounds__(LB, MINB) collide_kernel_tm(const CollideArgs 
             bar.war();
         }
 
-        // ---------------- per-cell FP64 reduction of the diagnostics
-        if (a.diag) {
-            const int warp = tid >> 5, nw = (nt + 31) >> 5;
-            // float-float sums and FP32 minima across the warp, one FP64 value per warp
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                FF v = dg.sum[k];
-#pragma unroll
-                for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
-                    FF u;
-                    u.hi = __shfl_xor_sync(wmask, v.hi, sh2);
-                    u.lo = __shfl_xor_sync(wmask, v.lo, sh2);
-                    if ((wmask >> (lane ^ sh2)) & 1u) v = ff_merge(v, u);
-                }
-                if (lane == 0) part[warp * kDiag + k] = ff_value(v);
-            }
-            float mnf = dg.min_f, mno = dg.min_out;
-#pragma unroll
-            for (int sh2 = 16; sh2 > 0; sh2 >>= 1) {
-                const float u1 = __shfl_xor_sync(wmask, mnf, sh2), u2 = __shfl_xor_sync(wmask, mno, sh2);
-                if ((wmask >> (lane ^ sh2)) & 1u) {
-                    mnf = fminf(mnf, u1);
-                    mno = fminf(mno, u2);
-                }
-            }
-            if (lane == 0) {
-                part[warp * kDiag + 7] = (double)mnf;
-                part[warp * kDiag + 8] = (double)s_maxnu[warp];
-                part[warp * kDiag + 9] = (double)mno;
-            }
-            __syncthreads();
-            if (tid < kDiag) {
-                const int k = tid;
-                double v = part[k];
-                for (int w2 = 1; w2 < nw; ++w2) {
-                    const double u = part[w2 * kDiag + k];
-                    v = (k == 7 || k == 9) ? fmin(v, u) : (k == 8 ? fmax(v, u) : v + u);
-                }
-                part[32 * kDiag + k] = v;
-            }
-            bar.full();
-            if (rank == 0 && tid < kDiag) {
-                // the other CTAs' values, all loads issued before the first use
-                const int k = tid;
-                double u[16];
-#pragma unroll
-                for (int r = 1; r < 16; ++r)
-                    if (r < C) u[r] = cl.map_shared_rank(part, r)[32 * kDiag + k];
-                double v = part[32 * kDiag + k];
-#pragma unroll
-                for (int r = 1; r < 16; ++r)
-                    if (r < C) v = (k == 7 || k == 9) ? fmin(v, u[r]) : (k == 8 ? fmax(v, u[r]) : v + u[r]);
-                const double hd = a.h * a.h * a.h;
-                if (k == 0 || k == 5) v *= hd;
-                else if (k >= 1 && k <= 3) v *= hd * a.h;
-                else if (k == 4) v *= 0.5 * hd * a.h * a.h;
-                a.diag[cglob * kDiag + k] = v;
-            }
-            // no barrier here: part[] is written again only in the next cell's reduction, after
-            // cluster barriers that rank 0 reaches only once these reads are done (the kernel's
-            // closing barrier covers the last cell)
-        }
+        // ---------------- per-cell reduction of the diagnostics
+        if (a.diag) diag_reduce_cell(a, dg, s_maxnu, part, wmask, lane, tid, nt, rank, C, bar, cl, cglob);
     }
     bar.war();   // no CTA leaves while a peer may still read its shared memory
 }
