@@ -46,9 +46,9 @@ __host__ __device__ constexpr bool occ2_built()
 }
 
 // ln f of the diagnostic sums (entropy F ln F and production Q ln F, f > 0).  FP32: the hardware
-// log2 approximation times ln 2 (__logf, a few instructions), whose error (about 2e-7 absolute on
-// ln f) is far below the FP32 path's parity bar of 2e-5 max|Q| sum |ln F| on the production sum;
-// the accurate logf cost as much per element as a length-N transform in the output pass.
+// log2 approximation times ln 2 (__logf, a few instructions instead of the accurate logf's
+// sequence), whose error (about 2e-7 absolute on ln f) is far below the FP32 path's parity bar of
+// 2e-5 max|Q| sum |ln F| on the production sum.
 template <typename T>
 __device__ __forceinline__ T log_t(T x);
 template <>
@@ -163,9 +163,8 @@ struct Diag {
 // Float-float accumulation (an unevaluated sum hi + lo of two FP32 values): Knuth's TwoSum gives
 // the exact rounding error of an FP32 addition, an FMA the exact error of a product (Dekker's
 // TwoProduct), so a running sum keeps about 48 significant bits in FP32 arithmetic.  The FP32 3D
-// kernels accumulate their per-cell diagnostics this way and convert to FP64 once per warp: on
-// GB300 the FP64 pipe runs at a small fraction of the FP32 rate, and FP64 sums over every row
-// cost more than the output pass itself.
+// kernels accumulate their per-cell diagnostics this way and convert to FP64 once per cell: on
+// GB300 the FP64 pipe runs at a small fraction of the FP32 rate.
 struct FF {
     float hi, lo;
 };

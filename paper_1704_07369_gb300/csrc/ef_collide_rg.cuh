@@ -185,8 +185,8 @@ __device__ __forceinline__ void rg_c2r_rows(const C2<float> *R0, int y0, const C
 // and across the cluster's CTAs (rank 0, distributed shared memory), then one conversion to FP64
 // and the cell's scale factors.  part (33 * kDiag doubles of shared memory) holds float-float
 // pairs here: [warp][k][hi, lo], [32][k][hi, lo] the CTA's.  Slot 8 (max nu) comes from the loss
-// op's per-warp maxima.  (GB300's FP64 pipe runs at a small fraction of the FP32 rate: FP64 sums
-// over the warps took about as long as a cell's output pass.)
+// op's per-warp maxima.  (GB300's FP64 pipe runs at a small fraction of the FP32 rate, so the
+// sums stay on the FP32 pipe; float-float keeps about 48 significant bits.)
 template <typename SYNC>
 __device__ __forceinline__ void diag_reduce_cell(const CollideArgs &a, const DiagF &dg, const float *s_maxnu, double *part,
                                                  unsigned wmask, int lane, int tid, int nt, int rank, int C, SYNC &bar,
