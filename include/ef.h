@@ -373,11 +373,13 @@ ef_status ef_galerkin_destroy(ef_galerkin_t g);
 
 /* Streaming a batch that lives in host memory (no counterpart in the paper; the paper's method
  * is per cell).  The cells (sizes N_host[c], back to back as for ef_plan_create_batched) are cut
- * into nchunks contiguous chunks of about equal work, each with its own batched plan and CUDA
- * stream, and a device copy of the whole batch is allocated here.  ef_stream_euler_step uploads
- * each chunk, runs nsteps Euler steps on it (ef_euler_step) and downloads it, in place in F_host;
- * chunks run concurrently, so copies in both directions overlap the collision steps of other
- * chunks when F_host is page-locked (pageable memory works but serialises the copies).  diag_host
+ * into nchunks contiguous chunks of about equal work, each with its own batched plan, and a device
+ * copy of the whole batch is allocated here with the plan's streams: one for the uploads, one for
+ * the downloads and up to four for the steps.  ef_stream_euler_step uploads each chunk, runs nsteps
+ * Euler steps on it (ef_euler_step) and downloads it, in place in F_host; the uploads run back to
+ * back, a chunk's steps start when its upload is done and its download when its steps are, so
+ * copies in both directions overlap the collision steps of other chunks when F_host is page-locked
+ * (pageable memory works but serialises the copies).  diag_host
  * (nullable) receives nsteps * ncells * EF_DIAG_STRIDE doubles, [step][cell][k] as ef_euler_step
  * (through a one-step device buffer allocated here, copied out after each step).  All work is
  * ordered after earlier work on `stream`, and later work on `stream` waits for it; the host

@@ -21,10 +21,17 @@ struct ef_stream_plan_s {
         ef_plan_t plan = nullptr;
         int64_t c0 = 0, nc = 0;        // first cell and cell count
         int64_t e0 = 0, ne = 0;        // first element and element count
-        cudaStream_t s = nullptr;
-        cudaEvent_t done = nullptr;
+        cudaStream_t s = nullptr;        // one of the compute streams (not owned)
+        cudaEvent_t up = nullptr;        // the chunk's upload is done
+        cudaEvent_t done = nullptr;      // the chunk's steps (and diagnostics copies) are done
     };
     std::vector<Chunk> chunks;
+    // a three-stage pipeline: every upload on one stream (the host-to-device copies run back to
+    // back), the steps on a few compute streams (at most kComputeStreams chunks in flight, so that
+    // their small launches do not crowd each other off the SMs), every download on one stream
+    cudaStream_t up_s = nullptr, down_s = nullptr;
+    std::vector<cudaStream_t> comp;
+    cudaEvent_t down_done = nullptr;
     void *F_dev = nullptr;
     double *diag_dev = nullptr;        // one step's diagnostics of the whole batch (made at create)
     cudaEvent_t fork = nullptr;
@@ -32,6 +39,8 @@ struct ef_stream_plan_s {
 };
 
 namespace {
+
+constexpr int kComputeStreams = 4;
 
 ef_status sp_fail(ef_status s, const std::string &m)
 {
@@ -51,9 +60,14 @@ void sp_free(ef_stream_plan_s *sp)
     if (!sp) return;
     for (auto &c : sp->chunks) {
         if (c.plan) ef_plan_destroy(c.plan);
-        if (c.s) cudaStreamDestroy(c.s);
+        if (c.up) cudaEventDestroy(c.up);
         if (c.done) cudaEventDestroy(c.done);
     }
+    for (cudaStream_t q : sp->comp)
+        if (q) cudaStreamDestroy(q);
+    if (sp->up_s) cudaStreamDestroy(sp->up_s);
+    if (sp->down_s) cudaStreamDestroy(sp->down_s);
+    if (sp->down_done) cudaEventDestroy(sp->down_done);
     if (sp->fork) cudaEventDestroy(sp->fork);
     cudaFree(sp->F_dev);
     cudaFree(sp->diag_dev);
@@ -111,12 +125,21 @@ ef_status ef_stream_plan_create(int d, int64_t ncells, const int *N_host, double
         ch.ne = elem - ch.e0;
         ef_status st = ef_plan_create_batched(d, ch.nc, N_host + ch.c0, L, kernel, R, prec, &ch.plan);
         if (st != EF_OK) { sp_free(sp); return st; }
-        e = cudaStreamCreateWithFlags(&ch.s, cudaStreamNonBlocking);
+        if ((int)sp->comp.size() < kComputeStreams) {
+            cudaStream_t q = nullptr;
+            e = cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking);
+            sp->comp.push_back(q);
+        }
+        ch.s = sp->comp[sp->chunks.size() % sp->comp.size()];
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ch.up, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ch.done, cudaEventDisableTiming);
         sp->chunks.push_back(ch);
         if (e != cudaSuccess) { sp_free(sp); return sp_cuda(e, "chunk stream"); }
     }
     e = cudaEventCreateWithFlags(&sp->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sp->down_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sp->up_s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sp->down_s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&sp->F_dev, (size_t)elem * sp->el);
     if (e == cudaSuccess) e = cudaMalloc((void **)&sp->diag_dev, (size_t)ncells * EF_DIAG_STRIDE * sizeof(double));
     if (e != cudaSuccess) { sp_free(sp); return sp_cuda(e, "stream plan buffers"); }
@@ -165,13 +188,20 @@ ef_status ef_stream_euler_step(ef_stream_plan_t sp, void *F_host, double dt, int
     unsigned char *Fh = static_cast<unsigned char *>(F_host);
     unsigned char *Fd = static_cast<unsigned char *>(sp->F_dev);
     const size_t row = EF_DIAG_STRIDE * sizeof(double);
-    size_t started = 0;                                // chunks with work enqueued on their stream
     ef_status st = EF_OK;
+    // every stream of the plan waits for the caller's prior work; the uploads also wait for the
+    // previous call's downloads (the device buffer is reused, whatever stream that call was on)
+    e = cudaStreamWaitEvent(sp->up_s, sp->fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sp->up_s, sp->down_done, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sp->down_s, sp->fork, 0);
+    for (size_t j = 0; e == cudaSuccess && j < sp->comp.size(); ++j) e = cudaStreamWaitEvent(sp->comp[j], sp->fork, 0);
+    if (e != cudaSuccess) return sp_cuda(e, "fork wait");
     for (auto &c : sp->chunks) {
-        e = cudaStreamWaitEvent(c.s, sp->fork, 0);
-        if (e != cudaSuccess) { st = sp_cuda(e, "fork wait"); break; }
-        ++started;
-        e = cudaMemcpyAsync(Fd + c.e0 * sp->el, Fh + c.e0 * sp->el, c.ne * sp->el, cudaMemcpyHostToDevice, c.s);
+        // upload (one stream: the copies run back to back), steps (the chunk's compute stream, after
+        // its upload), download (one stream, after the chunk's steps)
+        e = cudaMemcpyAsync(Fd + c.e0 * sp->el, Fh + c.e0 * sp->el, c.ne * sp->el, cudaMemcpyHostToDevice, sp->up_s);
+        if (e == cudaSuccess) e = cudaEventRecord(c.up, sp->up_s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c.s, c.up, 0);
         if (e != cudaSuccess) { st = sp_cuda(e, "upload"); break; }
         // one step at a time: the chunk's slice of the one-step diagnostics buffer is copied out
         // on the chunk's stream before the next step overwrites it
@@ -185,17 +215,26 @@ ef_status ef_stream_euler_step(ef_stream_plan_t sp, void *F_host, double dt, int
             }
         }
         if (st != EF_OK) break;
-        e = cudaMemcpyAsync(Fh + c.e0 * sp->el, Fd + c.e0 * sp->el, c.ne * sp->el, cudaMemcpyDeviceToHost, c.s);
+        e = cudaEventRecord(c.done, c.s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sp->down_s, c.done, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(Fh + c.e0 * sp->el, Fd + c.e0 * sp->el, c.ne * sp->el, cudaMemcpyDeviceToHost, sp->down_s);
         if (e != cudaSuccess) { st = sp_cuda(e, "download"); break; }
     }
-    // join every chunk that has work enqueued into the caller's stream, on success and on an error
-    // part way (so that F_host and diag_host are free for reuse once `stream` has completed)
-    for (size_t i = 0; i < started; ++i) {
-        auto &c = sp->chunks[i];
-        e = cudaEventRecord(c.done, c.s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c.done, 0);
+    // join every stream of the plan into the caller's stream, on success and on an error part way
+    // (so that F_host and diag_host are free for reuse once `stream` has completed); the events
+    // are recorded after all work enqueued so far on each stream
+    e = cudaEventRecord(sp->down_done, sp->up_s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, sp->down_done, 0);
+    if (e != cudaSuccess && st == EF_OK) st = sp_cuda(e, "join");
+    for (size_t j = 0; j < sp->comp.size(); ++j) {
+        e = cudaEventRecord(sp->chunks[j].done, sp->comp[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, sp->chunks[j].done, 0);
         if (e != cudaSuccess && st == EF_OK) st = sp_cuda(e, "join");
     }
+    e = cudaEventRecord(sp->down_done, sp->down_s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, sp->down_done, 0);
+    if (e != cudaSuccess && st == EF_OK) st = sp_cuda(e, "join");
     return st;
 }
 
