@@ -283,9 +283,10 @@ ef_status ef_surrogate_infer(ef_surrogate_t sur, const void *F_dev, float *qfeat
  * trained like the first from another seed).  With a checker set, the delivered band is the mean
  * of the two networks' decoded bands q and c (an ensemble of two), and the score
  * ||q - c||_2 / ||(q + c) / 2||_2 over the band (zero mode excluded) above tol (> 0) sends the cell
- * to the plain operator (flags bit 32, with 8).  Two independently trained networks disagree most
- * where each is least reliable, so a score threshold calibrated on held-out cells flags the cells
- * whose prediction misses the tolerance.
+ * to the plain operator (flags bit 32, with 8).  The score correlates with the error of the
+ * delivered band, so a threshold calibrated on held-out cells sends the cells most at risk to the
+ * plain operator; it bounds no single cell's error (a few misses can score below a threshold that
+ * flags a few percent of the cells).
  * Allocates the checker's output rows for max_batch cells on the first call (a set-up call);
  * checker = null switches the gate off.  The paper has no counterpart. */
 ef_status ef_surrogate_set_checker(ef_surrogate_t sur, ef_mlp_t checker, float tol);
